@@ -1,0 +1,186 @@
+"""ctypes binding of the plain C FP64 oracle (``sal_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: shares no code with the CUDA path and imports nothing from it.
+``build()`` compiles ``liboracle.so`` next to this file with gcc (OpenMP for the per-voxel
+loops).  All arrays cross as numpy float32 (volumes) or float64 (everything the oracle
+computes).
+
+Parity status: every function below is pinned by the ``-m "not gpu"`` tests against
+closed forms, library special cases (numpy FFT, numpy.pad) or brute force; none is
+"parity unpinned" against the method's own definition.  Against the paper's own printed
+output parity is unpinned: the paper prints no values (its result figure is an image of
+data not available here).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sal_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+REFLECT, PERIODIC = 0, 1
+STENCIL_26, STENCIL_LINE = 0, 1
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc if it is missing or older than its source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        f32p = ctypes.POINTER(ctypes.c_float)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L_, I_, D_ = ctypes.c_long, ctypes.c_int, ctypes.c_double
+        lib.orc_ext_index.argtypes = [L_, L_, I_]
+        lib.orc_ext_index.restype = L_
+        for name in ("oracle_local_spectrum_brute", "oracle_local_spectrum_separable"):
+            fn = getattr(lib, name)
+            fn.argtypes = [f32p, L_, L_, L_, I_, I_, L_, L_, L_, f64p]
+            fn.restype = I_
+        lib.oracle_weights.argtypes = [I_, f64p]
+        lib.oracle_weights.restype = None
+        lib.oracle_project.argtypes = [f64p, L_, I_, f64p]
+        lib.oracle_project.restype = None
+        lib.oracle_energy.argtypes = [f32p, L_, L_, L_, I_, I_, I_, I_, f64p]
+        lib.oracle_energy.restype = I_
+        lib.oracle_energy_at.argtypes = [f32p, L_, L_, L_, I_, I_, i64p, L_, I_, f64p]
+        lib.oracle_energy_at.restype = I_
+        lib.oracle_dcs.argtypes = [f64p, L_, L_, L_, I_, I_, I_, D_, I_, f64p]
+        lib.oracle_dcs.restype = I_
+        lib.oracle_stats.argtypes = [f64p, L_, f64p]
+        lib.oracle_stats.restype = None
+        lib.oracle_combine.argtypes = [f64p, f64p, L_, D_, D_, D_, D_, f64p]
+        lib.oracle_combine.restype = None
+        lib.oracle_saliency.argtypes = [f32p, L_, L_, L_, I_, I_, I_, D_, D_, D_, D_, D_, I_,
+                                        f64p, f64p, f64p, f64p]
+        lib.oracle_saliency.restype = I_
+        _lib = lib
+    return _lib
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def ext_index(i: int, n: int, bnd: int = REFLECT) -> int:
+    """Boundary extension of one coordinate onto 0..n-1."""
+    return int(_load().orc_ext_index(int(i), int(n), int(bnd)))
+
+
+def local_spectrum(V, t, x, y, L, bnd=REFLECT, brute=False) -> np.ndarray:
+    """|F| of the local cube at voxel (t, x, y): [L][L][L], centred signed frequency order."""
+    V, vp = _f32(V)
+    out, op = _f64(np.zeros((L, L, L)))
+    fn = _load().oracle_local_spectrum_brute if brute else _load().oracle_local_spectrum_separable
+    rc = fn(vp, *V.shape, L, bnd, t, x, y, op)
+    if rc:
+        raise ValueError(f"oracle local spectrum failed ({rc})")
+    return out
+
+
+def weights(L) -> np.ndarray:
+    """Projection weights w[3][L][L][L] (t, x, y), centred order, 0 at DC."""
+    out, op = _f64(np.zeros((3, L, L, L)))
+    _load().oracle_weights(L, op)
+    return out
+
+
+def project(mag, L) -> np.ndarray:
+    """Spectral energies [3][n] from magnitude spectra [n][L][L][L]."""
+    mag, mp = _f64(np.asarray(mag).reshape(-1, L * L * L))
+    n = mag.shape[0]
+    out, op = _f64(np.zeros((3, n)))
+    _load().oracle_project(mp, n, L, op)
+    return out
+
+
+def energy(V, L, bnd=REFLECT, brute=False, threads=None) -> np.ndarray:
+    """E_t, E_x, E_y of every voxel: [3][T][X][Y] float64."""
+    V, vp = _f32(V)
+    out, op = _f64(np.zeros((3,) + V.shape))
+    rc = _load().oracle_energy(vp, *V.shape, L, bnd, int(brute), threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_energy failed ({rc})")
+    return out
+
+
+def energy_at(V, coords, L, bnd=REFLECT, threads=None) -> np.ndarray:
+    """E_m at selected voxels ``coords`` [n][3] (int): [3][n] float64."""
+    V, vp = _f32(V)
+    c = np.ascontiguousarray(np.asarray(coords, dtype=np.int64).reshape(-1, 3))
+    n = c.shape[0]
+    out, op = _f64(np.zeros((3, n)))
+    rc = _load().oracle_energy_at(vp, *V.shape, L, bnd, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  n, threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_energy_at failed ({rc})")
+    return out
+
+
+def dcs(E, bnd=REFLECT, stencil=STENCIL_26, L=7, sigma=1.0, threads=None) -> np.ndarray:
+    """S_t, S_x, S_y from E [3][T][X][Y] (Eq. 5)."""
+    E, ep = _f64(E)
+    shape = E.shape[1:]
+    out, op = _f64(np.zeros(E.shape))
+    rc = _load().oracle_dcs(ep, *shape, bnd, stencil, L, float(sigma), threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_dcs failed ({rc})")
+    return out
+
+
+def stats(Sm) -> np.ndarray:
+    """[3][3] = (min, max, sum) of each map."""
+    Sm, sp = _f64(Sm)
+    out, op = _f64(np.zeros(9))
+    _load().oracle_stats(sp, Sm[0].size, op)
+    return out.reshape(3, 3)
+
+
+def combine(Sm, st, a=1 / 3, b=1 / 3, c=1 / 3, eps=1e-6) -> np.ndarray:
+    """Eq. 6 on min-max normalised maps."""
+    Sm, sp = _f64(Sm)
+    st, tp = _f64(np.asarray(st).reshape(9))
+    out, op = _f64(np.zeros(Sm.shape[1:]))
+    _load().oracle_combine(sp, tp, Sm[0].size, a, b, c, eps, op)
+    return out
+
+
+def saliency(V, L=7, bnd=REFLECT, stencil=STENCIL_26, sigma=1.0, a=1 / 3, b=1 / 3, c=1 / 3,
+             eps=1e-6, threads=None, full=False):
+    """The whole method.  Returns S, or (S, E, Sm, stats) when ``full``."""
+    V, vp = _f32(V)
+    S, sp = _f64(np.zeros(V.shape))
+    E, ep = _f64(np.zeros((3,) + V.shape))
+    Sm, mp = _f64(np.zeros((3,) + V.shape))
+    st, tp = _f64(np.zeros(9))
+    rc = _load().oracle_saliency(vp, *V.shape, L, bnd, stencil, float(sigma), a, b, c, eps,
+                                 threads or default_threads(), sp, ep, mp, tp)
+    if rc:
+        raise ValueError(f"oracle_saliency failed ({rc})")
+    return (S, E, Sm, st.reshape(3, 3)) if full else S

@@ -1,0 +1,432 @@
+/*
+ * Plain FP64 CPU oracle of the seismic saliency method (Shafiq, Long, Alshawi, AlRegib,
+ * "Saliency detection for seismic applications using multi-dimensional spectral
+ * projections and directional comparisons", ICIP 2017, Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls this
+ * file: only the tests, the smoke check and the benchmark's CPU-baseline leg do.  It
+ * shares no code, header, table or helper with the CUDA library; every quantity here is
+ * computed from its definition, in double precision, with plain loops and libm.
+ *
+ * Readings of the paper where it is silent or ambiguous (each is repeated where used):
+ *  R1  frequency indices in the projection weights are centred signed indices -h..h
+ *      (h = (L-1)/2), so that i = j = k = 0 is the centre of the spectral cube (Sec. 2,
+ *      text after Eq. 4) and the weights are symmetric;
+ *  R2  features use |F| (the magnitude spectrum); the weights are >= 0, so |F_m| = w_m |F|;
+ *  R3  "absolute mean over each local cube" (Sec. 2, third step) is the mean of |F_m| over
+ *      the L^3 - 1 non-DC points (the DC point is excluded, text after Eq. 4);
+ *  R4  one cube per voxel (stride 1), the voxel at offset h inside its cube, odd L;
+ *  R5  samples outside the volume come from a boundary extension: REFLECT (whole-sample
+ *      symmetric, edge not repeated: ... c b | a b c d | c b a ...) or PERIODIC (wrap);
+ *  R6  Eq. 5 is taken literally, w on the neighbour inside |.|, with Gaussian weights
+ *      g(o) = exp(-|o|^2 / (2 sigma^2)); E outside the volume uses the same extension;
+ *  R7  neighbourhoods: the 26 voxels around the centre (Q = 26), or the paper's d x 1
+ *      line of side d = L along axis m for map m (offsets +-1..+-h, Q = L - 1);
+ *  R8  before Eq. 6 each S_m is min-max normalised with global min and max; a map whose
+ *      range hi - lo <= eps * max(|hi|, |lo|) is treated as constant and becomes 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_REFLECT 0
+#define ORC_PERIODIC 1
+#define ORC_STENCIL_26 0
+#define ORC_STENCIL_LINE 1
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* R5: map any integer coordinate i onto 0..n-1. */
+long orc_ext_index(long i, long n, int bnd)
+{
+    if (bnd == ORC_PERIODIC) {
+        long r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    if (n == 1) return 0;
+    long period = 2 * (n - 1);
+    long r = i % period;
+    if (r < 0) r += period;
+    return r < n ? r : period - r;
+}
+
+static double vol_at(const float *V, long T, long X, long Y, int bnd, long t, long x, long y)
+{
+    long te = orc_ext_index(t, T, bnd), xe = orc_ext_index(x, X, bnd), ye = orc_ext_index(y, Y, bnd);
+    return (double)V[(te * X + xe) * Y + ye];
+}
+
+/* The local cube f[p][q][r] = V[t-h+p][x-h+q][y-h+r] (R4, R5), with its mean removed.
+ * Removing the mean changes no DFT coefficient off DC (the DFT of a constant is zero
+ * there); it makes the off-DC spectrum of a constant cube exactly zero in floating point.
+ * The DC coefficient is never used (text after Eq. 4). */
+static void load_cube(const float *V, long T, long X, long Y, int L, int bnd,
+                      long t, long x, long y, double *f)
+{
+    int h = (L - 1) / 2;
+    double s = 0.0;
+    for (int p = 0; p < L; ++p)
+        for (int q = 0; q < L; ++q)
+            for (int r = 0; r < L; ++r) {
+                double v = vol_at(V, T, X, Y, bnd, t - h + p, x - h + q, y - h + r);
+                f[(p * L + q) * L + r] = v;
+                s += v;
+            }
+    double mean = s / (double)(L * L * L);
+    for (int i = 0; i < L * L * L; ++i) f[i] -= mean;
+}
+
+/* Centred signed frequency index of storage slot s (R1): s = 0..L-1 -> -h..h. */
+static int freq_of_slot(int s, int L) { return s - (L - 1) / 2; }
+
+/* exp(-2 pi i n k / L) with the product reduced mod L first, so the angle is exact. */
+static void twiddle(int n, int k, int L, double *c, double *s)
+{
+    long m = ((long)n * (long)k) % L;
+    if (m < 0) m += L;
+    double a = -2.0 * ORC_PI * (double)m / (double)L;
+    *c = cos(a);
+    *s = sin(a);
+}
+
+/*
+ * |F[mu,nu,omega]| of one local cube by the direct triple sum of the DFT printed in Sec. 2
+ * (below Eq. 2):  F = L^-3 sum_{p,q,r} f[p,q,r] exp(-2 pi i (p mu + q nu + r omega) / L).
+ * Output mag[(mu+h)][(nu+h)][(omega+h)] for mu, nu, omega in -h..h (R1).  O(L^6).
+ */
+int oracle_local_spectrum_brute(const float *V, long T, long X, long Y, int L, int bnd,
+                                long t, long x, long y, double *mag)
+{
+    if (L < 1 || (L % 2) == 0) return -1;
+    int n3 = L * L * L;
+    double *f = (double *)malloc(sizeof(double) * n3);
+    if (!f) return -2;
+    load_cube(V, T, X, Y, L, bnd, t, x, y, f);
+    double inv = 1.0 / (double)n3;
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b)
+            for (int c = 0; c < L; ++c) {
+                int mu = freq_of_slot(a, L), nu = freq_of_slot(b, L), om = freq_of_slot(c, L);
+                double re = 0.0, im = 0.0;
+                for (int p = 0; p < L; ++p)
+                    for (int q = 0; q < L; ++q)
+                        for (int r = 0; r < L; ++r) {
+                            long m = ((long)p * mu + (long)q * nu + (long)r * om) % L;
+                            if (m < 0) m += L;
+                            double ang = -2.0 * ORC_PI * (double)m / (double)L;
+                            double v = f[(p * L + q) * L + r];
+                            re += v * cos(ang);
+                            im += v * sin(ang);
+                        }
+                mag[(a * L + b) * L + c] = sqrt(re * re + im * im) * inv;
+            }
+    /* DC slot: the mean was removed, so report the DC magnitude of the original cube. */
+    {
+        int h = (L - 1) / 2;
+        double s = 0.0;
+        for (int p = 0; p < L; ++p)
+            for (int q = 0; q < L; ++q)
+                for (int r = 0; r < L; ++r)
+                    s += vol_at(V, T, X, Y, bnd, t - h + p, x - h + q, y - h + r);
+        mag[(h * L + h) * L + h] = fabs(s) * inv;
+    }
+    free(f);
+    return 0;
+}
+
+/*
+ * The same spectrum with the DFT applied one axis at a time (the transform is separable:
+ * the exponential factors into one term per axis).  Stage 1 along t, stage 2 along x,
+ * stage 3 along y; each stage is a product with the L x L DFT matrix.  O(3 L^4).
+ */
+static void spectrum_separable_from_cube(const double *f, int L, double *mag)
+{
+    int n3 = L * L * L;
+    double *g1r = (double *)calloc(n3, sizeof(double)), *g1i = (double *)calloc(n3, sizeof(double));
+    double *g2r = (double *)calloc(n3, sizeof(double)), *g2i = (double *)calloc(n3, sizeof(double));
+    double *cs = (double *)malloc(sizeof(double) * L * L), *sn = (double *)malloc(sizeof(double) * L * L);
+    for (int a = 0; a < L; ++a)
+        for (int p = 0; p < L; ++p) twiddle(freq_of_slot(a, L), p, L, &cs[a * L + p], &sn[a * L + p]);
+    /* stage 1: G1[mu][q][r] = sum_p f[p][q][r] e^{-2 pi i p mu / L} */
+    for (int a = 0; a < L; ++a)
+        for (int q = 0; q < L; ++q)
+            for (int r = 0; r < L; ++r) {
+                double re = 0.0, im = 0.0;
+                for (int p = 0; p < L; ++p) {
+                    double v = f[(p * L + q) * L + r];
+                    re += v * cs[a * L + p];
+                    im += v * sn[a * L + p];
+                }
+                g1r[(a * L + q) * L + r] = re;
+                g1i[(a * L + q) * L + r] = im;
+            }
+    /* stage 2: G2[mu][nu][r] = sum_q G1[mu][q][r] e^{-2 pi i q nu / L} */
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b)
+            for (int r = 0; r < L; ++r) {
+                double re = 0.0, im = 0.0;
+                for (int q = 0; q < L; ++q) {
+                    double xr = g1r[(a * L + q) * L + r], xi = g1i[(a * L + q) * L + r];
+                    double c = cs[b * L + q], s = sn[b * L + q];
+                    re += xr * c - xi * s;
+                    im += xr * s + xi * c;
+                }
+                g2r[(a * L + b) * L + r] = re;
+                g2i[(a * L + b) * L + r] = im;
+            }
+    /* stage 3: F[mu][nu][omega] = L^-3 sum_r G2[mu][nu][r] e^{-2 pi i r omega / L} */
+    double inv = 1.0 / (double)n3;
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b)
+            for (int c3 = 0; c3 < L; ++c3) {
+                double re = 0.0, im = 0.0;
+                for (int r = 0; r < L; ++r) {
+                    double xr = g2r[(a * L + b) * L + r], xi = g2i[(a * L + b) * L + r];
+                    double c = cs[c3 * L + r], s = sn[c3 * L + r];
+                    re += xr * c - xi * s;
+                    im += xr * s + xi * c;
+                }
+                mag[(a * L + b) * L + c3] = sqrt(re * re + im * im) * inv;
+            }
+    free(g1r); free(g1i); free(g2r); free(g2i); free(cs); free(sn);
+}
+
+int oracle_local_spectrum_separable(const float *V, long T, long X, long Y, int L, int bnd,
+                                    long t, long x, long y, double *mag)
+{
+    if (L < 1 || (L % 2) == 0) return -1;
+    int n3 = L * L * L, h = (L - 1) / 2;
+    double *f = (double *)malloc(sizeof(double) * n3);
+    if (!f) return -2;
+    load_cube(V, T, X, Y, L, bnd, t, x, y, f);
+    spectrum_separable_from_cube(f, L, mag);
+    double s = 0.0;
+    for (int p = 0; p < L; ++p)
+        for (int q = 0; q < L; ++q)
+            for (int r = 0; r < L; ++r) s += vol_at(V, T, X, Y, bnd, t - h + p, x - h + q, y - h + r);
+    mag[(h * L + h) * L + h] = fabs(s) / (double)n3;
+    free(f);
+    return 0;
+}
+
+/*
+ * Projection weights of Eq. 1-4, stored w[m][(mu+h)][(nu+h)][(omega+h)] for m = t, x, y:
+ *   w_t = sqrt(nu^2 + omega^2) / rho,  w_x = sqrt(mu^2 + omega^2) / rho,
+ *   w_y = sqrt(mu^2 + nu^2) / rho,     rho = sqrt(mu^2 + nu^2 + omega^2)
+ * (i, j, k of the paper are mu, nu, omega here, reading R1).  The DC point, where the
+ * ratios are 0/0, gets weight 0: it is excluded from the features (text after Eq. 4).
+ */
+void oracle_weights(int L, double *w)
+{
+    int n3 = L * L * L;
+    for (int a = 0; a < L; ++a)
+        for (int b = 0; b < L; ++b)
+            for (int c = 0; c < L; ++c) {
+                double i = freq_of_slot(a, L), j = freq_of_slot(b, L), k = freq_of_slot(c, L);
+                int idx = (a * L + b) * L + c;
+                double rho = sqrt(i * i + j * j + k * k);
+                if (rho == 0.0) {
+                    w[idx] = w[n3 + idx] = w[2 * n3 + idx] = 0.0;
+                } else {
+                    w[idx] = sqrt(j * j + k * k) / rho;
+                    w[n3 + idx] = sqrt(i * i + k * k) / rho;
+                    w[2 * n3 + idx] = sqrt(i * i + j * j) / rho;
+                }
+            }
+}
+
+/* Spectral energies (Sec. 2, third step, readings R2, R3): E_m = (L^3-1)^-1 sum_{!=DC} w_m |F|. */
+void oracle_project(const double *mag, long n_vox, int L, double *E)
+{
+    int n3 = L * L * L;
+    double *w = (double *)malloc(sizeof(double) * 3 * n3);
+    oracle_weights(L, w);
+    int h = (L - 1) / 2, dc = (h * L + h) * L + h;
+    for (long v = 0; v < n_vox; ++v)
+        for (int m = 0; m < 3; ++m) {
+            double s = 0.0;
+            for (int i = 0; i < n3; ++i)
+                if (i != dc) s += w[m * n3 + i] * mag[v * n3 + i];
+            E[m * n_vox + v] = s / (double)(n3 - 1);
+        }
+    free(w);
+}
+
+/*
+ * E_t, E_x, E_y for every voxel of V (steps one to three of Sec. 2).  E is [3][T*X*Y].
+ * `brute` selects the direct DFT sum; otherwise the separable one.  OpenMP over t.
+ */
+int oracle_energy(const float *V, long T, long X, long Y, int L, int bnd, int brute,
+                  int nthreads, double *E)
+{
+    if (L < 1 || (L % 2) == 0 || T < 1 || X < 1 || Y < 1) return -1;
+    long N = T * X * Y;
+    int n3 = L * L * L, h = (L - 1) / 2, dc = (h * L + h) * L + h;
+    double *w = (double *)malloc(sizeof(double) * 3 * n3);
+    oracle_weights(L, w);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (long t = 0; t < T; ++t) {
+        double *mag = (double *)malloc(sizeof(double) * n3);
+        for (long x = 0; x < X; ++x)
+            for (long y = 0; y < Y; ++y) {
+                int rc = brute ? oracle_local_spectrum_brute(V, T, X, Y, L, bnd, t, x, y, mag)
+                               : oracle_local_spectrum_separable(V, T, X, Y, L, bnd, t, x, y, mag);
+                if (rc) err = rc;
+                long v = (t * X + x) * Y + y;
+                for (int m = 0; m < 3; ++m) {
+                    double s = 0.0;
+                    for (int i = 0; i < n3; ++i)
+                        if (i != dc) s += w[m * n3 + i] * mag[i];
+                    E[m * N + v] = s / (double)(n3 - 1);
+                }
+            }
+        free(mag);
+    }
+    free(w);
+    return err;
+}
+
+/* E_m at selected voxels only (separable DFT), for checks on volumes too large to sweep. */
+int oracle_energy_at(const float *V, long T, long X, long Y, int L, int bnd,
+                     const int64_t *coords /* [n][3] */, long n, int nthreads, double *E /* [3][n] */)
+{
+    if (L < 1 || (L % 2) == 0) return -1;
+    int n3 = L * L * L, h = (L - 1) / 2, dc = (h * L + h) * L + h;
+    double *w = (double *)malloc(sizeof(double) * 3 * n3);
+    oracle_weights(L, w);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+    for (long k = 0; k < n; ++k) {
+        double *mag = (double *)malloc(sizeof(double) * n3);
+        oracle_local_spectrum_separable(V, T, X, Y, L, bnd, coords[3 * k], coords[3 * k + 1],
+                                        coords[3 * k + 2], mag);
+        for (int m = 0; m < 3; ++m) {
+            double s = 0.0;
+            for (int i = 0; i < n3; ++i)
+                if (i != dc) s += w[m * n3 + i] * mag[i];
+            E[m * n + k] = s / (double)(n3 - 1);
+        }
+        free(mag);
+    }
+    free(w);
+    return 0;
+}
+
+/* Offsets of the neighbourhood of map m (reading R7); returns Q. */
+static int neighbourhood(int stencil, int m, int L, int off[][3])
+{
+    int Q = 0;
+    if (stencil == ORC_STENCIL_26) {
+        for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b)
+                for (int c = -1; c <= 1; ++c) {
+                    if (a == 0 && b == 0 && c == 0) continue;
+                    off[Q][0] = a; off[Q][1] = b; off[Q][2] = c; ++Q;
+                }
+    } else {
+        int h = (L - 1) / 2;
+        for (int k = -h; k <= h; ++k) {
+            if (k == 0) continue;
+            off[Q][0] = off[Q][1] = off[Q][2] = 0;
+            off[Q][m] = k;
+            ++Q;
+        }
+    }
+    return Q;
+}
+
+/*
+ * Directional centre-surround comparison, Eq. 5 (reading R6):
+ *   S_m[v] = Q^-1 sum_{o in N_m} | E_m[v] - g(o) E_m[v + o] |,  g(o) = exp(-|o|^2 / (2 sigma^2)).
+ * E and Sm are [3][T*X*Y].
+ */
+int oracle_dcs(const double *E, long T, long X, long Y, int bnd, int stencil, int L,
+               double sigma, int nthreads, double *Sm)
+{
+    if (T < 1 || X < 1 || Y < 1 || sigma <= 0.0) return -1;
+    if (stencil != ORC_STENCIL_26 && (L < 3 || (L % 2) == 0)) return -1;
+    long N = T * X * Y;
+    for (int m = 0; m < 3; ++m) {
+        int off[64][3];
+        int Q = neighbourhood(stencil, m, L, off);
+        double g[64];
+        for (int k = 0; k < Q; ++k) {
+            double d2 = (double)(off[k][0] * off[k][0] + off[k][1] * off[k][1] + off[k][2] * off[k][2]);
+            g[k] = exp(-d2 / (2.0 * sigma * sigma));
+        }
+        const double *Em = E + m * N;
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1)
+        for (long t = 0; t < T; ++t)
+            for (long x = 0; x < X; ++x)
+                for (long y = 0; y < Y; ++y) {
+                    double c = Em[(t * X + x) * Y + y];
+                    double s = 0.0;
+                    for (int k = 0; k < Q; ++k) {
+                        long tn = orc_ext_index(t + off[k][0], T, bnd);
+                        long xn = orc_ext_index(x + off[k][1], X, bnd);
+                        long yn = orc_ext_index(y + off[k][2], Y, bnd);
+                        s += fabs(c - g[k] * Em[(tn * X + xn) * Y + yn]);
+                    }
+                    Sm[m * N + (t * X + x) * Y + y] = s / (double)Q;
+                }
+    }
+    return 0;
+}
+
+/* Global min, max and sum of each S_m: stats[3m + 0..2]. */
+void oracle_stats(const double *Sm, long N, double *stats)
+{
+    for (int m = 0; m < 3; ++m) {
+        double lo = Sm[m * N], hi = Sm[m * N], s = 0.0;
+        for (long v = 0; v < N; ++v) {
+            double a = Sm[m * N + v];
+            if (a < lo) lo = a;
+            if (a > hi) hi = a;
+            s += a;
+        }
+        stats[3 * m] = lo;
+        stats[3 * m + 1] = hi;
+        stats[3 * m + 2] = s;
+    }
+}
+
+/* Eq. 6 on min-max normalised maps (reading R8): S = a N_t + b N_x + c N_y. */
+void oracle_combine(const double *Sm, const double *stats, long N, double a, double b, double c,
+                    double eps, double *S)
+{
+    double wts[3] = {a, b, c};
+    double lo[3], scale[3];
+    for (int m = 0; m < 3; ++m) {
+        double l = stats[3 * m], hgh = stats[3 * m + 1];
+        double mag = fabs(hgh) > fabs(l) ? fabs(hgh) : fabs(l);
+        lo[m] = l;
+        scale[m] = (hgh - l) <= eps * mag ? 0.0 : 1.0 / (hgh - l);
+    }
+    for (long v = 0; v < N; ++v) {
+        double s = 0.0;
+        for (int m = 0; m < 3; ++m) s += wts[m] * (Sm[m * N + v] - lo[m]) * scale[m];
+        S[v] = s;
+    }
+}
+
+/* The whole method (Fig. 1): energies, DCS, normalisation and Eq. 6.  Optional outputs may be NULL. */
+int oracle_saliency(const float *V, long T, long X, long Y, int L, int bnd, int stencil,
+                    double sigma, double a, double b, double c, double eps, int nthreads,
+                    double *S, double *E_out, double *Sm_out, double *stats_out)
+{
+    long N = T * X * Y;
+    double *E = E_out ? E_out : (double *)malloc(sizeof(double) * 3 * N);
+    double *Sm = Sm_out ? Sm_out : (double *)malloc(sizeof(double) * 3 * N);
+    double st[9];
+    int rc = oracle_energy(V, T, X, Y, L, bnd, 0, nthreads, E);
+    if (!rc) rc = oracle_dcs(E, T, X, Y, bnd, stencil, L, sigma, nthreads, Sm);
+    if (!rc) {
+        oracle_stats(Sm, N, st);
+        oracle_combine(Sm, st, N, a, b, c, eps, S);
+        if (stats_out) memcpy(stats_out, st, sizeof(st));
+    }
+    if (!E_out) free(E);
+    if (!Sm_out) free(Sm);
+    return rc;
+}
