@@ -1,0 +1,354 @@
+"""Saliency throughput benchmark (voxels/s) of the GB300 CUDA path, with the FP64 CPU
+oracle as the reference arm.
+
+Default workload: the plain FP32 method on an F3-shaped synthetic volume
+462 x 951 x 651 (time x crossline x inline, 286,024,662 voxels, 1.14 GB float32), local
+cube L = 7, 26-neighbourhood, REFLECT boundary.  One step = one pass of the whole hot
+path over the volume: spectral energies (fused local 3D DFT + projections + mean),
+directional centre-surround, FP64 statistics and the normalised combination.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank processes its own copy of the workload (independent
+volumes, no data-path collective; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (shape, kind, seed)
+    "f3": ((462, 951, 651), "f3", 1),
+    "cube64": ((64, 64, 64), "basic", 0),
+    "cube256": ((256, 256, 256), "basic", 2),
+}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def algorithmic_flops_per_voxel(L: int) -> int:
+    """FP32 flops per voxel of the fused energy stage as the algorithm defines it (FMA = 2).
+
+    Separable real-input DFT with the +-k folding (stage t on the real cube columns, stage
+    x on the mu >= 0 half, stage y per voxel), |F| (mul + fma + sqrt), the projection
+    weights (3 FMAs per (mu, |nu|, |omega|) group) and the final scale.  Each stage is
+    counted once per voxel, i.e. without the halo recomputation of a tiled kernel.
+    """
+    H = (L - 1) // 2
+    real_pass = 5 * H + 4 * H * H                  # t stage, and x stage of mu = 0
+    cplx_pass = 10 * H + 8 * H * H + 4 * H         # x stage of one mu > 0
+    cline = 10 * H + 4 + H * (8 * H + 13)          # y stage: one complex line (all omega)
+    rline = 4 * H + H * (4 * H + 4)                # y stage: the real (0, 0) line
+    n_cl = H + H * (2 * H + 1)
+    groups = H + H * (H + 1) + H * (H + 1) ** 2
+    pair_adds = H * H * (H + 1)
+    y = n_cl * cline + rline + 6 * groups + pair_adds
+    return real_pass + (real_pass + H * cplx_pass) + y + 3
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx = [], []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [s.strip() for s in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(V: np.ndarray, L: int, target_s: float = 15.0):
+    """Time the CPU oracle on a crop of the workload volume sized for about target_s seconds."""
+    import oracle
+    oracle.build()
+    T, X, Y = V.shape
+    cores = cpu_cores()
+    probe = np.ascontiguousarray(V[:min(T, 32), :min(X, 16), :min(Y, 64)])
+    t0 = time.perf_counter()
+    oracle.saliency(probe, L=L, threads=cores)
+    rate = probe.size / max(time.perf_counter() - t0, 1e-3)
+    want = max(int(rate * target_s), 4096)
+    ny = min(Y, 128)
+    nx = max(1, min(X, want // (T * ny)))
+    crop = np.ascontiguousarray(V[:, :nx, :ny])
+    t0 = time.perf_counter()
+    oracle.saliency(crop, L=L, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": crop.size / dt, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, whole method on a {T}x{nx}x{ny} crop ({crop.size} voxels) of the "
+                      f"workload volume, {dt:.1f} s, OpenMP over t"}, crop.shape, dt
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_1901_11095_gb300 import synth
+    import oracle
+    oracle.build()
+    shape, kind, seed = WORKLOADS[args.workload]
+    V = synth.make_volume(shape, seed=seed, kind=kind)
+    cores = cpu_cores()
+    T, X, Y = V.shape
+    crop = np.ascontiguousarray(V[:, :min(X, 8), :min(Y, 64)])
+    for _ in range(args.warmup):
+        oracle.saliency(crop[:, :1, :], L=args.L, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.saliency(crop, L=args.L, threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = crop.size / (ms / 1e3)
+    out = {"impl": "reference", "metric": "saliency voxels/s", "value": value, "unit": "voxels/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(args),
+           "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+                            "sample": f"each step: FP64 oracle on a {crop.shape[0]}x{crop.shape[1]}x{crop.shape[2]} "
+                                      f"crop ({crop.size} voxels) of the workload volume"},
+           "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(args) -> dict:
+    shape = WORKLOADS[args.workload][0]
+    return {"workload": f"plain method {args.precision.upper()}, {'F3-shaped' if args.workload == 'f3' else 'synthetic'}"
+                        f" volume {shape[0]}x{shape[1]}x{shape[2]}, local cube {args.L}, 26-neighbourhood",
+            "volume": list(shape), "L": args.L, "precision": args.precision, "boundary": "reflect",
+            "stencil": "26", "l2": "inputs larger than L2 (V 1.14 GB, E and S_m 3.4 GB each); no flush needed"
+            if args.workload == "f3" else "flush buffer written between steps"}
+
+
+def run_ours(args, rank: int, world: int) -> None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_1901_11095_gb300 import api, synth
+
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
+    shape, kind, seed = WORKLOADS[args.workload]
+    V_np = synth.make_volume(shape, seed=seed + rank, kind=kind)
+    N = V_np.size
+    p = api.params(L=args.L, precision=args.precision)
+    V = torch.from_numpy(V_np).to(dev)
+    E = torch.empty((3,) + shape, device=dev, dtype=torch.float32)
+    Sm = torch.empty_like(E)
+    S = torch.empty(shape, device=dev, dtype=torch.float32)
+    stats = torch.empty(9, device=dev, dtype=torch.float64)
+    dims = api.dims_of(V)
+    ws_dcs = torch.empty(api.sal_dcs_workspace_size(dims, p), device=dev, dtype=torch.uint8)
+    ws_all = torch.empty(api.sal_workspace_size(dims, p), device=dev, dtype=torch.uint8)
+    stream = torch.cuda.current_stream(dev)
+    flush = None if N * 4 > 256 << 20 else torch.empty(512 << 20, device=dev, dtype=torch.uint8)
+
+    def step(ev=None):
+        if flush is not None:
+            flush.zero_()
+        if ev is not None:
+            ev[0].record(stream)
+        api.sal_spectral_energy(V, p, E=E, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        api.sal_directional_compare(E, p, Sm=Sm, stats=stats, ws=ws_dcs, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        api.sal_combine(Sm, stats, p, S=S, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            step(evs[i])
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    k1 = [e[0].elapsed_time(e[1]) for e in evs]
+    k2 = [e[1].elapsed_time(e[2]) for e in evs]
+    k4 = [e[2].elapsed_time(e[3]) for e in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][3])
+    ms = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms / 1e3)
+
+    # end to end through the public API: pinned host V -> device, sal_saliency, S -> pinned host
+    Vh = torch.from_numpy(V_np).pin_memory()
+    Sh = torch.empty(shape, dtype=torch.float32).pin_memory()
+    Vd = torch.empty_like(V)
+
+    def e2e_step():
+        Vd.copy_(Vh, non_blocking=True)
+        api.sal_saliency(Vd, p, S=S, stats=stats, ws=ws_all, stream=stream)
+        Sh.copy_(S, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_e2e = max(1, min(args.steps, 5))
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    k1_ms = statistics.mean(k1)
+    flops = algorithmic_flops_per_voxel(args.L) * N
+    achieved = flops / (k1_ms / 1e3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
+    k4_gbs = 16 * N / (statistics.mean(k4) / 1e3) / 1e9
+    out = {
+        "metric": "saliency voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args),
+        "roofline": {"bound": "alu", "kernel": "spectral energy (fused local DFT, projections, mean)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "traffic": None,
+                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
+                                    f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
+                     "flops_per_voxel": algorithmic_flops_per_voxel(args.L)},
+        "kernels_ms": {"spectral_energy": k1_ms, "directional_compare_and_stats": statistics.mean(k2),
+                       "combine": statistics.mean(k4)},
+        "hbm_stages": {"directional_compare_GBs": k2_gbs, "combine_GBs": k4_gbs, "peak_GBs": hbm,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
+                       "bytes_per_voxel": {"directional_compare": 24, "combine": 16}},
+        "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N, "ms_per_step": e2e_ms},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        cb, _, _ = oracle_sample(V_np, args.L, target_s=args.cpu_seconds)
+        out["cpu_baseline"] = cb
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="f3")
+    ap.add_argument("--L", type=int, default=7)
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sys.path.insert(0, ROOT)
+    import __graft_entry__
+    __graft_entry__.build()
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

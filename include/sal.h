@@ -1,0 +1,154 @@
+/*
+ * sal.h - C ABI of the GB300 seismic saliency library (libsal.so).
+ *
+ * The method is the one of Shafiq, Long, Alshawi and AlRegib, "Saliency detection for
+ * seismic applications using multi-dimensional spectral projections and directional
+ * comparisons" (ICIP 2017), Sec. 2 and Fig. 1:
+ *   (1) a local 3D DFT of an L x L x L cube around every voxel (the DFT printed below Eq. 2),
+ *   (2) projection of each spectral point onto the three planes (Eq. 1-4), DC excluded,
+ *   (3) the absolute mean of each projected cube: spectral energies E_t, E_x, E_y,
+ *   (4) directional centre-surround comparison of each E_m (Eq. 5): maps S_t, S_x, S_y,
+ *   (5) their weighted combination (Eq. 6) into the saliency map S, the size of V.
+ *
+ * Conventions shared by every call
+ *  - Volumes are float32, C order [t][x][y] (t = time/depth, x = crossline, y = inline,
+ *    y contiguous), T*X*Y voxels.  Per-map arrays are planar: [3][T*X*Y] for m = t, x, y.
+ *  - Every data pointer is a DEVICE pointer owned by the caller.  The library allocates
+ *    and frees nothing; scratch goes in the caller's workspace `ws` (size from the
+ *    matching *_workspace_size query).  Device pointers must be 16-byte aligned.
+ *  - Calls are asynchronous on the caller's CUDA stream `stream` (a cudaStream_t passed
+ *    as void*; NULL = the legacy default stream).  They return once work is enqueued.
+ *  - Arguments are checked on the host before anything is launched; a bad argument
+ *    returns SAL_ERR_INVALID_ARG (or SAL_ERR_UNSUPPORTED, SAL_ERR_WORKSPACE) and launches
+ *    nothing.  A CUDA launch error returns SAL_ERR_CUDA.  sal_last_error() gives a
+ *    thread-local message for the last failing call.  No C++ exception crosses the ABI.
+ *  - Readings of the paper that these calls implement:
+ *      centred signed frequency indices -h..h (h = (L-1)/2) in Eq. 1-4, so the DC point
+ *      is the cube centre; features use |F|; the energy is the mean over the L^3 - 1
+ *      non-DC points; one cube per voxel, centred on it, odd L; samples outside the
+ *      volume come from the boundary extension (REFLECT: whole-sample symmetric without
+ *      repeating the edge; PERIODIC: wrap); Eq. 5 is taken literally with Gaussian
+ *      weights g(o) = exp(-|o|^2 / (2 sigma^2)) on the neighbour; each S_m is min-max
+ *      normalised with its global min and max before Eq. 6, and a map whose range
+ *      hi - lo <= eps * max(|hi|, |lo|) becomes 0.
+ */
+#ifndef SAL_H
+#define SAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SAL_API __attribute__((visibility("default")))
+#else
+#define SAL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SAL_OK = 0,
+    SAL_ERR_INVALID_ARG = 1,  /* null pointer, bad size, misaligned pointer, bad enum */
+    SAL_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement (e.g. even L) */
+    SAL_ERR_WORKSPACE = 3,    /* workspace smaller than the size query returned */
+    SAL_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed; see sal_last_error() */
+    SAL_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+    SAL_ERR_INTERNAL = 6
+} sal_status;
+
+typedef enum { SAL_PREC_FP32 = 0, SAL_PREC_TF32 = 1, SAL_PREC_BF16 = 2 } sal_precision;
+typedef enum { SAL_BND_REFLECT = 0, SAL_BND_PERIODIC = 1 } sal_boundary;
+/* SAL_STENCIL_26: the 26 voxels around the centre (Q = 26).
+ * SAL_STENCIL_LINE: the paper's d x 1 window of side d = L along axis m for map m
+ * (offsets +-1..+-h, Q = L - 1), Sec. 2 text after Eq. 5. */
+typedef enum { SAL_STENCIL_26 = 0, SAL_STENCIL_LINE = 1 } sal_stencil;
+
+typedef struct { int64_t T, X, Y; } sal_dims;
+
+typedef struct {
+    int32_t L;          /* local cube side, odd, 3..15 (Sec. 2: "L defines the size of the local data cube") */
+    int32_t precision;  /* sal_precision of the DFT stage */
+    int32_t boundary;   /* sal_boundary */
+    int32_t stencil;    /* sal_stencil */
+    float sigma;        /* Gaussian width of the Eq. 5 weights, in voxels (> 0) */
+    int32_t reserved;   /* must be 0 */
+    double a, b, c;     /* Eq. 6 weights of S_t, S_x, S_y (equal in the paper) */
+    double eps;         /* relative range below which a map counts as constant */
+} sal_params;
+
+/* Number of doubles in a stats array: (min, max, sum) of S_t, S_x, S_y in that order. */
+#define SAL_STATS_LEN 9
+
+/* Fill *p with the defaults: L = 7, FP32, REFLECT, 26-neighbourhood, sigma = 1,
+ * a = b = c = 1/3 (the paper's equal weights, Sec. 2 after Eq. 6), eps = 1e-6. */
+SAL_API sal_status sal_params_default(sal_params *p);
+
+/* Workspace bytes needed by sal_saliency for this volume and these parameters. */
+SAL_API sal_status sal_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes);
+
+/* Workspace bytes needed by sal_directional_compare. */
+SAL_API sal_status sal_dcs_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes);
+
+/*
+ * Local magnitude spectra (Sec. 2 first step; the DFT printed below Eq. 2, normalised by
+ * L^-3) of the voxels of a region of interest: roi_lo[3] = first voxel (t, x, y),
+ * roi_ext[3] = extent; the region must lie inside the volume.  `mag` receives
+ * [roi voxels in C order][L][L][L] float32, frequency slots in centred order
+ * (slot s holds signed index s - h); the DC slot holds |mean of the cube|.
+ * Meant for inspection and tests (L^3 floats per voxel): keep the region small.
+ */
+SAL_API sal_status sal_local_spectra(const float *V, sal_dims dims, const sal_params *p,
+                             const int64_t roi_lo[3], const int64_t roi_ext[3],
+                             float *mag, void *stream);
+
+/*
+ * Spectral energies from magnitude spectra (Eq. 1-4 and the third step of Sec. 2):
+ * E_m[v] = (L^3 - 1)^-1 sum over non-DC points of w_m |F|.  `mag` is [n_vox][L][L][L] in the
+ * layout sal_local_spectra writes; `E` receives [3][n_vox].
+ */
+SAL_API sal_status sal_project(const float *mag, int64_t n_vox, int32_t L, float *E, void *stream);
+
+/*
+ * Fused steps 1-3 for a whole volume: E [3][T*X*Y] straight from V, no spectrum stored.
+ * p->precision selects the DFT arithmetic (FP32 CUDA cores, or TF32/BF16 tensor cores
+ * with FP32 accumulation).
+ */
+SAL_API sal_status sal_spectral_energy(const float *V, sal_dims dims, const sal_params *p, float *E,
+                               void *stream);
+
+/*
+ * Directional centre-surround comparison, Eq. 5, of each E_m: Sm [3][T*X*Y], plus the
+ * global (min, max, sum) of each S_m in `stats` (device, SAL_STATS_LEN doubles; the
+ * reductions are FP64).  `ws` must hold sal_dcs_workspace_size bytes.
+ */
+SAL_API sal_status sal_directional_compare(const float *E, sal_dims dims, const sal_params *p,
+                                   float *Sm, double *stats, void *ws, size_t ws_bytes,
+                                   void *stream);
+
+/*
+ * Weighted combination, Eq. 6, of the min-max normalised maps:
+ * S = a N_t + b N_x + c N_y with N_m = (S_m - min_m) / (max_m - min_m).  `stats` is the
+ * device array sal_directional_compare wrote.
+ */
+SAL_API sal_status sal_combine(const float *Sm, const double *stats, sal_dims dims, const sal_params *p,
+                       float *S, void *stream);
+
+/*
+ * The whole method of Fig. 1 on one volume: V -> S.  `stats` (device, SAL_STATS_LEN
+ * doubles) may be NULL; otherwise it receives the S_m statistics.  `ws` must hold
+ * sal_workspace_size bytes (it holds E, S_m and the reduction partials).
+ */
+SAL_API sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, float *S,
+                        double *stats, void *ws, size_t ws_bytes, void *stream);
+
+/* Static text for a status code. */
+SAL_API const char *sal_status_string(sal_status s);
+/* Thread-local detail of the last failing call on this thread ("" if none). */
+SAL_API const char *sal_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAL_H */

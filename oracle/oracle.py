@@ -61,6 +61,8 @@ def _load():
         lib.oracle_energy.restype = I_
         lib.oracle_energy_at.argtypes = [f32p, L_, L_, L_, I_, I_, i64p, L_, I_, f64p]
         lib.oracle_energy_at.restype = I_
+        lib.oracle_maps_at.argtypes = [f32p, L_, L_, L_, I_, I_, I_, D_, i64p, L_, I_, f64p, f64p]
+        lib.oracle_maps_at.restype = I_
         lib.oracle_dcs.argtypes = [f64p, L_, L_, L_, I_, I_, I_, D_, I_, f64p]
         lib.oracle_dcs.restype = I_
         lib.oracle_stats.argtypes = [f64p, L_, f64p]
@@ -141,6 +143,20 @@ def energy_at(V, coords, L, bnd=REFLECT, threads=None) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle_energy_at failed ({rc})")
     return out
+
+
+def maps_at(V, coords, L, bnd=REFLECT, stencil=STENCIL_26, sigma=1.0, threads=None):
+    """(E, S_m) at selected voxels ``coords`` [n][3]: two [3][n] float64 arrays."""
+    V, vp = _f32(V)
+    c = np.ascontiguousarray(np.asarray(coords, dtype=np.int64).reshape(-1, 3))
+    n = c.shape[0]
+    E, ep = _f64(np.zeros((3, n)))
+    S, sp = _f64(np.zeros((3, n)))
+    rc = _load().oracle_maps_at(vp, *V.shape, L, bnd, stencil, float(sigma),
+                                c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n, threads or default_threads(), ep, sp)
+    if rc:
+        raise ValueError(f"oracle_maps_at failed ({rc})")
+    return E, S
 
 
 def dcs(E, bnd=REFLECT, stencil=STENCIL_26, L=7, sigma=1.0, threads=None) -> np.ndarray:

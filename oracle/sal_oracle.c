@@ -430,3 +430,49 @@ int oracle_saliency(const float *V, long T, long X, long Y, int L, int bnd, int 
     if (!Sm_out) free(Sm);
     return rc;
 }
+
+/* E_m and S_m (Eq. 5) at selected voxels only: the energies of each voxel's neighbours are
+ * computed from their own cubes, so no full-volume sweep is needed.  For checks on
+ * volumes too large for the whole-volume oracle. */
+int oracle_maps_at(const float *V, long T, long X, long Y, int L, int bnd, int stencil, double sigma,
+                   const int64_t *coords /* [n][3] */, long n, int nthreads, double *E /* [3][n] */,
+                   double *Sm /* [3][n] */)
+{
+    if (L < 3 || (L % 2) == 0 || sigma <= 0.0) return -1;
+    int n3 = L * L * L, h = (L - 1) / 2, dc = (h * L + h) * L + h;
+    double *w = (double *)malloc(sizeof(double) * 3 * n3);
+    oracle_weights(L, w);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+    for (long k = 0; k < n; ++k) {
+        double *mag = (double *)malloc(sizeof(double) * n3);
+        long t = coords[3 * k], x = coords[3 * k + 1], y = coords[3 * k + 2];
+        for (int m = 0; m < 3; ++m) {
+            int off[64][3];
+            int Q = neighbourhood(stencil, m, L, off);
+            double e[65];
+            for (int q = 0; q <= Q; ++q) {
+                long tn = t, xn = x, yn = y;
+                if (q < Q) {
+                    tn = orc_ext_index(t + off[q][0], T, bnd);
+                    xn = orc_ext_index(x + off[q][1], X, bnd);
+                    yn = orc_ext_index(y + off[q][2], Y, bnd);
+                }
+                oracle_local_spectrum_separable(V, T, X, Y, L, bnd, tn, xn, yn, mag);
+                double s = 0.0;
+                for (int i = 0; i < n3; ++i)
+                    if (i != dc) s += w[m * n3 + i] * mag[i];
+                e[q] = s / (double)(n3 - 1);
+            }
+            double c = e[Q], s = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                double d2 = (double)(off[q][0] * off[q][0] + off[q][1] * off[q][1] + off[q][2] * off[q][2]);
+                s += fabs(c - exp(-d2 / (2.0 * sigma * sigma)) * e[q]);
+            }
+            E[m * n + k] = c;
+            Sm[m * n + k] = s / (double)Q;
+        }
+        free(mag);
+    }
+    free(w);
+    return 0;
+}

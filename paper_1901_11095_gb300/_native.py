@@ -1,0 +1,83 @@
+"""ctypes binding of libsal.so: the C ABI of include/sal.h, call for call.
+
+Argument marshalling only.  Tensors are torch CUDA tensors (device memory owned by the
+caller); every computation happens in the library's CUDA kernels.  There is no CPU
+fallback: if libsal.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsal.so")
+
+SAL_OK, SAL_ERR_INVALID_ARG, SAL_ERR_UNSUPPORTED, SAL_ERR_WORKSPACE, SAL_ERR_CUDA, SAL_ERR_TIMEOUT, \
+    SAL_ERR_INTERNAL = range(7)
+SAL_PREC_FP32, SAL_PREC_TF32, SAL_PREC_BF16 = 0, 1, 2
+SAL_BND_REFLECT, SAL_BND_PERIODIC = 0, 1
+SAL_STENCIL_26, SAL_STENCIL_LINE = 0, 1
+SAL_STATS_LEN = 9
+
+
+class SalDims(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("X", ctypes.c_int64), ("Y", ctypes.c_int64)]
+
+
+class SalParams(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("boundary", ctypes.c_int32),
+                ("stencil", ctypes.c_int32), ("sigma", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class SalError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} [status {status}]")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsal.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsal.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)
+        pp = ctypes.POINTER(SalParams)
+        sig = {
+            "sal_params_default": [pp],
+            "sal_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
+            "sal_dcs_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
+            "sal_local_spectra": [vp, SalDims, pp, i64p, i64p, vp, vp],
+            "sal_project": [vp, ctypes.c_int64, ctypes.c_int32, vp, vp],
+            "sal_spectral_energy": [vp, SalDims, pp, vp, vp],
+            "sal_directional_compare": [vp, SalDims, pp, vp, vp, vp, sz, vp],
+            "sal_combine": [vp, vp, SalDims, pp, vp, vp],
+            "sal_saliency": [vp, SalDims, pp, vp, vp, vp, sz, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sal_status_string.argtypes = [ctypes.c_int]
+        L.sal_status_string.restype = ctypes.c_char_p
+        L.sal_last_error.argtypes = []
+        L.sal_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != SAL_OK:
+        l = lib()
+        raise SalError(status, f"{l.sal_status_string(status).decode()}: {l.sal_last_error().decode()}")
+
+
+def exported_symbols() -> list[str]:
+    return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
+            "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_combine", "sal_saliency",
+            "sal_status_string", "sal_last_error"]

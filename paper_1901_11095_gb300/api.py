@@ -1,0 +1,144 @@
+"""Python face of the C ABI: one function per entry point of include/sal.h, same names.
+
+Marshalling only: torch CUDA tensors provide device memory and the current stream; the
+library's kernels do all the computing.  Outputs and workspaces that the caller does not
+pass are allocated with torch (the library itself never allocates).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+from ._native import SalDims, SalParams, check
+
+_PREC = {"fp32": N.SAL_PREC_FP32, "tf32": N.SAL_PREC_TF32, "bf16": N.SAL_PREC_BF16}
+_BND = {"reflect": N.SAL_BND_REFLECT, "periodic": N.SAL_BND_PERIODIC}
+_STENCIL = {"26": N.SAL_STENCIL_26, "line": N.SAL_STENCIL_LINE}
+
+
+def sal_params_default() -> SalParams:
+    p = SalParams()
+    check(N.lib().sal_params_default(ctypes.byref(p)))
+    return p
+
+
+def params(L: int = 7, precision="fp32", boundary="reflect", stencil="26", sigma: float = 1.0,
+           a: float = 1 / 3, b: float = 1 / 3, c: float = 1 / 3, eps: float = 1e-6) -> SalParams:
+    """A sal_params struct from readable values (names or the enum integers)."""
+    p = sal_params_default()
+    p.L = int(L)
+    p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    p.boundary = _BND[boundary] if isinstance(boundary, str) else int(boundary)
+    p.stencil = _STENCIL[str(stencil)] if isinstance(stencil, str) else int(stencil)
+    p.sigma, p.a, p.b, p.c, p.eps = float(sigma), float(a), float(b), float(c), float(eps)
+    return p
+
+
+def dims_of(V: torch.Tensor) -> SalDims:
+    if V.dim() != 3:
+        raise ValueError("volume must be 3-D [T, X, Y]")
+    return SalDims(*[int(s) for s in V.shape])
+
+
+def _dev(t: torch.Tensor, dtype=torch.float32, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def sal_workspace_size(dims: SalDims, p: SalParams) -> int:
+    n = ctypes.c_size_t()
+    check(N.lib().sal_workspace_size(dims, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_dcs_workspace_size(dims: SalDims, p: SalParams) -> int:
+    n = ctypes.c_size_t()
+    check(N.lib().sal_dcs_workspace_size(dims, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_local_spectra(V: torch.Tensor, p: SalParams, roi_lo, roi_ext, mag: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """|F| of every voxel of a region: [ext_t, ext_x, ext_y, L, L, L], centred slots."""
+    L = p.L
+    if mag is None:
+        mag = torch.empty(tuple(int(e) for e in roi_ext) + (L, L, L), device=V.device, dtype=torch.float32)
+    lo = (ctypes.c_int64 * 3)(*[int(v) for v in roi_lo])
+    ex = (ctypes.c_int64 * 3)(*[int(v) for v in roi_ext])
+    check(N.lib().sal_local_spectra(_dev(V, name="V"), dims_of(V), ctypes.byref(p), lo, ex,
+                                    _dev(mag, name="mag"), _stream(stream)))
+    return mag
+
+
+def sal_project(mag: torch.Tensor, L: int, E: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Spectral energies [3, n] from spectra [..., L, L, L]."""
+    n = mag.numel() // (L ** 3)
+    if E is None:
+        E = torch.empty((3, n), device=mag.device, dtype=torch.float32)
+    check(N.lib().sal_project(_dev(mag, name="mag"), n, int(L), _dev(E, name="E"), _stream(stream)))
+    return E
+
+
+def sal_spectral_energy(V: torch.Tensor, p: SalParams, E: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """E_t, E_x, E_y of every voxel: [3, T, X, Y]."""
+    if E is None:
+        E = torch.empty((3,) + tuple(V.shape), device=V.device, dtype=torch.float32)
+    check(N.lib().sal_spectral_energy(_dev(V, name="V"), dims_of(V), ctypes.byref(p), _dev(E, name="E"),
+                                      _stream(stream)))
+    return E
+
+
+def sal_directional_compare(E: torch.Tensor, p: SalParams, Sm: torch.Tensor | None = None,
+                            stats: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """S_t, S_x, S_y [3, T, X, Y] and their FP64 (min, max, sum) [9]."""
+    dims = SalDims(*[int(s) for s in E.shape[1:]])
+    if Sm is None:
+        Sm = torch.empty_like(E)
+    if stats is None:
+        stats = torch.empty(N.SAL_STATS_LEN, device=E.device, dtype=torch.float64)
+    need = sal_dcs_workspace_size(dims, p)
+    if ws is None:
+        ws = torch.empty(need, device=E.device, dtype=torch.uint8)
+    check(N.lib().sal_directional_compare(_dev(E, name="E"), dims, ctypes.byref(p), _dev(Sm, name="Sm"),
+                                          _dev(stats, torch.float64, "stats"), _dev(ws, torch.uint8, "ws"),
+                                          ws.numel(), _stream(stream)))
+    return Sm, stats
+
+
+def sal_combine(Sm: torch.Tensor, stats: torch.Tensor, p: SalParams, S: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Eq. 6 on the min-max normalised maps: S [T, X, Y]."""
+    dims = SalDims(*[int(s) for s in Sm.shape[1:]])
+    if S is None:
+        S = torch.empty(Sm.shape[1:], device=Sm.device, dtype=torch.float32)
+    check(N.lib().sal_combine(_dev(Sm, name="Sm"), _dev(stats, torch.float64, "stats"), dims, ctypes.byref(p),
+                              _dev(S, name="S"), _stream(stream)))
+    return S
+
+
+def sal_saliency(V: torch.Tensor, p: SalParams, S: torch.Tensor | None = None, stats: torch.Tensor | None = None,
+                 ws: torch.Tensor | None = None, stream=None):
+    """The whole method, V -> S.  Returns (S, stats or None)."""
+    dims = dims_of(V)
+    if S is None:
+        S = torch.empty_like(V)
+    need = sal_workspace_size(dims, p)
+    if ws is None:
+        ws = torch.empty(need, device=V.device, dtype=torch.uint8)
+    sp = _dev(stats, torch.float64, "stats") if stats is not None else None
+    check(N.lib().sal_saliency(_dev(V, name="V"), dims, ctypes.byref(p), _dev(S, name="S"), sp,
+                               _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
+    return S, stats

@@ -1,0 +1,273 @@
+// C ABI of libsal.so: argument checks, workspace layout and launches (declared in sal.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "sal_internal.cuh"
+
+namespace sal {
+
+void make_tables(int L, SpecTables *t)
+{
+    memset(t, 0, sizeof(*t));
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int n = 0; n < L && n < 16; ++n) {
+        t->cs[n] = (float)cos(2.0 * pi * n / L);
+        t->sn[n] = (float)sin(2.0 * pi * n / L);
+    }
+    // Eq. 1-4 with centred indices: w_t = |(nu, om)| / rho, w_x = |(mu, om)| / rho, w_y = |(mu, nu)| / rho
+    const int h = (L - 1) / 2;
+    for (int mu = 0; mu <= h; ++mu)
+        for (int nu = 0; nu <= h; ++nu)
+            for (int om = 0; om <= h; ++om) {
+                float *w = &t->w[((mu * kMaxHalf + nu) * kMaxHalf + om) * 3];
+                const double rho = sqrt((double)(mu * mu + nu * nu + om * om));
+                if (rho == 0.0) {
+                    w[0] = w[1] = w[2] = 0.f;
+                } else {
+                    w[0] = (float)(sqrt((double)(nu * nu + om * om)) / rho);
+                    w[1] = (float)(sqrt((double)(mu * mu + om * om)) / rho);
+                    w[2] = (float)(sqrt((double)(mu * mu + nu * nu)) / rho);
+                }
+            }
+    const double n3 = (double)L * L * L;
+    t->escale = (float)(2.0 / ((n3 - 1.0) * n3));
+}
+
+}  // namespace sal
+
+namespace {
+
+thread_local char g_err[512];
+
+sal_status fail(sal_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+sal_status ok()
+{
+    g_err[0] = 0;
+    return SAL_OK;
+}
+
+sal_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SAL_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+sal_status check_dims(sal_dims d)
+{
+    if (d.T < 1 || d.X < 1 || d.Y < 1) return fail(SAL_ERR_INVALID_ARG, "dims must be >= 1 (got %lld x %lld x %lld)",
+                                                   (long long)d.T, (long long)d.X, (long long)d.Y);
+    const double n = (double)d.T * (double)d.X * (double)d.Y;
+    if (n > 4.0e12) return fail(SAL_ERR_INVALID_ARG, "volume too large");
+    return SAL_OK;
+}
+
+sal_status check_L(int L)
+{
+    if (L < 3 || L > sal::kMaxL) return fail(SAL_ERR_INVALID_ARG, "L must be in [3, %d] (got %d)", sal::kMaxL, L);
+    if ((L & 1) == 0) return fail(SAL_ERR_UNSUPPORTED, "even L has no centre voxel (got %d)", L);
+    return SAL_OK;
+}
+
+sal_status check_params(const sal_params *p)
+{
+    if (!p) return fail(SAL_ERR_INVALID_ARG, "params is NULL");
+    sal_status s = check_L(p->L);
+    if (s) return s;
+    if (p->precision < SAL_PREC_FP32 || p->precision > SAL_PREC_BF16)
+        return fail(SAL_ERR_INVALID_ARG, "bad precision %d", p->precision);
+    if (p->boundary != SAL_BND_REFLECT && p->boundary != SAL_BND_PERIODIC)
+        return fail(SAL_ERR_INVALID_ARG, "bad boundary %d", p->boundary);
+    if (p->stencil != SAL_STENCIL_26 && p->stencil != SAL_STENCIL_LINE)
+        return fail(SAL_ERR_INVALID_ARG, "bad stencil %d", p->stencil);
+    if (!(p->sigma > 0.f) || !isfinite(p->sigma)) return fail(SAL_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    if (p->reserved != 0) return fail(SAL_ERR_INVALID_ARG, "reserved must be 0");
+    if (!isfinite(p->a) || !isfinite(p->b) || !isfinite(p->c)) return fail(SAL_ERR_INVALID_ARG, "a, b, c must be finite");
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return fail(SAL_ERR_INVALID_ARG, "eps must be finite and >= 0");
+    return SAL_OK;
+}
+
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct WsLayout {
+    size_t E, Sm, partials, stats, total;
+};
+
+WsLayout saliency_layout(sal_dims d)
+{
+    const size_t N = (size_t)(d.T * d.X * d.Y);
+    WsLayout w;
+    w.E = 0;
+    w.Sm = round256(w.E + 3 * N * sizeof(float));
+    w.partials = round256(w.Sm + 3 * N * sizeof(float));
+    w.stats = round256(w.partials + 9 * (size_t)sal::dcs_num_partials(d) * sizeof(double));
+    w.total = round256(w.stats + SAL_STATS_LEN * sizeof(double));
+    return w;
+}
+
+size_t dcs_ws_bytes(sal_dims d) { return round256(9 * (size_t)sal::dcs_num_partials(d) * sizeof(double)); }
+
+sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, float *E, cudaStream_t s)
+{
+    if (p->precision != SAL_PREC_FP32)
+        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available in this build", p->precision);
+    cudaError_t e = sal::launch_energy_fp32(V, d, p->L, p->boundary, E, s);
+    return e == cudaSuccess ? SAL_OK : cuda_fail(e, "spectral energy launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+sal_status sal_params_default(sal_params *p)
+{
+    if (!p) return fail(SAL_ERR_INVALID_ARG, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    p->L = 7;
+    p->precision = SAL_PREC_FP32;
+    p->boundary = SAL_BND_REFLECT;
+    p->stencil = SAL_STENCIL_26;
+    p->sigma = 1.0f;
+    p->a = p->b = p->c = 1.0 / 3.0;
+    p->eps = 1e-6;
+    return ok();
+}
+
+sal_status sal_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = saliency_layout(dims).total;
+    return ok();
+}
+
+sal_status sal_dcs_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = dcs_ws_bytes(dims);
+    return ok();
+}
+
+sal_status sal_local_spectra(const float *V, sal_dims dims, const sal_params *p, const int64_t roi_lo[3],
+                             const int64_t roi_ext[3], float *mag, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !mag || !roi_lo || !roi_ext) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(mag)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const int64_t D[3] = {dims.T, dims.X, dims.Y};
+    for (int i = 0; i < 3; ++i)
+        if (roi_lo[i] < 0 || roi_ext[i] < 0 || roi_lo[i] + roi_ext[i] > D[i])
+            return fail(SAL_ERR_INVALID_ARG, "region of interest leaves the volume on axis %d", i);
+    cudaError_t e = sal::launch_local_spectra(V, dims, p->L, p->boundary, roi_lo, roi_ext, mag, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_local_spectra");
+}
+
+sal_status sal_project(const float *mag, int64_t n_vox, int32_t L, float *E, void *stream)
+{
+    sal_status s = check_L(L);
+    if (s) return s;
+    if (n_vox < 0) return fail(SAL_ERR_INVALID_ARG, "n_vox < 0");
+    if (n_vox > 0 && (!mag || !E)) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(mag) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    cudaError_t e = sal::launch_project(mag, n_vox, L, E, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_project");
+}
+
+sal_status sal_spectral_energy(const float *V, sal_dims dims, const sal_params *p, float *E, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !E) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    s = energy_dispatch(V, dims, p, E, (cudaStream_t)stream);
+    return s ? s : ok();
+}
+
+sal_status sal_directional_compare(const float *E, sal_dims dims, const sal_params *p, float *Sm, double *stats,
+                                   void *ws, size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!E || !Sm || !stats || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(E) || !aligned16(Sm) || !aligned16(stats) || !aligned16(ws))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const size_t need = dcs_ws_bytes(dims);
+    if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = sal::launch_dcs(E, dims, p, Sm, (double *)ws, stats, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_directional_compare");
+}
+
+sal_status sal_combine(const float *Sm, const double *stats, sal_dims dims, const sal_params *p, float *S, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!Sm || !stats || !S) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(Sm) || !aligned16(stats) || !aligned16(S))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    cudaError_t e = sal::launch_combine(Sm, stats, dims, p, S, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_combine");
+}
+
+sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, float *S, double *stats, void *ws,
+                        size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !S || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(S) || !aligned16(ws) || (stats && !aligned16(stats)))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const WsLayout w = saliency_layout(dims);
+    if (ws_bytes < w.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+    char *base = (char *)ws;
+    float *E = (float *)(base + w.E);
+    float *Sm = (float *)(base + w.Sm);
+    double *part = (double *)(base + w.partials);
+    double *st = stats ? stats : (double *)(base + w.stats);
+    cudaStream_t cs = (cudaStream_t)stream;
+    s = energy_dispatch(V, dims, p, E, cs);
+    if (s) return s;
+    cudaError_t e = sal::launch_dcs(E, dims, p, Sm, part, st, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");
+    e = sal::launch_combine(Sm, st, dims, p, S, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+    return ok();
+}
+
+const char *sal_status_string(sal_status s)
+{
+    switch (s) {
+        case SAL_OK: return "SAL_OK";
+        case SAL_ERR_INVALID_ARG: return "SAL_ERR_INVALID_ARG";
+        case SAL_ERR_UNSUPPORTED: return "SAL_ERR_UNSUPPORTED";
+        case SAL_ERR_WORKSPACE: return "SAL_ERR_WORKSPACE";
+        case SAL_ERR_CUDA: return "SAL_ERR_CUDA";
+        case SAL_ERR_TIMEOUT: return "SAL_ERR_TIMEOUT";
+        case SAL_ERR_INTERNAL: return "SAL_ERR_INTERNAL";
+    }
+    return "SAL_ERR_UNKNOWN";
+}
+
+const char *sal_last_error(void) { return g_err; }
+
+}  // extern "C"

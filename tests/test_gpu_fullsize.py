@@ -1,0 +1,68 @@
+"""Parity at full size: the F3-shaped 462 x 951 x 651 volume (L = 7), in the launch
+configuration the benchmark times, checked on sampled voxels the oracle computes one by
+one (E_m and S_m from each voxel's own cubes) and through properties that hold at any
+size (global statistics bracket every sample, S in [0, 1])."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1901_11095_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (462, 951, 651)
+TOL_MAP = 2e-5
+
+
+@pytest.fixture(scope="module")
+def f3_run():
+    V = synth.make_volume(SHAPE, seed=1, kind="f3")
+    dev = torch.device("cuda:0")
+    Vd = torch.from_numpy(V).to(dev)
+    p = api.params(L=7)
+    E = api.sal_spectral_energy(Vd, p)
+    Sm, stats = api.sal_directional_compare(E, p)
+    S = api.sal_combine(Sm, stats, p)
+    S2, _ = api.sal_saliency(Vd, p, stats=torch.empty(9, dtype=torch.float64, device=dev))
+    torch.cuda.synchronize()
+    return V, E, Sm, stats, S, S2
+
+
+def _coords(n=1200, seed=0):
+    rng = np.random.default_rng(seed)
+    T, X, Y = SHAPE
+    pts = [tuple(int(v) for v in (rng.integers(0, T), rng.integers(0, X), rng.integers(0, Y))) for _ in range(n)]
+    for t in (0, 1, 2, T - 3, T - 2, T - 1):                  # faces, edges and corners
+        for x in (0, 3, X // 2, X - 1):
+            for y in (0, 2, Y // 2, Y - 4, Y - 1):
+                pts.append((t, x, y))
+    return np.array(pts, dtype=np.int64)
+
+
+def test_sampled_maps_match_oracle(f3_run):
+    V, E, Sm, stats, S, S2 = f3_run
+    c = _coords()
+    E_ref, Sm_ref = O.maps_at(V, c, 7)
+    idx = torch.from_numpy(c).to(E.device)
+    for m in range(3):
+        e = E[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+        s = Sm[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+        assert np.abs(e - E_ref[m]).max() / np.abs(E_ref[m]).max() < TOL_MAP
+        assert np.abs(s - Sm_ref[m]).max() / np.abs(Sm_ref[m]).max() < TOL_MAP
+    st = stats.cpu().numpy().reshape(3, 3)
+    for m in range(3):
+        assert st[m, 0] <= Sm_ref[m].min() * (1 + TOL_MAP) and st[m, 1] >= Sm_ref[m].max() * (1 - TOL_MAP)
+        n = np.prod(SHAPE)
+        assert st[m, 0] * n <= st[m, 2] <= st[m, 1] * n
+
+
+def test_saliency_properties(f3_run):
+    V, E, Sm, stats, S, S2 = f3_run
+    assert torch.equal(S, S2)                     # fused call == the split calls the benchmark times
+    assert float(S.min()) >= 0.0 and float(S.max()) <= 1.0 + 1e-6
+    assert bool(torch.isfinite(S).all()) and bool(torch.isfinite(E).all())
+    # the voxel holding each map's maximum normalises to 1 in that map
+    st = stats.cpu().numpy().reshape(3, 3)
+    for m in range(3):
+        assert float(Sm[m].max()) == st[m, 1] and float(Sm[m].min()) == st[m, 0]

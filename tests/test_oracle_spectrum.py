@@ -139,3 +139,15 @@ def test_brute_energy_equals_separable_energy():
     a = O.energy(V, 3, brute=True)
     b = O.energy(V, 3, brute=False)
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("stencil,L,bnd", [(O.STENCIL_26, 5, O.REFLECT), (O.STENCIL_LINE, 7, O.PERIODIC),
+                                          (O.STENCIL_26, 3, O.PERIODIC)])
+def test_maps_at_agrees_with_whole_volume(stencil, L, bnd):
+    V = synth.make_volume((9, 11, 10), seed=6)
+    S, E, Sm, _ = O.saliency(V, L=L, bnd=bnd, stencil=stencil, sigma=1.4, full=True)
+    coords = [(0, 0, 0), (8, 10, 9), (4, 5, 5), (0, 10, 3), (8, 0, 9)]
+    Ea, Sa = O.maps_at(V, coords, L, bnd=bnd, stencil=stencil, sigma=1.4)
+    for i, c in enumerate(coords):
+        np.testing.assert_allclose(Ea[:, i], E[(slice(None),) + c], rtol=1e-13)
+        np.testing.assert_allclose(Sa[:, i], Sm[(slice(None),) + c], rtol=1e-12, atol=1e-16)
