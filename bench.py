@@ -34,6 +34,7 @@ WORKLOADS = {
     "f3": ((462, 951, 651), "f3", 1),
     "cube64": ((64, 64, 64), "basic", 0),
     "cube256": ((256, 256, 256), "basic", 2),
+    "slab": ((462, 951, 160), "f3", 1),     # a profiling case: the F3 shape cut to 160 inlines
 }
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128

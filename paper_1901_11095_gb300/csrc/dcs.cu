@@ -17,17 +17,41 @@ namespace sal {
 
 namespace {
 
-constexpr int DT = 4, DX = 8, DY = 32, DR = 4;          // output tile and outputs per thread
-constexpr int DNT = DT * DX * (DY / DR);                // 256 threads
-constexpr int DSMEM = (DT + 2 * kMaxH) * DX * DY;       // largest halo tile (LINE along t, h = 7)
+// Output tile of one CTA (one map per CTA: blockIdx.y = m).  Every thread owns a 4 x 4
+// block (4 planes along t, 4 columns along y) at one x.
+constexpr int DT = 8, DX = 8, DY = 64, QT = 4, QY = 4;
+constexpr int DNT = (DT / QT) * DX * (DY / QY);         // 256 threads
 constexpr int kRedBlocks = 160;                         // first pass of the partial reduction
 
 struct DcsConsts {
-    float g[3];            // 26-neighbourhood weights for |o|^2 = 1, 2, 3
-    float gl[kMaxH + 1];   // line weights for offset k = 1..h
+    float g[4];            // 26-neighbourhood weights for |o|^2 = 0 (unused), 1, 2, 3
+    float gl[kMaxH + 1];   // line weights for offset k = 0..h
     float invQ;
-    int stencil, h;
+    int h;
 };
+
+// Halo geometry of one map: radii along t, x, y and the shared-memory pitches.  Column c
+// of the halo row (c = 0 is y0 - ry) is stored at c + off, with off chosen so that the
+// tile's first output column y0 lands on a 16-byte boundary.
+struct Halo {
+    int rt, rx, ry, PX, PP, off, pitch, planes;
+    __host__ __device__ constexpr Halo(int rt_, int rx_, int ry_)
+        : rt(rt_), rx(rx_), ry(ry_), PX(0), PP(0), off(0), pitch(0), planes(0)
+    {
+        PX = DX + 2 * rx_;
+        off = ((ry_ + 3) & ~3) - ry_;
+        pitch = (off + DY + 2 * ry_ + 3) & ~3;
+        PP = PX * pitch;
+        planes = DT + 2 * rt_;
+    }
+    __host__ __device__ constexpr int floats() const { return planes * PP; }
+};
+
+__host__ __device__ inline Halo halo_for(int stencil, int m, int h)
+{
+    if (stencil == SAL_STENCIL_26) return Halo(1, 1, 1);
+    return Halo(m == 0 ? h : 0, m == 1 ? h : 0, m == 2 ? h : 0);
+}
 
 __device__ __forceinline__ float warp_min(float v)
 {
@@ -48,128 +72,202 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Stages the halo tile of E_m in shared memory with asynchronous 4-byte copies: each warp
+// takes whole rows (t, x) of the tile, its lanes consecutive columns, so every warp-wide
+// copy reads one contiguous run of E.  Rows and columns outside the volume are mapped by
+// the boundary extension (once per row for t and x, per column only at the y faces).
+__device__ __forceinline__ void stage_tile(const float *__restrict__ Em, float *sE, const Halo &hl, int64_t T, int64_t X,
+                                           int64_t Y, int bnd, int64_t t0, int64_t x0, int64_t y0)
+{
+    const int rows = hl.planes * hl.PX, W = DY + 2 * hl.ry;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < rows; r += DNT / 32) {
+        const int a = r / hl.PX, b = r - a * hl.PX;
+        const int64_t gt = ext_index(t0 - hl.rt + a, T, bnd);
+        const int64_t gx = ext_index(x0 - hl.rx + b, X, bnd);
+        const float *src = Em + (gt * X + gx) * Y;
+        float *dst = sE + a * hl.PP + b * hl.pitch + hl.off;
+        for (int c = lane; c < W; c += 32) {
+            int64_t gy = y0 - hl.ry + c;
+            if (gy < 0 || gy >= Y) gy = ext_index(gy, Y, bnd);
+            cp_async4(dst + c, src + gy);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// The same staging for the 26-neighbourhood, with its geometry fixed at compile time
+// (10 planes x 10 rows x 66 columns, pitch 72, column c stored at c + 3).
+__device__ __forceinline__ void stage_tile26(const float *__restrict__ Em, float *sE, int64_t T, int64_t X, int64_t Y,
+                                             int bnd, int64_t t0, int64_t x0, int64_t y0)
+{
+    constexpr int PX = DX + 2, PITCH = 72, OFF = 3, W = DY + 2, ROWS = (DT + 2) * PX;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool y_inside = y0 >= 1 && y0 + DY + 1 <= Y;
+#pragma unroll 2
+    for (int r = warp; r < ROWS; r += DNT / 32) {
+        const int a = r / PX, b = r - a * PX;
+        const int64_t gt = ext_index(t0 - 1 + a, T, bnd);
+        const int64_t gx = ext_index(x0 - 1 + b, X, bnd);
+        const float *rowp = Em + (gt * X + gx) * Y;
+        float *dst = sE + r * PITCH + OFF;
+        if (y_inside) {
+            const float *src = rowp + (y0 - 1);
+#pragma unroll
+            for (int c = lane; c < W; c += 32) cp_async4(dst + c, src + c);
+        } else {
+#pragma unroll
+            for (int c = lane; c < W; c += 32) cp_async4(dst + c, rowp + ext_index(y0 - 1 + c, Y, bnd));
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// 26-neighbourhood: out[to][yo] = sum_o |c - g(o) n| for this thread's 4 x 4 block.
+__device__ __forceinline__ void dcs26(const float *sE, const Halo &hl, int tq, int x, int yq, const DcsConsts &k,
+                                      float (&out)[QT][QY])
+{
+    // halo indices: plane 4tq + p, row x + b, column 4yq + c (c = 0..5) at storage + off
+    const float *base = sE + (QT * tq) * hl.PP + x * hl.pitch + hl.off + QY * yq;
+    float cen[QT][QY];
+#pragma unroll
+    for (int to = 0; to < QT; ++to) {
+        const float *row = base + (to + 1) * hl.PP + hl.pitch + 1;
+#pragma unroll
+        for (int yo = 0; yo < QY; ++yo) {
+            cen[to][yo] = row[yo];
+            out[to][yo] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < QT + 2; ++p)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float *row = base + p * hl.PP + b * hl.pitch;
+            float w[QY + 2];
+            w[0] = row[0];
+            const float4 mid = *reinterpret_cast<const float4 *>(row + 1);
+            w[1] = mid.x; w[2] = mid.y; w[3] = mid.z; w[4] = mid.w;
+            w[5] = row[5];
+#pragma unroll
+            for (int to = 0; to < QT; ++to) {
+                const int dt = p - (to + 1);
+                if (dt < -1 || dt > 1) continue;
+#pragma unroll
+                for (int yo = 0; yo < QY; ++yo)
+#pragma unroll
+                    for (int cc = -1; cc <= 1; ++cc) {
+                        const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
+                        if (d2 == 0) continue;
+                        out[to][yo] += fabsf(fmaf(-k.g[d2], w[yo + 1 + cc], cen[to][yo]));
+                    }
+            }
+        }
+}
+
+// d x 1 line along axis m: out = sum_{q=1..h} |c - g(q) n(+q)| + |c - g(q) n(-q)|.
+__device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m, int tq, int x, int yq,
+                                         const DcsConsts &k, float (&out)[QT][QY])
+{
+    const int stride = m == 0 ? hl.PP : (m == 1 ? hl.pitch : 1);
+    const float *base = sE + (QT * tq + hl.rt) * hl.PP + (x + hl.rx) * hl.pitch + hl.off + hl.ry + QY * yq;
+#pragma unroll
+    for (int to = 0; to < QT; ++to)
+#pragma unroll
+        for (int yo = 0; yo < QY; ++yo) {
+            const float *c = base + to * hl.PP + yo;
+            const float cv = *c;
+            float s = 0.f;
+            for (int q = 1; q <= k.h; ++q) {
+                s += fabsf(fmaf(-k.gl[q], c[q * stride], cv));
+                s += fabsf(fmaf(-k.gl[q], c[-q * stride], cv));
+            }
+            out[to][yo] = s;
+        }
+}
+
+template <int STENCIL>
 __global__ void __launch_bounds__(DNT) dcs_kernel(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y,
                                                   int bnd, int tiles_x, int tiles_y, float *__restrict__ Sm,
                                                   double *__restrict__ partials, int64_t nparts,
                                                   const __grid_constant__ DcsConsts k)
 {
-    __shared__ __align__(16) float sE[DSMEM];
-    __shared__ double red[DNT / 32][9];
+    extern __shared__ __align__(16) float sE[];
+    __shared__ double red[DNT / 32][3];
+    const int m = blockIdx.y;
     const int64_t tile = blockIdx.x;
     const int ty = (int)(tile % tiles_y);
     const int tx = (int)((tile / tiles_y) % tiles_x);
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
     const int64_t t0 = tt * DT, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
     const int64_t N = T * X * Y;
+    const Halo hl = halo_for(STENCIL, m, k.h);
 
-    const int j = threadIdx.x % (DY / DR), row = threadIdx.x / (DY / DR);
-    const int t = row / DX, x = row - t * DX;
-    const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + DR * j;
-    const bool row_ok = gt < T && gx < X;
+    if (STENCIL == SAL_STENCIL_26)
+        stage_tile26(E + m * N, sE, T, X, Y, bnd, t0, x0, y0);
+    else
+        stage_tile(E + m * N, sE, hl, T, X, Y, bnd, t0, x0, y0);
+    __syncthreads();
 
-    float st_min[3], st_max[3], st_sum[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const int rt = k.stencil == SAL_STENCIL_26 ? 1 : (m == 0 ? k.h : 0);
-        const int rx = k.stencil == SAL_STENCIL_26 ? 1 : (m == 1 ? k.h : 0);
-        const int ry = k.stencil == SAL_STENCIL_26 ? 1 : (m == 2 ? k.h : 0);
-        const int PX = DX + 2 * rx, PYr = DY + 2 * ry, n = (DT + 2 * rt) * PX * PYr;
-        const float *Em = E + m * N;
-        for (int i = threadIdx.x; i < n; i += DNT) {
-            const int r = i / PYr, yy = i - r * PYr;
-            const int a = r / PX, xx = r - a * PX;
-            const int64_t et = ext_index(t0 - rt + a, T, bnd);
-            const int64_t ex = ext_index(x0 - rx + xx, X, bnd);
-            const int64_t ey = ext_index(y0 - ry + yy, Y, bnd);
-            sE[i] = __ldg(Em + (et * X + ex) * Y + ey);
-        }
-        __syncthreads();
+    const int yq = threadIdx.x % (DY / QY);
+    const int x = (threadIdx.x / (DY / QY)) % DX;
+    const int tq = threadIdx.x / ((DY / QY) * DX);
+    float out[QT][QY];
+    if (STENCIL == SAL_STENCIL_26)
+        dcs26(sE, hl, tq, x, yq, k, out);
+    else
+        dcs_line(sE, hl, m, tq, x, yq, k, out);
 
-        float out[DR];
-        if (k.stencil == SAL_STENCIL_26) {
-            // window rows (t + a, x + b), columns y0-1 .. y0+4 of this thread
-            const float *base = sE + ((t + 1) * PX + (x + 1)) * PYr + (DR * j + 1);
-            float c[DR];
+    float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
+    const int64_t gx = x0 + x, gy = y0 + QY * yq;
+    if (gx < X) {
 #pragma unroll
-            for (int r = 0; r < DR; ++r) { c[r] = base[r]; out[r] = 0.f; }
-#pragma unroll
-            for (int a = -1; a <= 1; ++a)
-#pragma unroll
-                for (int b = -1; b <= 1; ++b) {
-                    const float2 *p = reinterpret_cast<const float2 *>(base + (a * PX + b) * PYr - 1);
-                    float w[DR + 2];
-#pragma unroll
-                    for (int q = 0; q < (DR + 2) / 2; ++q) {
-                        const float2 v = p[q];
-                        w[2 * q] = v.x;
-                        w[2 * q + 1] = v.y;
-                    }
-#pragma unroll
-                    for (int r = 0; r < DR; ++r)
-#pragma unroll
-                        for (int cc = -1; cc <= 1; ++cc) {
-                            const int d2 = a * a + b * b + cc * cc;
-                            if (d2 == 0) continue;
-                            out[r] += fabsf(fmaf(-k.g[d2 - 1], w[r + 1 + cc], c[r]));
-                        }
-                }
-        } else {
-            const int stride = m == 0 ? PX * PYr : (m == 1 ? PYr : 1);
-            const float *base = sE + ((t + rt) * PX + (x + rx)) * PYr + (DR * j + ry);
-#pragma unroll
-            for (int r = 0; r < DR; ++r) {
-                const float c = base[r];
-                float s = 0.f;
-                for (int q = 1; q <= k.h; ++q) {
-                    s += fabsf(fmaf(-k.gl[q], base[r + q * stride], c));
-                    s += fabsf(fmaf(-k.gl[q], base[r - q * stride], c));
-                }
-                out[r] = s;
-            }
-        }
-
-        float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
-        if (row_ok) {
+        for (int to = 0; to < QT; ++to) {
+            const int64_t gt = t0 + QT * tq + to;
+            if (gt >= T) break;
             float *o = Sm + m * N + (gt * X + gx) * Y + gy;
 #pragma unroll
-            for (int r = 0; r < DR; ++r) {
-                out[r] *= k.invQ;
-                if (gy + r < Y) {
-                    mn = fminf(mn, out[r]);
-                    mx = fmaxf(mx, out[r]);
-                    sm += out[r];
+            for (int yo = 0; yo < QY; ++yo) {
+                out[to][yo] *= k.invQ;
+                if (gy + yo < Y) {
+                    mn = fminf(mn, out[to][yo]);
+                    mx = fmaxf(mx, out[to][yo]);
+                    sm += out[to][yo];
                 }
             }
-            if (gy + DR <= Y && (Y & 3) == 0) {
-                *reinterpret_cast<float4 *>(o) = make_float4(out[0], out[1], out[2], out[3]);
+            if (gy + QY <= Y && (Y & 3) == 0) {
+                *reinterpret_cast<float4 *>(o) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
             } else {
 #pragma unroll
-                for (int r = 0; r < DR; ++r)
-                    if (gy + r < Y) o[r] = out[r];
+                for (int yo = 0; yo < QY; ++yo)
+                    if (gy + yo < Y) o[yo] = out[to][yo];
             }
         }
-        st_min[m] = warp_min(mn);
-        st_max[m] = warp_max(mx);
-        st_sum[m] = warp_sum(sm);
-        __syncthreads();   // sE is reloaded for the next map
     }
-
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    sm = warp_sum(sm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-        for (int m = 0; m < 3; ++m) {
-            red[warp][3 * m] = st_min[m];
-            red[warp][3 * m + 1] = st_max[m];
-            red[warp][3 * m + 2] = st_sum[m];
-        }
+    if (lane == 0) {
+        red[warp][0] = mn;
+        red[warp][1] = mx;
+        red[warp][2] = sm;
+    }
     __syncthreads();
-    if (threadIdx.x < 9) {
-        const int q = threadIdx.x, kind = q % 3;
+    if (threadIdx.x < 3) {
+        const int q = threadIdx.x;
         double v = red[0][q];
         for (int w = 1; w < DNT / 32; ++w) {
             const double u = red[w][q];
-            v = kind == 0 ? fmin(v, u) : (kind == 1 ? fmax(v, u) : v + u);
+            v = q == 0 ? fmin(v, u) : (q == 1 ? fmax(v, u) : v + u);
         }
-        partials[q * nparts + blockIdx.x] = v;
+        partials[(3 * m + q) * nparts + blockIdx.x] = v;
     }
 }
 
@@ -262,14 +360,30 @@ cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *S
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     DcsConsts k;
     const double s2 = 2.0 * (double)p->sigma * (double)p->sigma;
-    for (int i = 0; i < 3; ++i) k.g[i] = (float)exp(-(double)(i + 1) / s2);
+    for (int i = 0; i < 4; ++i) k.g[i] = (float)exp(-(double)i / s2);
     const int h = (p->L - 1) / 2;
     for (int i = 0; i <= kMaxH; ++i) k.gl[i] = (float)exp(-(double)(i * i) / s2);
-    k.stencil = p->stencil;
     k.h = h;
     k.invQ = (float)(1.0 / (p->stencil == SAL_STENCIL_26 ? 26.0 : (double)(2 * h)));
-    dcs_kernel<<<(unsigned)tiles, DNT, 0, s>>>(E, d.T, d.X, d.Y, p->boundary, (int)nx, (int)ny, Sm, partials, tiles, k);
-    cudaError_t e = cudaGetLastError();
+    int smem = 0;
+    for (int m = 0; m < 3; ++m) {
+        const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
+        smem = f > smem ? f : smem;
+    }
+    const dim3 grid((unsigned)tiles, 3);
+    cudaError_t e;
+    if (p->stencil == SAL_STENCIL_26) {
+        e = cudaFuncSetAttribute(dcs_kernel<SAL_STENCIL_26>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        dcs_kernel<SAL_STENCIL_26><<<grid, DNT, smem, s>>>(E, d.T, d.X, d.Y, p->boundary, (int)nx, (int)ny, Sm, partials,
+                                                          tiles, k);
+    } else {
+        e = cudaFuncSetAttribute(dcs_kernel<SAL_STENCIL_LINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        dcs_kernel<SAL_STENCIL_LINE><<<grid, DNT, smem, s>>>(E, d.T, d.X, d.Y, p->boundary, (int)nx, (int)ny, Sm,
+                                                            partials, tiles, k);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double *second = partials + 9 * tiles;
     reduce_partials_kernel<<<kRedBlocks, 256, 0, s>>>(partials, tiles, second, kRedBlocks);
@@ -278,7 +392,6 @@ cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *S
     reduce_partials_kernel<<<1, 256, 0, s>>>(second, kRedBlocks, stats, 1);
     return cudaGetLastError();
 }
-
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s)
 {

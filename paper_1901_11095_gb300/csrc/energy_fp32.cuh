@@ -17,6 +17,11 @@
 // non-zero frequency sum to zero) so that a constant cube has an exactly zero spectrum.
 // Indices are taken relative to the cube centre; that multiplies each coefficient by a
 // unit phase, which |F| does not see.
+//
+// Complex values travel as packed pairs (re, im) and use the f32x2 add/sub/fma forms of
+// sm_100-family GPUs, one instruction per complex add or complex-by-real FMA.  The loops
+// over mu and nu stay rolled so the hot loop fits the instruction cache; the loops inside
+// one length-L transform, whose indices select twiddles and registers, are unrolled.
 #pragma once
 #include "sal_internal.cuh"
 
@@ -39,57 +44,127 @@ struct EGeo {
     static constexpr int NG2 = ROWS * L * PY2;          // float2 of one mu-slice of G2
     static constexpr int NALIAS = (NV * 4 > NG2 * 8) ? NV : NG2 * 2;
     static constexpr size_t SMEM = sizeof(float) * (size_t)(NG1 + NALIAS);
+    static constexpr int NZ = R + 2 * H;                // window of one thread's R outputs
 };
 
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// ---- packed pairs of floats -------------------------------------------------------------
+typedef unsigned long long f2x;   // .x in the low word, .y in the high word
 
-// Magnitudes of one complex line of the y transform, window centred at Z[C]:
+__device__ __forceinline__ f2x pk(float x, float y)
+{
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float lo(f2x v)
+{
+    float x;
+    asm("{ .reg .f32 t; mov.b64 {%0, t}, %1; }" : "=f"(x) : "l"(v));
+    return x;
+}
+__device__ __forceinline__ float hi(f2x v)
+{
+    float y;
+    asm("{ .reg .f32 t; mov.b64 {t, %0}, %1; }" : "=f"(y) : "l"(v));
+    return y;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b)
+{
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b)
+{
+    f2x r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c)
+{
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b)
+{
+    f2x r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// |F| of the magnitude stage: the hardware approximate square root (relative error of a
+// few ulp, far inside the path's tolerance).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Twiddles of one cube size in registers, as broadcast pairs: c2[k] = (cos, cos) and
+// s2[k] = (sin, sin) of 2 pi k / L, k = 0..L-1.
+template <int L>
+struct Tw {
+    f2x c2[L], s2[L];
+    __device__ __forceinline__ void load(const SpecTables &tb)
+    {
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            c2[k] = pk(tb.cs[k], tb.cs[k]);
+            s2[k] = pk(tb.sn[k], tb.sn[k]);
+        }
+    }
+};
+
+// Magnitudes of one complex line of the y transform, window centred at Z[c]:
 // m[0] = |F(0)|, m[w] = |F(w)| + |F(-w)| for w = 1..H.
-template <int L, int C, int NZ>
-__device__ __forceinline__ void line_mags(const float2 (&Z)[NZ], const SpecTables &tb, float (&m)[(L + 1) / 2])
+template <int L, int NZ>
+__device__ __forceinline__ void line_mags(const f2x (&Z)[NZ], int c, const Tw<L> &tw, float (&m)[(L + 1) / 2])
 {
     constexpr int H = (L - 1) / 2;
-    const float2 z0 = Z[C];
-    float2 U[H + 1], D[H + 1];
-    float2 s = z0;
+    const f2x z0 = Z[c];
+    const f2x m2 = pk(-2.f, -2.f);
+    f2x U[H + 1], D[H + 1];
+    f2x s = z0;
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
-        float2 p = f2add(Z[C + k], Z[C - k]);
-        s = f2add(s, p);
-        U[k] = make_float2(fmaf(-2.f, z0.x, p.x), fmaf(-2.f, z0.y, p.y));
-        D[k] = f2sub(Z[C + k], Z[C - k]);
+        const f2x p = add2(Z[c + k], Z[c - k]);
+        s = add2(s, p);
+        U[k] = fma2(z0, m2, p);
+        D[k] = sub2(Z[c + k], Z[c - k]);
     }
-    m[0] = sqrtf(fmaf(s.x, s.x, s.y * s.y));
+    {
+        const float sx = lo(s), sy = hi(s);
+        m[0] = sqrt_approx(fmaf(sx, sx, sy * sy));
+    }
 #pragma unroll
     for (int w = 1; w <= H; ++w) {
-        float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+        f2x A = mul2(U[1], tw.c2[w % L]);
+        f2x B = mul2(D[1], tw.s2[w % L]);
 #pragma unroll
-        for (int k = 1; k <= H; ++k) {
-            const float c = tb.cs[(w * k) % L], sn = tb.sn[(w * k) % L];
-            A.x = fmaf(U[k].x, c, A.x);
-            A.y = fmaf(U[k].y, c, A.y);
-            B.x = fmaf(D[k].x, sn, B.x);
-            B.y = fmaf(D[k].y, sn, B.y);
+        for (int k = 2; k <= H; ++k) {
+            A = fma2(U[k], tw.c2[(w * k) % L], A);
+            B = fma2(D[k], tw.s2[(w * k) % L], B);
         }
-        const float pr = A.x + B.y, pi = A.y - B.x;   // F(+w) = A - iB
-        const float qr = A.x - B.y, qi = A.y + B.x;   // F(-w) = A + iB
-        m[w] = sqrtf(fmaf(pr, pr, pi * pi)) + sqrtf(fmaf(qr, qr, qi * qi));
+        const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+        const float pr = ax + by, pi = ay - bx;   // F(+w) = A - iB
+        const float qr = ax - by, qi = ay + bx;   // F(-w) = A + iB
+        m[w] = sqrt_approx(fmaf(pr, pr, pi * pi)) + sqrt_approx(fmaf(qr, qr, qi * qi));
     }
 }
 
-// Real line (the mu = 0, nu = 0 line): m[w] = |F(w)| for w = 1..H (the -w point is the
-// conjugate mirror, counted by the half-spectrum factor).
-template <int L, int C, int NZ>
-__device__ __forceinline__ void line_mags_real(const float2 (&Z)[NZ], const SpecTables &tb, float (&m)[(L + 1) / 2])
+// Real line (the mu = 0, nu = 0 line; the imaginary halves are zero): m[w] = |F(w)| for
+// w = 1..H (the -w point is the conjugate mirror, counted by the half-spectrum factor).
+template <int L, int NZ>
+__device__ __forceinline__ void line_mags_real(const f2x (&Z)[NZ], int c, const Tw<L> &tw, float (&m)[(L + 1) / 2])
 {
     constexpr int H = (L - 1) / 2;
-    const float z0 = Z[C].x;
+    const float z0 = lo(Z[c]);
     float U[H + 1], D[H + 1];
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
-        U[k] = fmaf(-2.f, z0, Z[C + k].x + Z[C - k].x);
-        D[k] = Z[C + k].x - Z[C - k].x;
+        U[k] = fmaf(-2.f, z0, lo(Z[c + k]) + lo(Z[c - k]));
+        D[k] = lo(Z[c + k]) - lo(Z[c - k]);
     }
     m[0] = 0.f;
 #pragma unroll
@@ -97,138 +172,118 @@ __device__ __forceinline__ void line_mags_real(const float2 (&Z)[NZ], const Spec
         float A = 0.f, B = 0.f;
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
-            A = fmaf(U[k], tb.cs[(w * k) % L], A);
-            B = fmaf(D[k], tb.sn[(w * k) % L], B);
+            A = fmaf(U[k], lo(tw.c2[(w * k) % L]), A);
+            B = fmaf(D[k], lo(tw.s2[(w * k) % L]), B);
         }
-        m[w] = sqrtf(fmaf(A, A, B * B));
+        m[w] = sqrt_approx(fmaf(A, A, B * B));
     }
 }
 
 template <class G>
-__device__ __forceinline__ void load_line(const float2 *sG2, int row, int nu, int j, float2 (&Z)[G::R + 2 * G::H])
+__device__ __forceinline__ void load_line(const float2 *sG2, int row, int nu, int j, f2x (&Z)[G::NZ])
 {
-    static_assert((G::R + 2 * G::H) % 2 == 0, "even window");
-    const float4 *p = reinterpret_cast<const float4 *>(sG2 + ((row * G::L + nu + G::H) * G::PY2 + G::R * j));
+    static_assert(G::NZ % 2 == 0, "even window");
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(sG2 + ((row * G::L + nu + G::H) * G::PY2 + G::R * j));
 #pragma unroll
-    for (int k = 0; k < (G::R + 2 * G::H) / 2; ++k) {
-        const float4 v = p[k];
-        Z[2 * k] = make_float2(v.x, v.y);
-        Z[2 * k + 1] = make_float2(v.z, v.w);
+    for (int k = 0; k < G::NZ / 2; ++k) {
+        const ulonglong2 v = p[k];
+        Z[2 * k] = v.x;
+        Z[2 * k + 1] = v.y;
     }
 }
 
-template <class G, int MU, int NU>
-__device__ __forceinline__ void accum(const float (&m)[G::H + 1], const SpecTables &tb, float &et, float &ex, float &ey,
-                                      int wfirst)
+// Projection weights of the (mu, |nu|) group for omega = 0..H, from the parameter bank.
+template <class G>
+__device__ __forceinline__ void load_w(const SpecTables &tb, int mu, int nu, float (&w)[G::H + 1][3])
 {
+    const float *src = &tb.w[(mu * kMaxHalf + nu) * kMaxHalf * 3];
 #pragma unroll
-    for (int w = 0; w <= G::H; ++w) {
-        if (w < wfirst) continue;
-        const float *wt = &tb.w[((MU * kMaxHalf + NU) * kMaxHalf + w) * 3];
-        et = fmaf(wt[0], m[w], et);
-        ex = fmaf(wt[1], m[w], ex);
-        ey = fmaf(wt[2], m[w], ey);
+    for (int om = 0; om <= G::H; ++om) {
+        w[om][0] = src[om * 3];
+        w[om][1] = src[om * 3 + 1];
+        w[om][2] = src[om * 3 + 2];
     }
 }
 
-// y stage for one mu: every thread owns R consecutive outputs of one (t, x) row.
-template <class G, int MU>
-__device__ __forceinline__ void y_stage(const float2 *sG2, int row, int j, const SpecTables &tb,
-                                        float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+template <class G>
+__device__ __forceinline__ void accum(const float (&m)[G::H + 1], const float (&w)[G::H + 1][3], int wfirst, float &et,
+                                      float &ex, float &ey)
 {
-    constexpr int H = G::H, R = G::R, NZ = R + 2 * H;
-    if (MU == 0) {
-        {   // nu = 0: real line, omega > 0 only
-            float2 Z[NZ];
-            load_line<G>(sG2, row, 0, j, Z);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float m[H + 1];
-                switch (r) {  // compile-time centre
-                    case 0: line_mags_real<G::L, H + 0>(Z, tb, m); break;
-                    case 1: line_mags_real<G::L, H + 1>(Z, tb, m); break;
-                    case 2: line_mags_real<G::L, H + 2>(Z, tb, m); break;
-                    default: line_mags_real<G::L, H + 3>(Z, tb, m); break;
-                }
-                accum<G, 0, 0>(m, tb, et[r], ex[r], ey[r], 1);
-            }
-        }
+    for (int om = 0; om <= G::H; ++om) {
+        if (om < wfirst) continue;
+        et = fmaf(w[om][0], m[om], et);
+        ex = fmaf(w[om][1], m[om], ex);
+        ey = fmaf(w[om][2], m[om], ey);
+    }
+}
+
+// One complex line (weights of group (mu, nu)) for the thread's R outputs.
+template <class G>
+__device__ __forceinline__ void y_single(const float2 *sG2, int row, int j, int mu, int nu, const SpecTables &tb,
+                                         const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+{
+    f2x Z[G::NZ];
+    load_line<G>(sG2, row, nu, j, Z);
+    float w[G::H + 1][3];
+    load_w<G>(tb, mu, nu, w);
 #pragma unroll
-        for (int nu = 1; nu <= H; ++nu) {   // nu > 0: all omega; the nu < 0 lines are conjugate mirrors
-            float2 Z[NZ];
-            load_line<G>(sG2, row, nu, j, Z);
+    for (int r = 0; r < G::R; ++r) {
+        float m[G::H + 1];
+        line_mags<G::L>(Z, r + G::H, tw, m);
+        accum<G>(m, w, 0, et[r], ex[r], ey[r]);
+    }
+}
+
+// The +nu and -nu lines of one mu > 0, which share their weights.
+template <class G>
+__device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu, int nu, const SpecTables &tb,
+                                       const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+{
+    f2x Zp[G::NZ], Zm[G::NZ];
+    load_line<G>(sG2, row, nu, j, Zp);
+    load_line<G>(sG2, row, -nu, j, Zm);
+    float w[G::H + 1][3];
+    load_w<G>(tb, mu, nu, w);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float m[H + 1];
-                switch (r) {
-                    case 0: line_mags<G::L, H + 0>(Z, tb, m); break;
-                    case 1: line_mags<G::L, H + 1>(Z, tb, m); break;
-                    case 2: line_mags<G::L, H + 2>(Z, tb, m); break;
-                    default: line_mags<G::L, H + 3>(Z, tb, m); break;
-                }
+    for (int r = 0; r < G::R; ++r) {
+        float mp[G::H + 1], mm[G::H + 1];
+        line_mags<G::L>(Zp, r + G::H, tw, mp);
+        line_mags<G::L>(Zm, r + G::H, tw, mm);
 #pragma unroll
-                for (int w = 0; w <= H; ++w) {
-                    const float *wt = &tb.w[((0 * kMaxHalf + nu) * kMaxHalf + w) * 3];
-                    et[r] = fmaf(wt[0], m[w], et[r]);
-                    ex[r] = fmaf(wt[1], m[w], ex[r]);
-                    ey[r] = fmaf(wt[2], m[w], ey[r]);
-                }
-            }
-        }
-    } else {
-        {   // nu = 0
-            float2 Z[NZ];
-            load_line<G>(sG2, row, 0, j, Z);
+        for (int om = 0; om <= G::H; ++om) mp[om] += mm[om];
+        accum<G>(mp, w, 0, et[r], ex[r], ey[r]);
+    }
+}
+
+// The real mu = 0, nu = 0 line, omega > 0 only.
+template <class G>
+__device__ __forceinline__ void y_real(const float2 *sG2, int row, int j, const SpecTables &tb, const Tw<G::L> &tw,
+                                       float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+{
+    f2x Z[G::NZ];
+    load_line<G>(sG2, row, 0, j, Z);
+    float w[G::H + 1][3];
+    load_w<G>(tb, 0, 0, w);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float m[H + 1];
-                switch (r) {
-                    case 0: line_mags<G::L, H + 0>(Z, tb, m); break;
-                    case 1: line_mags<G::L, H + 1>(Z, tb, m); break;
-                    case 2: line_mags<G::L, H + 2>(Z, tb, m); break;
-                    default: line_mags<G::L, H + 3>(Z, tb, m); break;
-                }
-                accum<G, MU, 0>(m, tb, et[r], ex[r], ey[r], 0);
-            }
-        }
-#pragma unroll
-        for (int nu = 1; nu <= H; ++nu) {   // the +nu and -nu lines share their weights
-            float2 Zp[NZ], Zm[NZ];
-            load_line<G>(sG2, row, nu, j, Zp);
-            load_line<G>(sG2, row, -nu, j, Zm);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float mp[H + 1], mm[H + 1];
-                switch (r) {
-                    case 0: line_mags<G::L, H + 0>(Zp, tb, mp); line_mags<G::L, H + 0>(Zm, tb, mm); break;
-                    case 1: line_mags<G::L, H + 1>(Zp, tb, mp); line_mags<G::L, H + 1>(Zm, tb, mm); break;
-                    case 2: line_mags<G::L, H + 2>(Zp, tb, mp); line_mags<G::L, H + 2>(Zm, tb, mm); break;
-                    default: line_mags<G::L, H + 3>(Zp, tb, mp); line_mags<G::L, H + 3>(Zm, tb, mm); break;
-                }
-#pragma unroll
-                for (int w = 0; w <= H; ++w) {
-                    const float s = mp[w] + mm[w];
-                    const float *wt = &tb.w[((MU * kMaxHalf + nu) * kMaxHalf + w) * 3];
-                    et[r] = fmaf(wt[0], s, et[r]);
-                    ex[r] = fmaf(wt[1], s, ex[r]);
-                    ey[r] = fmaf(wt[2], s, ey[r]);
-                }
-            }
-        }
+    for (int r = 0; r < G::R; ++r) {
+        float m[G::H + 1];
+        line_mags_real<G::L>(Z, r + G::H, tw, m);
+        accum<G>(m, w, 1, et[r], ex[r], ey[r]);
     }
 }
 
 // x stage for one mu: G1[mu](x-h..x+h, y') -> G2[mu, nu](x, y') for the BT x BX x PY items.
-template <class G, int MU>
-__device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, const SpecTables &tb)
+template <class G>
+__device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
 {
     constexpr int L = G::L, H = G::H, PY = G::PY, NITEM = G::ROWS * PY;
-    for (int i = threadIdx.x; i < NITEM; i += G::NT) {
-        const int row = i / PY, yy = i - row * PY;
-        const int t = row / G::BX, x = row - t * G::BX;
-        const float *g = sG1 + ((t * G::HX + x) * L) * PY + yy;   // column x' = x + k, k = 0..L-1
-        float2 *o = sG2 + (row * L + H) * G::PY2 + yy;            // slot of nu = 0
-        if (MU == 0) {
+    if (mu == 0) {
+        for (int i = threadIdx.x; i < NITEM; i += G::NT) {
+            const int row = i / PY, yy = i - row * PY;
+            const int t = row / G::BX, x = row - t * G::BX;
+            const float *g = sG1 + ((t * G::HX + x) * L) * PY + yy;
+            float2 *o = sG2 + (row * L + H) * G::PY2 + yy;
             float z[L];
 #pragma unroll
             for (int k = 0; k < L; ++k) z[k] = g[k * L * PY];
@@ -247,61 +302,49 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, const Spe
                 float A = 0.f, B = 0.f;
 #pragma unroll
                 for (int k = 1; k <= H; ++k) {
-                    A = fmaf(U[k], tb.cs[(nu * k) % L], A);
-                    B = fmaf(D[k], tb.sn[(nu * k) % L], B);
+                    A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
+                    B = fmaf(D[k], lo(tw.s2[(nu * k) % L]), B);
                 }
-                o[nu * G::PY2] = make_float2(A, -B);
+                o[nu * G::PY2] = make_float2(A, -B);   // G2(+nu) = A - iB; nu < 0 is its mirror
             }
-        } else {
-            float2 z[L];
+        }
+    } else {
+        const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
+        const f2x m2 = pk(-2.f, -2.f);
+        for (int i = threadIdx.x; i < NITEM; i += G::NT) {
+            const int row = i / PY, yy = i - row * PY;
+            const int t = row / G::BX, x = row - t * G::BX;
+            const float *g = sG1 + ((t * G::HX + x) * L) * PY + yy;
+            f2x *o = reinterpret_cast<f2x *>(sG2 + (row * L + H) * G::PY2 + yy);
+            f2x z[L];
 #pragma unroll
-            for (int k = 0; k < L; ++k)
-                z[k] = make_float2(g[k * L * PY + (2 * MU - 1) * PY], g[k * L * PY + (2 * MU) * PY]);
-            const float2 z0 = z[H];
-            float2 s = z0, U[H + 1], D[H + 1];
+            for (int k = 0; k < L; ++k) z[k] = pk(g[k * L * PY + cre], g[k * L * PY + cim]);
+            const f2x z0 = z[H];
+            f2x s = z0, U[H + 1], D[H + 1];
 #pragma unroll
             for (int k = 1; k <= H; ++k) {
-                const float2 p = f2add(z[H + k], z[H - k]);
-                s = f2add(s, p);
-                U[k] = make_float2(fmaf(-2.f, z0.x, p.x), fmaf(-2.f, z0.y, p.y));
-                D[k] = f2sub(z[H + k], z[H - k]);
+                const f2x p = add2(z[H + k], z[H - k]);
+                s = add2(s, p);
+                U[k] = fma2(z0, m2, p);
+                D[k] = sub2(z[H + k], z[H - k]);
             }
             o[0] = s;
 #pragma unroll
             for (int nu = 1; nu <= H; ++nu) {
-                float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+                f2x A = mul2(U[1], tw.c2[nu % L]);
+                f2x B = mul2(D[1], tw.s2[nu % L]);
 #pragma unroll
-                for (int k = 1; k <= H; ++k) {
-                    const float c = tb.cs[(nu * k) % L], sn = tb.sn[(nu * k) % L];
-                    A.x = fmaf(U[k].x, c, A.x);
-                    A.y = fmaf(U[k].y, c, A.y);
-                    B.x = fmaf(D[k].x, sn, B.x);
-                    B.y = fmaf(D[k].y, sn, B.y);
+                for (int k = 2; k <= H; ++k) {
+                    A = fma2(U[k], tw.c2[(nu * k) % L], A);
+                    B = fma2(D[k], tw.s2[(nu * k) % L], B);
                 }
-                o[nu * G::PY2] = make_float2(A.x + B.y, A.y - B.x);    // G2(+nu) = A - iB
-                o[-nu * G::PY2] = make_float2(A.x - B.y, A.y + B.x);   // G2(-nu) = A + iB
+                const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+                o[nu * G::PY2] = pk(ax + by, ay - bx);    // G2(+nu) = A - iB
+                o[-nu * G::PY2] = pk(ax - by, ay + bx);   // G2(-nu) = A + iB
             }
         }
     }
 }
-
-template <class G, int MU>
-struct MuLoop {
-    __device__ __forceinline__ static void run(const float *sG1, float2 *sG2, int row, int j, const SpecTables &tb,
-                                               float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
-    {
-        x_stage<G, MU>(sG1, sG2, tb);
-        __syncthreads();
-        y_stage<G, MU>(sG2, row, j, tb, et, ex, ey);
-        __syncthreads();
-        MuLoop<G, MU + 1>::run(sG1, sG2, row, j, tb, et, ex, ey);
-    }
-};
-template <class G>
-struct MuLoop<G, G::H + 1> {
-    __device__ __forceinline__ static void run(const float *, float2 *, int, int, const SpecTables &, float (&)[G::R],
-                                               float (&)[G::R], float (&)[G::R]) {}
-};
 
 template <class G>
 __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restrict__ V, int64_t T, int64_t X,
@@ -309,7 +352,6 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
                                                             float *__restrict__ E,
                                                             const __grid_constant__ SpecTables tb)
 {
-    static_assert(G::R == 4, "y_stage unrolls four outputs per thread");
     constexpr int L = G::L, H = G::H, PY = G::PY;
     extern __shared__ __align__(16) float smem[];
     float *sG1 = smem;
@@ -322,16 +364,31 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
     const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
 
-    // halo tile of V, boundary-extended (every address maps inside the volume)
-    for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-        const int r = i / PY, yy = i - r * PY;
-        const int a = r / G::HX, xx = r - a * G::HX;
-        const int64_t gt = ext_index(t0 - H + a, T, bnd);
-        const int64_t gx = ext_index(x0 - H + xx, X, bnd);
-        const int64_t gy = ext_index(y0 - H + yy, Y, bnd);
-        sV[i] = __ldg(V + (gt * X + gx) * Y + gy);
+    // halo tile of V by asynchronous 4-byte copies, one warp per row (t, x) and
+    // consecutive columns per lane; outside the volume the boundary extension supplies
+    // the samples (mapped once per row for t and x, per column only at the y faces)
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int r = warp; r < (G::BT + 2 * H) * G::HX; r += G::NT / 32) {
+            const int a = r / G::HX, xx = r - a * G::HX;
+            const int64_t gt = ext_index(t0 - H + a, T, bnd);
+            const int64_t gx = ext_index(x0 - H + xx, X, bnd);
+            const float *src = V + (gt * X + gx) * Y;
+            float *dst = sV + r * PY;
+#pragma unroll
+            for (int c = lane; c < PY; c += 32) {
+                int64_t gy = y0 - H + c;
+                if (gy < 0 || gy >= Y) gy = ext_index(gy, Y, bnd);
+                const unsigned d = (unsigned)__cvta_generic_to_shared(dst + c);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + gy) : "memory");
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
+
+    Tw<L> tw;
+    tw.load(tb);
 
     // stage t: (t, x', y') -> G1 components [Re G1(0), Re G1(1), Im G1(1), ...]
     for (int i = threadIdx.x; i < G::BT * G::HX * PY; i += G::NT) {
@@ -356,8 +413,8 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
             float A = 0.f, B = 0.f;
 #pragma unroll
             for (int k = 1; k <= H; ++k) {
-                A = fmaf(U[k], tb.cs[(mu * k) % L], A);
-                B = fmaf(D[k], tb.sn[(mu * k) % L], B);
+                A = fmaf(U[k], lo(tw.c2[(mu * k) % L]), A);
+                B = fmaf(D[k], lo(tw.s2[(mu * k) % L]), B);
             }
             o[(2 * mu - 1) * PY] = A;     // G1(mu) = A - iB
             o[(2 * mu) * PY] = -B;
@@ -369,27 +426,40 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
     float et[G::R], ex[G::R], ey[G::R];
 #pragma unroll
     for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
-    MuLoop<G, 0>::run(sG1, sG2, row, j, tb, et, ex, ey);
+
+#pragma unroll 1
+    for (int mu = 0; mu <= H; ++mu) {
+        x_stage<G>(sG1, sG2, mu, tw);
+        __syncthreads();
+        if (mu == 0) {
+            y_real<G>(sG2, row, j, tb, tw, et, ex, ey);
+#pragma unroll 1
+            for (int nu = 1; nu <= H; ++nu) y_single<G>(sG2, row, j, 0, nu, tb, tw, et, ex, ey);
+        } else {
+            y_single<G>(sG2, row, j, mu, 0, tb, tw, et, ex, ey);
+#pragma unroll 1
+            for (int nu = 1; nu <= H; ++nu) y_pair<G>(sG2, row, j, mu, nu, tb, tw, et, ex, ey);
+        }
+        __syncthreads();
+    }
 
     const int t = row / G::BX, x = row - t * G::BX;
     const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + G::R * j;
     if (gt >= T || gx >= X) return;
     const int64_t N = T * X * Y;
     float *e0 = E + (gt * X + gx) * Y + gy;
+    const float sc = tb.escale;
     if (gy + G::R <= Y && (reinterpret_cast<uintptr_t>(e0) & 15) == 0 && (Y & 3) == 0) {
-        *reinterpret_cast<float4 *>(e0) =
-            make_float4(et[0] * tb.escale, et[1] * tb.escale, et[2] * tb.escale, et[3] * tb.escale);
-        *reinterpret_cast<float4 *>(e0 + N) =
-            make_float4(ex[0] * tb.escale, ex[1] * tb.escale, ex[2] * tb.escale, ex[3] * tb.escale);
-        *reinterpret_cast<float4 *>(e0 + 2 * N) =
-            make_float4(ey[0] * tb.escale, ey[1] * tb.escale, ey[2] * tb.escale, ey[3] * tb.escale);
+        *reinterpret_cast<float4 *>(e0) = make_float4(et[0] * sc, et[1] * sc, et[2] * sc, et[3] * sc);
+        *reinterpret_cast<float4 *>(e0 + N) = make_float4(ex[0] * sc, ex[1] * sc, ex[2] * sc, ex[3] * sc);
+        *reinterpret_cast<float4 *>(e0 + 2 * N) = make_float4(ey[0] * sc, ey[1] * sc, ey[2] * sc, ey[3] * sc);
     } else {
 #pragma unroll
         for (int r = 0; r < G::R; ++r) {
             if (gy + r < Y) {
-                e0[r] = et[r] * tb.escale;
-                e0[r + N] = ex[r] * tb.escale;
-                e0[r + 2 * N] = ey[r] * tb.escale;
+                e0[r] = et[r] * sc;
+                e0[r + N] = ex[r] * sc;
+                e0[r + 2 * N] = ey[r] * sc;
             }
         }
     }
@@ -398,6 +468,7 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
 template <class G>
 cudaError_t launch_energy_impl(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s)
 {
+    static_assert(G::R == 4, "four outputs per thread along y");
     SpecTables tb;
     make_tables(G::L, &tb);
     const int64_t nt = (d.T + G::BT - 1) / G::BT;

@@ -62,7 +62,8 @@ def test_saliency_matches_oracle(shape, L, bnd, stc, sigma, seed):
     S_ref, E_ref, Sm_ref, st_ref = O.saliency(V, L=L, bnd=BND[bnd], stencil=STC[stc], sigma=sigma, full=True)
     assert nerr(S.cpu().numpy(), S_ref) < TOL_S
     st = stats.cpu().numpy().reshape(3, 3)
-    np.testing.assert_allclose(st[:, :2], st_ref[:, :2], rtol=TOL_MAP)
+    for m in range(3):      # normwise: min and max carry the error of their map, relative to its scale
+        np.testing.assert_allclose(st[m, :2], st_ref[m, :2], rtol=0, atol=TOL_MAP * np.abs(Sm_ref[m]).max())
     np.testing.assert_allclose(st[:, 2], st_ref[:, 2], rtol=1e-4)
 
 
@@ -135,7 +136,8 @@ def test_directional_compare_matches_oracle(stc, L, bnd, sigma):
         assert nerr(Smh[m], Sm_ref[m]) < TOL_MAP
     st_ref = O.stats(Sm_ref)
     sth = st.cpu().numpy().reshape(3, 3)
-    np.testing.assert_allclose(sth[:, :2], st_ref[:, :2], rtol=TOL_MAP)
+    for m in range(3):
+        np.testing.assert_allclose(sth[m, :2], st_ref[m, :2], rtol=0, atol=TOL_MAP * np.abs(Sm_ref[m]).max())
     np.testing.assert_allclose(sth[:, 2], st_ref[:, 2], rtol=1e-5)
     # the FP64 min / max reductions are exact on the maps the kernel wrote
     for m in range(3):
