@@ -364,26 +364,25 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
     const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
 
-    // halo tile of V by asynchronous 4-byte copies, one warp per row (t, x) and
-    // consecutive columns per lane; outside the volume the boundary extension supplies
-    // the samples (mapped once per row for t and x, per column only at the y faces)
-    {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int r = warp; r < (G::BT + 2 * H) * G::HX; r += G::NT / 32) {
+    // halo tile of V; outside the volume the boundary extension supplies the samples
+    const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
+                        y0 + G::BY + H <= Y;
+    if (inside) {
+        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            const int r = i / PY, yy = i - r * PY;
+            const int a = r / G::HX, xx = r - a * G::HX;
+            sV[i] = __ldg(src + ((int64_t)a * X + xx) * Y + yy);
+        }
+    } else {
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            const int r = i / PY, yy = i - r * PY;
             const int a = r / G::HX, xx = r - a * G::HX;
             const int64_t gt = ext_index(t0 - H + a, T, bnd);
             const int64_t gx = ext_index(x0 - H + xx, X, bnd);
-            const float *src = V + (gt * X + gx) * Y;
-            float *dst = sV + r * PY;
-#pragma unroll
-            for (int c = lane; c < PY; c += 32) {
-                int64_t gy = y0 - H + c;
-                if (gy < 0 || gy >= Y) gy = ext_index(gy, Y, bnd);
-                const unsigned d = (unsigned)__cvta_generic_to_shared(dst + c);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + gy) : "memory");
-            }
+            const int64_t gy = ext_index(y0 - H + yy, Y, bnd);
+            sV[i] = __ldg(V + (gt * X + gx) * Y + gy);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
 
