@@ -143,6 +143,34 @@ SAL_API sal_status sal_combine(const float *Sm, const double *stats, sal_dims di
 SAL_API sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, float *S,
                         double *stats, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Directional compare for callers that cannot allocate device memory.
+ *
+ * The same computation and kernels as sal_directional_compare, but without a workspace
+ * argument: the scratch for the per-tile reduction records is a fixed array inside the
+ * library.  It serves callers that may not allocate device memory themselves, for example
+ * a plug-in whose host application owns the whole GPU memory budget and forbids
+ * allocations by its plug-ins, or a processing loop that must never enter the allocator.
+ * The paper has no counterpart of this call; it is an interface convenience.
+ *
+ * Limits and behaviour:
+ *  - the volume may need at most SAL_DCS_STATIC_MAX_TILES tiles of 8 x 8 x 64 voxels
+ *    (ceil(T/8) * ceil(X/8) * ceil(Y/64)); a larger volume returns SAL_ERR_WORKSPACE and
+ *    launches nothing.  The array takes 9 * (SAL_DCS_STATIC_MAX_TILES + 160) doubles,
+ *    about 9.4 MB, on every GPU that loads the library, until the process exits;
+ *  - the first call on a device looks up the array's device address (a one-time set-up
+ *    for that device); make that first call before any stream capture;
+ *  - every call shares the one array and overwrites every record it reads, so nothing has
+ *    to be cleared between calls; two calls whose kernels overlap on the GPU (different
+ *    streams, or different host threads on one device) race on it and must be ordered by
+ *    the caller;
+ *  - E, Sm and stats are the caller's device memory, as for sal_directional_compare;
+ *    this entry point calls no allocation routine.
+ */
+#define SAL_DCS_STATIC_MAX_TILES 131072
+SAL_API sal_status sal_directional_compare_static(const float *E, sal_dims dims, const sal_params *p,
+                                                  float *Sm, double *stats, void *stream);
+
 /* Static text for a status code. */
 SAL_API const char *sal_status_string(sal_status s);
 /* Thread-local detail of the last failing call on this thread ("" if none). */

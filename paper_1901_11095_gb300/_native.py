@@ -18,6 +18,7 @@ SAL_PREC_FP32, SAL_PREC_TF32, SAL_PREC_BF16 = 0, 1, 2
 SAL_BND_REFLECT, SAL_BND_PERIODIC = 0, 1
 SAL_STENCIL_26, SAL_STENCIL_LINE = 0, 1
 SAL_STATS_LEN = 9
+SAL_DCS_STATIC_MAX_TILES = 131072
 
 
 class SalDims(ctypes.Structure):
@@ -56,6 +57,7 @@ def lib():
             "sal_project": [vp, ctypes.c_int64, ctypes.c_int32, vp, vp],
             "sal_spectral_energy": [vp, SalDims, pp, vp, vp],
             "sal_directional_compare": [vp, SalDims, pp, vp, vp, vp, sz, vp],
+            "sal_directional_compare_static": [vp, SalDims, pp, vp, vp, vp],
             "sal_combine": [vp, vp, SalDims, pp, vp, vp],
             "sal_saliency": [vp, SalDims, pp, vp, vp, vp, sz, vp],
         }
@@ -79,5 +81,6 @@ def check(status: int) -> None:
 
 def exported_symbols() -> list[str]:
     return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
-            "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_combine", "sal_saliency",
+            "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_directional_compare_static",
+            "sal_combine", "sal_saliency",
             "sal_status_string", "sal_last_error"]

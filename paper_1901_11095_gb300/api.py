@@ -118,6 +118,21 @@ def sal_directional_compare(E: torch.Tensor, p: SalParams, Sm: torch.Tensor | No
     return Sm, stats
 
 
+def sal_directional_compare_static(E: torch.Tensor, p: SalParams, Sm: torch.Tensor | None = None,
+                                   stats: torch.Tensor | None = None, stream=None):
+    """sal_directional_compare without a workspace: the library's fixed scratch serves the
+    reduction, for callers that may not allocate device memory (outputs must be passed in
+    by such callers; the defaults here allocate them with torch only for convenience)."""
+    dims = SalDims(*[int(s) for s in E.shape[1:]])
+    if Sm is None:
+        Sm = torch.empty_like(E)
+    if stats is None:
+        stats = torch.empty(N.SAL_STATS_LEN, device=E.device, dtype=torch.float64)
+    check(N.lib().sal_directional_compare_static(_dev(E, name="E"), dims, ctypes.byref(p), _dev(Sm, name="Sm"),
+                                                 _dev(stats, torch.float64, "stats"), _stream(stream)))
+    return Sm, stats
+
+
 def sal_combine(Sm: torch.Tensor, stats: torch.Tensor, p: SalParams, S: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
     """Eq. 6 on the min-max normalised maps: S [T, X, Y]."""

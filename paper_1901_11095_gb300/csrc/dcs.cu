@@ -11,6 +11,8 @@
 // finish the FP64 reduction.
 #include <float.h>
 
+#include <mutex>
+
 #include "sal_internal.cuh"
 
 namespace sal {
@@ -405,6 +407,45 @@ cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, con
     if (blocks < 1) blocks = 1;
     combine_kernel<<<(unsigned)blocks, 256, 0, s>>>(Sm, stats, N, p->a, p->b, p->c, p->eps, S);
     return cudaGetLastError();
+}
+
+// ---- directional compare with fixed scratch --------------------------------------------
+// Scratch for the partial records of sal_directional_compare_static: a file-scope device
+// array, so that entry point allocates nothing.  Its size is fixed at build time; every
+// GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) double g_dcs_static_scratch[9 * (SAL_DCS_STATIC_MAX_TILES + kRedBlocks)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+int64_t dcs_num_tiles(sal_dims d)
+{
+    int64_t nt, nx, ny;
+    dcs_tiles(d, &nt, &nx, &ny);
+    return nt * nx * ny;
+}
+
+// Device address of the fixed scratch on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address comes from cudaGetSymbolAddress, once
+// per device (with that device current), and is cached.
+cudaError_t dcs_static_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_dcs_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace sal

@@ -216,6 +216,26 @@ sal_status sal_directional_compare(const float *E, sal_dims dims, const sal_para
     return e == cudaSuccess ? ok() : cuda_fail(e, "sal_directional_compare");
 }
 
+sal_status sal_directional_compare_static(const float *E, sal_dims dims, const sal_params *p, float *Sm,
+                                          double *stats, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!E || !Sm || !stats) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(E) || !aligned16(Sm) || !aligned16(stats))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const int64_t tiles = sal::dcs_num_tiles(dims);
+    if (tiles > SAL_DCS_STATIC_MAX_TILES)
+        return fail(SAL_ERR_WORKSPACE, "volume needs %lld tiles of fixed scratch; at most %d fit",
+                    (long long)tiles, SAL_DCS_STATIC_MAX_TILES);
+    double *scratch = nullptr;
+    cudaError_t e = sal::dcs_static_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fixed scratch address");
+    e = sal::launch_dcs(E, dims, p, Sm, scratch, stats, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_directional_compare_static");
+}
+
 sal_status sal_combine(const float *Sm, const double *stats, sal_dims dims, const sal_params *p, float *S, void *stream)
 {
     sal_status s = check_dims(dims);

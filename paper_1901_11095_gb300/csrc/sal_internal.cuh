@@ -54,6 +54,9 @@ cudaError_t launch_project(const float *mag, int64_t n, int L, float *E, cudaStr
 int64_t dcs_num_partials(sal_dims d);
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials,
                        double *stats, cudaStream_t s);
+// Fixed-scratch variant of the directional compare (no allocation by caller or library).
+int64_t dcs_num_tiles(sal_dims d);
+cudaError_t dcs_static_scratch(double **out);
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s);
 
