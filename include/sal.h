@@ -78,6 +78,9 @@ typedef struct {
     double eps;         /* relative range below which a map counts as constant */
 } sal_params;
 
+/* Largest number of volumes one batched call takes. */
+#define SAL_BATCH_MAX 128
+
 /* Number of doubles in a stats array: (min, max, sum) of S_t, S_x, S_y in that order. */
 #define SAL_STATS_LEN 9
 
@@ -170,6 +173,72 @@ SAL_API sal_status sal_saliency(const float *V, sal_dims dims, const sal_params 
 #define SAL_DCS_STATIC_MAX_TILES 131072
 SAL_API sal_status sal_directional_compare_static(const float *E, sal_dims dims, const sal_params *p,
                                                   float *Sm, double *stats, void *stream);
+
+/* ---- Many uneven volumes at once --------------------------------------------------------
+ * One volume of a batch: device pointers owned by the caller (V input, S output), both
+ * float32 C order [T][X][Y] and 16-byte aligned. */
+typedef struct {
+    const float *V;
+    float *S;
+    int64_t T, X, Y;
+} sal_volume;
+
+/* Workspace bytes for sal_saliency_batched / sal_graph_create_batched over these volumes
+ * (per volume: E and S_m, 24 bytes per voxel, and its reduction records). */
+SAL_API sal_status sal_batch_workspace_size(const sal_volume *vols, int32_t n, const sal_params *p,
+                                            size_t *bytes);
+
+/*
+ * The whole method (Fig. 1) on n <= SAL_BATCH_MAX independent volumes of any sizes, each
+ * stage as ONE persistent launch over the tiles of all volumes: spectral energies,
+ * directional compare, per-volume FP64 statistics, combination.  Results equal those of
+ * sal_saliency on each volume.  `vols` is a host array; `stats` (device, n * 9 doubles,
+ * volume-major) may be NULL.  The spectral-energy tile shape is the autotuner's choice
+ * for (L, precision, size class of the largest volume) when one is cached, else the default.
+ */
+SAL_API sal_status sal_saliency_batched(const sal_volume *vols, int32_t n, const sal_params *p,
+                                        double *stats, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * The same batch captured once into a CUDA graph and replayed with sal_graph_launch.
+ * Creation may run the autotuner first (when no tile shape is cached for the batch), which
+ * times candidate launches on `stream` and synchronises it; the capture itself runs on a
+ * private stream.  The graph keeps the pointers it was built with: the volumes, `stats`
+ * and `ws` must stay valid and unchanged in size until sal_graph_destroy.  Host memory for
+ * the graph object is the only allocation; no device memory is allocated by the library.
+ */
+typedef struct sal_graph sal_graph;
+SAL_API sal_status sal_graph_create_batched(const sal_volume *vols, int32_t n, const sal_params *p,
+                                            double *stats, void *ws, size_t ws_bytes, void *stream,
+                                            sal_graph **out);
+/* Replays the captured batch on `stream` (asynchronous). */
+SAL_API sal_status sal_graph_launch(sal_graph *g, void *stream);
+SAL_API sal_status sal_graph_destroy(sal_graph *g);
+
+/* ---- Autotuner of the spectral-energy tile shape ----------------------------------------
+ * A choice: cube side, precision, size class (0: fewer than 16 Mi voxels per volume,
+ * 1: larger), candidate index and its BT x BX x BY output tile, and its measured time. */
+typedef struct {
+    int32_t L, precision, size_class, shape;
+    int32_t bt, bx, by;
+    float ms;
+} sal_tile_choice;
+
+/* Times every candidate tile shape of the spectral-energy kernel on this volume (E is a
+ * device buffer of 3 * T * X * Y floats it may overwrite), caches the fastest for the
+ * process and returns it.  Synchronises `stream`: not for use during stream capture. */
+SAL_API sal_status sal_autotune(const float *V, sal_dims dims, const sal_params *p, float *E, void *stream,
+                                sal_tile_choice *out);
+/* The same over a batch (times the persistent batched launch; ws as for the batch). */
+SAL_API sal_status sal_autotune_batched(const sal_volume *vols, int32_t n, const sal_params *p, void *ws,
+                                        size_t ws_bytes, void *stream, sal_tile_choice *out);
+/* The shape the calls would use now for a volume of n_vox voxels (the default when none is cached). */
+SAL_API sal_status sal_autotune_query(int32_t L, int32_t precision, int64_t n_vox, sal_tile_choice *out);
+/* Saves / loads the cache as text; a malformed file is refused (SAL_ERR_INVALID_ARG) and
+ * leaves the cache unchanged.  clear empties it. */
+SAL_API sal_status sal_autotune_save(const char *path);
+SAL_API sal_status sal_autotune_load(const char *path);
+SAL_API sal_status sal_autotune_clear(void);
 
 /* Static text for a status code. */
 SAL_API const char *sal_status_string(sal_status s);

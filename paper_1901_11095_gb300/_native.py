@@ -19,6 +19,7 @@ SAL_BND_REFLECT, SAL_BND_PERIODIC = 0, 1
 SAL_STENCIL_26, SAL_STENCIL_LINE = 0, 1
 SAL_STATS_LEN = 9
 SAL_DCS_STATIC_MAX_TILES = 131072
+SAL_BATCH_MAX = 128
 
 
 class SalDims(ctypes.Structure):
@@ -29,6 +30,17 @@ class SalParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("boundary", ctypes.c_int32),
                 ("stencil", ctypes.c_int32), ("sigma", ctypes.c_float), ("reserved", ctypes.c_int32),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class SalVolume(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_void_p), ("S", ctypes.c_void_p), ("T", ctypes.c_int64), ("X", ctypes.c_int64),
+                ("Y", ctypes.c_int64)]
+
+
+class SalTileChoice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("size_class", ctypes.c_int32),
+                ("shape", ctypes.c_int32), ("bt", ctypes.c_int32), ("bx", ctypes.c_int32), ("by", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 class SalError(RuntimeError):
@@ -60,6 +72,19 @@ def lib():
             "sal_directional_compare_static": [vp, SalDims, pp, vp, vp, vp],
             "sal_combine": [vp, vp, SalDims, pp, vp, vp],
             "sal_saliency": [vp, SalDims, pp, vp, vp, vp, sz, vp],
+            "sal_batch_workspace_size": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, ctypes.POINTER(sz)],
+            "sal_saliency_batched": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, vp, vp, sz, vp],
+            "sal_graph_create_batched": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, vp, vp, sz, vp,
+                                         ctypes.POINTER(vp)],
+            "sal_graph_launch": [vp, vp],
+            "sal_graph_destroy": [vp],
+            "sal_autotune": [vp, SalDims, pp, vp, vp, ctypes.POINTER(SalTileChoice)],
+            "sal_autotune_batched": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, vp, sz, vp,
+                                     ctypes.POINTER(SalTileChoice)],
+            "sal_autotune_query": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(SalTileChoice)],
+            "sal_autotune_save": [ctypes.c_char_p],
+            "sal_autotune_load": [ctypes.c_char_p],
+            "sal_autotune_clear": [],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -82,5 +107,7 @@ def check(status: int) -> None:
 def exported_symbols() -> list[str]:
     return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
             "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_directional_compare_static",
-            "sal_combine", "sal_saliency",
-            "sal_status_string", "sal_last_error"]
+            "sal_combine", "sal_saliency", "sal_batch_workspace_size", "sal_saliency_batched",
+            "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",
+            "sal_autotune_batched", "sal_autotune_query", "sal_autotune_save", "sal_autotune_load",
+            "sal_autotune_clear", "sal_status_string", "sal_last_error"]

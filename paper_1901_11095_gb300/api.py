@@ -11,7 +11,7 @@ import ctypes
 import torch
 
 from . import _native as N
-from ._native import SalDims, SalParams, check
+from ._native import SalDims, SalParams, SalTileChoice, SalVolume, check
 
 _PREC = {"fp32": N.SAL_PREC_FP32, "tf32": N.SAL_PREC_TF32, "bf16": N.SAL_PREC_BF16}
 _BND = {"reflect": N.SAL_BND_REFLECT, "periodic": N.SAL_BND_PERIODIC}
@@ -157,3 +157,118 @@ def sal_saliency(V: torch.Tensor, p: SalParams, S: torch.Tensor | None = None, s
     check(N.lib().sal_saliency(_dev(V, name="V"), dims, ctypes.byref(p), _dev(S, name="S"), sp,
                                _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
     return S, stats
+
+
+def _volumes(Vs, Ss):
+    arr = (SalVolume * len(Vs))()
+    for i, (V, S) in enumerate(zip(Vs, Ss)):
+        arr[i] = SalVolume(_dev(V, name="V"), _dev(S, name="S"), *[int(v) for v in V.shape])
+    return arr
+
+
+def _shape_volumes(shapes):
+    arr = (SalVolume * len(shapes))()
+    for i, sh in enumerate(shapes):
+        arr[i] = SalVolume(None, None, *[int(v) for v in sh])
+    return arr
+
+
+def sal_batch_workspace_size(shapes, p: SalParams) -> int:
+    """Workspace bytes of a batch of volumes with these [T, X, Y] shapes."""
+    n = ctypes.c_size_t()
+    check(N.lib().sal_batch_workspace_size(_shape_volumes(shapes), len(shapes), ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_saliency_batched(Vs, p: SalParams, Ss=None, stats: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None):
+    """The whole method on a list of volumes, each stage one persistent launch.  Returns (Ss, stats)."""
+    if Ss is None:
+        Ss = [torch.empty_like(V) for V in Vs]
+    if ws is None:
+        ws = torch.empty(sal_batch_workspace_size([V.shape for V in Vs], p), device=Vs[0].device, dtype=torch.uint8)
+    sp = _dev(stats, torch.float64, "stats") if stats is not None else None
+    check(N.lib().sal_saliency_batched(_volumes(Vs, Ss), len(Vs), ctypes.byref(p), sp, _dev(ws, torch.uint8, "ws"),
+                                       ws.numel(), _stream(stream)))
+    return Ss, stats
+
+
+class SalGraph:
+    """A batch captured once into a CUDA graph by the library (sal_graph_create_batched);
+    launch() replays it.  Holds references to every buffer the graph uses."""
+
+    def __init__(self, Vs, p: SalParams, Ss=None, stats: torch.Tensor | None = None,
+                 ws: torch.Tensor | None = None, stream=None):
+        self.Vs = list(Vs)
+        self.Ss = Ss if Ss is not None else [torch.empty_like(V) for V in self.Vs]
+        self.stats = stats
+        self.ws = ws if ws is not None else torch.empty(sal_batch_workspace_size([V.shape for V in self.Vs], p),
+                                                        device=self.Vs[0].device, dtype=torch.uint8)
+        self.p = p
+        h = ctypes.c_void_p()
+        sp = _dev(stats, torch.float64, "stats") if stats is not None else None
+        check(N.lib().sal_graph_create_batched(_volumes(self.Vs, self.Ss), len(self.Vs), ctypes.byref(p), sp,
+                                               _dev(self.ws, torch.uint8, "ws"), self.ws.numel(), _stream(stream),
+                                               ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        check(N.lib().sal_graph_launch(self._h, _stream(stream)))
+        return self.Ss
+
+    def close(self):
+        if self._h:
+            check(N.lib().sal_graph_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sal_graph_create_batched(Vs, p: SalParams, **kw) -> SalGraph:
+    return SalGraph(Vs, p, **kw)
+
+
+def _choice(c: SalTileChoice) -> dict:
+    return {k: getattr(c, k) for k, _ in SalTileChoice._fields_}
+
+
+def sal_autotune(V: torch.Tensor, p: SalParams, E: torch.Tensor | None = None, stream=None) -> dict:
+    """Times the candidate tile shapes on V, caches and returns the fastest."""
+    if E is None:
+        E = torch.empty((3,) + tuple(V.shape), device=V.device, dtype=torch.float32)
+    c = SalTileChoice()
+    check(N.lib().sal_autotune(_dev(V, name="V"), dims_of(V), ctypes.byref(p), _dev(E, name="E"), _stream(stream),
+                               ctypes.byref(c)))
+    return _choice(c)
+
+
+def sal_autotune_batched(Vs, p: SalParams, ws: torch.Tensor | None = None, stream=None) -> dict:
+    Ss = [torch.empty_like(V) for V in Vs]
+    if ws is None:
+        ws = torch.empty(sal_batch_workspace_size([V.shape for V in Vs], p), device=Vs[0].device, dtype=torch.uint8)
+    c = SalTileChoice()
+    check(N.lib().sal_autotune_batched(_volumes(Vs, Ss), len(Vs), ctypes.byref(p), _dev(ws, torch.uint8, "ws"),
+                                       ws.numel(), _stream(stream), ctypes.byref(c)))
+    return _choice(c)
+
+
+def sal_autotune_query(L: int, precision: int, n_vox: int) -> dict:
+    c = SalTileChoice()
+    check(N.lib().sal_autotune_query(int(L), int(precision), int(n_vox), ctypes.byref(c)))
+    return _choice(c)
+
+
+def sal_autotune_save(path: str) -> None:
+    check(N.lib().sal_autotune_save(str(path).encode()))
+
+
+def sal_autotune_load(path: str) -> None:
+    check(N.lib().sal_autotune_load(str(path).encode()))
+
+
+def sal_autotune_clear() -> None:
+    check(N.lib().sal_autotune_clear())

@@ -137,6 +137,7 @@ __device__ __forceinline__ void dcs26(const float *sE, const Halo &hl, int tq, i
 {
     // halo indices: plane 4tq + p, row x + b, column 4yq + c (c = 0..5) at storage + off
     const float *base = sE + (QT * tq) * hl.PP + x * hl.pitch + hl.off + QY * yq;
+    const float g[4] = {0.f, k.g[1], k.g[2], k.g[3]};
     float cen[QT][QY];
 #pragma unroll
     for (int to = 0; to < QT; ++to) {
@@ -167,7 +168,7 @@ __device__ __forceinline__ void dcs26(const float *sE, const Halo &hl, int tq, i
                     for (int cc = -1; cc <= 1; ++cc) {
                         const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
                         if (d2 == 0) continue;
-                        out[to][yo] += fabsf(fmaf(-k.g[d2], w[yo + 1 + cc], cen[to][yo]));
+                        out[to][yo] += fabsf(fmaf(-g[d2], w[yo + 1 + cc], cen[to][yo]));
                     }
             }
         }
@@ -194,16 +195,13 @@ __device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m,
         }
 }
 
+// One map m of one output tile of one volume; writes the tile's (min, max, sum) record.
 template <int STENCIL>
-__global__ void __launch_bounds__(DNT) dcs_kernel(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y,
-                                                  int bnd, int tiles_x, int tiles_y, float *__restrict__ Sm,
-                                                  double *__restrict__ partials, int64_t nparts,
-                                                  const __grid_constant__ DcsConsts k)
+__device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y, int bnd,
+                                         int m, int64_t tile, int tiles_x, int tiles_y, float *__restrict__ Sm,
+                                         double *__restrict__ partials, int64_t nparts, const DcsConsts &k, float *sE,
+                                         double (*red)[3])
 {
-    extern __shared__ __align__(16) float sE[];
-    __shared__ double red[DNT / 32][3];
-    const int m = blockIdx.y;
-    const int64_t tile = blockIdx.x;
     const int ty = (int)(tile % tiles_y);
     const int tx = (int)((tile / tiles_y) % tiles_x);
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
@@ -269,7 +267,43 @@ __global__ void __launch_bounds__(DNT) dcs_kernel(const float *__restrict__ E, i
             const double u = red[w][q];
             v = q == 0 ? fmin(v, u) : (q == 1 ? fmax(v, u) : v + u);
         }
-        partials[(3 * m + q) * nparts + blockIdx.x] = v;
+        partials[(3 * m + q) * nparts + tile] = v;
+    }
+}
+
+// Volumes of one launch; work item k of the launch is (volume, map, tile), map-major
+// within each volume.
+struct DVol {
+    const float *E;
+    float *Sm;
+    double *part;          // [9][tiles] records of this volume
+    int64_t T, X, Y;
+    int64_t item0, tiles;
+    int tiles_x, tiles_y;
+};
+struct DBatch {
+    int n, bnd;
+    int64_t total;
+    DVol v[kMaxBatch];
+};
+
+template <int STENCIL>
+__global__ void __launch_bounds__(DNT) dcs_kernel(const __grid_constant__ DBatch bt, const __grid_constant__ DcsConsts k)
+{
+    extern __shared__ __align__(16) float sE[];
+    __shared__ double red[DNT / 32][3];
+    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
+        int lo = 0, hi = bt.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        const DVol &v = bt.v[lo];
+        const int64_t local = it - v.item0;
+        const int m = (int)(local / v.tiles);
+        dcs_tile<STENCIL>(v.E, v.T, v.X, v.Y, bt.bnd, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm, v.part,
+                          v.tiles, k, sE, red);
+        __syncthreads();
     }
 }
 
@@ -353,13 +387,8 @@ int64_t dcs_num_partials(sal_dims d)
     return nt * nx * ny + kRedBlocks;   // per-tile records, then the first reduction pass
 }
 
-cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials, double *stats,
-                       cudaStream_t s)
+DcsConsts dcs_consts(const sal_params *p)
 {
-    int64_t nt, nx, ny;
-    dcs_tiles(d, &nt, &nx, &ny);
-    const int64_t tiles = nt * nx * ny;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     DcsConsts k;
     const double s2 = 2.0 * (double)p->sigma * (double)p->sigma;
     for (int i = 0; i < 4; ++i) k.g[i] = (float)exp(-(double)i / s2);
@@ -367,25 +396,74 @@ cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *S
     for (int i = 0; i <= kMaxH; ++i) k.gl[i] = (float)exp(-(double)(i * i) / s2);
     k.h = h;
     k.invQ = (float)(1.0 / (p->stencil == SAL_STENCIL_26 ? 26.0 : (double)(2 * h)));
+    return k;
+}
+
+// Launches the compare over n volumes (persistent grid when batched).
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    DBatch bt;
+    bt.n = n;
+    bt.bnd = p->boundary;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        DVol &v = bt.v[i];
+        int64_t nt, nx, ny;
+        const sal_dims d{vols[i].T, vols[i].X, vols[i].Y};
+        dcs_tiles(d, &nt, &nx, &ny);
+        v.E = vols[i].E;
+        v.Sm = vols[i].Sm;
+        v.part = vols[i].part;
+        v.T = d.T;
+        v.X = d.X;
+        v.Y = d.Y;
+        v.tiles = nt * nx * ny;
+        v.tiles_x = (int)nx;
+        v.tiles_y = (int)ny;
+        v.item0 = total;
+        total += 3 * v.tiles;
+    }
+    bt.total = total;
+    const DcsConsts k = dcs_consts(p);
+    const int h = (p->L - 1) / 2;
     int smem = 0;
     for (int m = 0; m < 3; ++m) {
         const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
         smem = f > smem ? f : smem;
     }
-    const dim3 grid((unsigned)tiles, 3);
-    cudaError_t e;
-    if (p->stencil == SAL_STENCIL_26) {
-        e = cudaFuncSetAttribute(dcs_kernel<SAL_STENCIL_26>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void *fn = p->stencil == SAL_STENCIL_26 ? (const void *)dcs_kernel<SAL_STENCIL_26>
+                                                  : (const void *)dcs_kernel<SAL_STENCIL_LINE>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = total;
+    if (persistent) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DNT, smem);
         if (e != cudaSuccess) return e;
-        dcs_kernel<SAL_STENCIL_26><<<grid, DNT, smem, s>>>(E, d.T, d.X, d.Y, p->boundary, (int)nx, (int)ny, Sm, partials,
-                                                          tiles, k);
-    } else {
-        e = cudaFuncSetAttribute(dcs_kernel<SAL_STENCIL_LINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        dcs_kernel<SAL_STENCIL_LINE><<<grid, DNT, smem, s>>>(E, d.T, d.X, d.Y, p->boundary, (int)nx, (int)ny, Sm,
-                                                            partials, tiles, k);
+        const int64_t resident = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+        if (grid > resident) grid = resident;
     }
-    e = cudaGetLastError();
+    if (grid <= 0) return cudaSuccess;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (p->stencil == SAL_STENCIL_26)
+        dcs_kernel<SAL_STENCIL_26><<<(unsigned)grid, DNT, smem, s>>>(bt, k);
+    else
+        dcs_kernel<SAL_STENCIL_LINE><<<(unsigned)grid, DNT, smem, s>>>(bt, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials, double *stats,
+                       cudaStream_t s)
+{
+    int64_t nt, nx, ny;
+    dcs_tiles(d, &nt, &nx, &ny);
+    const int64_t tiles = nt * nx * ny;
+    if (3 * tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    DVolDesc v{E, Sm, partials, d.T, d.X, d.Y};
+    cudaError_t e = launch_dcs_items(&v, 1, p, false, s);
     if (e != cudaSuccess) return e;
     double *second = partials + 9 * tiles;
     reduce_partials_kernel<<<kRedBlocks, 256, 0, s>>>(partials, tiles, second, kRedBlocks);
@@ -394,6 +472,7 @@ cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *S
     reduce_partials_kernel<<<1, 256, 0, s>>>(second, kRedBlocks, stats, 1);
     return cudaGetLastError();
 }
+
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s)
 {

@@ -1,28 +1,75 @@
-// Dispatch of the FP32 spectral-energy kernel on the cube side L.
+// Dispatch of the FP32 spectral-energy kernel on the cube side L and the tile shape.
 #include "sal_internal.cuh"
 
 namespace sal {
 
-cudaError_t launch_energy_fp32_l3(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l5(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l7(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l9(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l11(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l13(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
-cudaError_t launch_energy_fp32_l15(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_l3(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l5(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l7(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l9(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l11(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l13(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+cudaError_t launch_energy_fp32_l15(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s);
+
+namespace {
+struct ShapeList {
+    int L;
+    TileShape s[3];
+};
+// Candidate tile shapes (BT x BX x BY output voxels per CTA) per cube side; index 0 is the
+// default when the autotuner has not chosen.
+const ShapeList kShapes[] = {
+    {3, {{2, 8, 32}, {4, 8, 32}, {1, 16, 32}}},
+    {5, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
+    {7, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
+    {9, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
+    {11, {{1, 8, 32}, {1, 16, 32}}},
+    {13, {{1, 8, 32}, {1, 16, 32}}},
+    {15, {{1, 8, 32}, {1, 16, 32}}},
+};
+const ShapeList *shapes_of(int L)
+{
+    for (const ShapeList &s : kShapes)
+        if (s.L == L) return &s;
+    return nullptr;
+}
+}  // namespace
+
+int energy_num_shapes(int L)
+{
+    const ShapeList *s = shapes_of(L);
+    if (!s) return 0;
+    int n = 0;
+    while (n < 3 && s->s[n].bt > 0) ++n;
+    return n;
+}
+
+TileShape energy_shape(int L, int idx)
+{
+    const ShapeList *s = shapes_of(L);
+    if (!s || idx < 0 || idx >= energy_num_shapes(L)) return TileShape{0, 0, 0};
+    return s->s[idx];
+}
+
+cudaError_t launch_energy_fp32_batch(const EVolDesc *vols, int n, int L, int bnd, int shape, bool persistent,
+                                     cudaStream_t s)
+{
+    switch (L) {
+        case 3: return launch_energy_fp32_l3(vols, n, bnd, shape, persistent, s);
+        case 5: return launch_energy_fp32_l5(vols, n, bnd, shape, persistent, s);
+        case 7: return launch_energy_fp32_l7(vols, n, bnd, shape, persistent, s);
+        case 9: return launch_energy_fp32_l9(vols, n, bnd, shape, persistent, s);
+        case 11: return launch_energy_fp32_l11(vols, n, bnd, shape, persistent, s);
+        case 13: return launch_energy_fp32_l13(vols, n, bnd, shape, persistent, s);
+        case 15: return launch_energy_fp32_l15(vols, n, bnd, shape, persistent, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_energy_fp32(const float *V, sal_dims d, int L, int bnd, float *E, cudaStream_t s)
 {
-    switch (L) {
-        case 3: return launch_energy_fp32_l3(V, d, bnd, E, s);
-        case 5: return launch_energy_fp32_l5(V, d, bnd, E, s);
-        case 7: return launch_energy_fp32_l7(V, d, bnd, E, s);
-        case 9: return launch_energy_fp32_l9(V, d, bnd, E, s);
-        case 11: return launch_energy_fp32_l11(V, d, bnd, E, s);
-        case 13: return launch_energy_fp32_l13(V, d, bnd, E, s);
-        case 15: return launch_energy_fp32_l15(V, d, bnd, E, s);
-        default: return cudaErrorInvalidValue;
-    }
+    EVolDesc v{V, E, d.T, d.X, d.Y};
+    return launch_energy_fp32_batch(&v, 1, L, bnd, 0, false, s);
 }
 
 }  // namespace sal

@@ -346,19 +346,17 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, c
     }
 }
 
+// One output tile of one volume.  Every thread of the CTA calls it with the same tile.
 template <class G>
-__global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restrict__ V, int64_t T, int64_t X,
-                                                            int64_t Y, int bnd, int tiles_x, int tiles_y,
-                                                            float *__restrict__ E,
-                                                            const __grid_constant__ SpecTables tb)
+__device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                            int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
+                                            const SpecTables &tb, float *smem)
 {
     constexpr int L = G::L, H = G::H, PY = G::PY;
-    extern __shared__ __align__(16) float smem[];
     float *sG1 = smem;
     float2 *sG2 = reinterpret_cast<float2 *>(smem + G::NG1);
     float *sV = smem + G::NG1;   // aliases sG2: dead once stage t is done
 
-    const int64_t tile = blockIdx.x;
     const int ty = (int)(tile % tiles_y);
     const int tx = (int)((tile / tiles_y) % tiles_x);
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
@@ -444,7 +442,7 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
 
     const int t = row / G::BX, x = row - t * G::BX;
     const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + G::R * j;
-    if (gt >= T || gx >= X) return;
+    if (gt >= T || gx >= X) return;   // the last barrier of the tile is behind every thread
     const int64_t N = T * X * Y;
     float *e0 = E + (gt * X + gx) * Y + gy;
     const float sc = tb.escale;
@@ -464,22 +462,87 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const float *__restr
     }
 }
 
+// Volumes of one launch: a single volume, or a batch of uneven volumes walked by a
+// persistent grid (tile k of the launch belongs to the volume whose tile0 range holds it).
+struct EVol {
+    const float *V;
+    float *E;
+    int64_t T, X, Y;
+    int64_t tile0;
+    int tiles_x, tiles_y;
+};
+struct EBatch {
+    int n, bnd;
+    int64_t total;
+    EVol v[kMaxBatch];
+};
+
 template <class G>
-cudaError_t launch_energy_impl(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s)
+__global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const __grid_constant__ EBatch bt,
+                                                            const __grid_constant__ SpecTables tb)
+{
+    extern __shared__ __align__(16) float smem[];
+    for (int64_t k = blockIdx.x; k < bt.total; k += gridDim.x) {
+        int lo = 0, hi = bt.n - 1;      // last volume whose first tile is <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bt.v[mid].tile0 <= k) lo = mid; else hi = mid - 1;
+        }
+        const EVol &v = bt.v[lo];
+        energy_tile<G>(v.V, v.T, v.X, v.Y, bt.bnd, k - v.tile0, v.tiles_x, v.tiles_y, v.E, tb, smem);
+        __syncthreads();
+    }
+}
+
+template <class G>
+int64_t energy_tiles(int64_t T, int64_t X, int64_t Y, int *tx, int *ty)
+{
+    const int64_t nt = (T + G::BT - 1) / G::BT, nx = (X + G::BX - 1) / G::BX, ny = (Y + G::BY - 1) / G::BY;
+    *tx = (int)nx;
+    *ty = (int)ny;
+    return nt * nx * ny;
+}
+
+// Launches over `n` volumes.  persistent: grid = resident CTAs of the whole GPU (walks all
+// tiles); otherwise one CTA per tile.
+template <class G>
+cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persistent, cudaStream_t s)
 {
     static_assert(G::R == 4, "four outputs per thread along y");
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     SpecTables tb;
     make_tables(G::L, &tb);
-    const int64_t nt = (d.T + G::BT - 1) / G::BT;
-    const int64_t nx = (d.X + G::BX - 1) / G::BX;
-    const int64_t ny = (d.Y + G::BY - 1) / G::BY;
-    const int64_t tiles = nt * nx * ny;
-    if (tiles <= 0) return cudaSuccess;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    EBatch bt;
+    bt.n = n;
+    bt.bnd = bnd;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        EVol &v = bt.v[i];
+        v.V = vols[i].V;
+        v.E = vols[i].E;
+        v.T = vols[i].T;
+        v.X = vols[i].X;
+        v.Y = vols[i].Y;
+        v.tile0 = total;
+        total += energy_tiles<G>(v.T, v.X, v.Y, &v.tiles_x, &v.tiles_y);
+    }
+    bt.total = total;
+    if (total <= 0) return cudaSuccess;
     auto kern = energy_fp32_kernel<G>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)tiles, G::NT, G::SMEM, s>>>(V, d.T, d.X, d.Y, bnd, (int)nx, (int)ny, E, tb);
+    int64_t grid = total;
+    if (persistent) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, G::SMEM);
+        if (e != cudaSuccess) return e;
+        const int64_t resident = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+        if (grid > resident) grid = resident;
+    }
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)grid, G::NT, G::SMEM, s>>>(bt, tb);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,17 @@
-// FP32 spectral-energy kernel instantiated for L = 9 (one translation unit per cube size).
+// FP32 spectral-energy kernel instantiated for L = 9, one kernel per candidate tile shape
+// (one translation unit per cube size).
 #include "energy_fp32.cuh"
 
 namespace sal {
 
-cudaError_t launch_energy_fp32_l9(const float *V, sal_dims d, int bnd, float *E, cudaStream_t s)
+cudaError_t launch_energy_fp32_l9(const EVolDesc *vols, int n, int bnd, int shape, bool persistent, cudaStream_t s)
 {
-    return energy_detail::launch_energy_impl<energy_detail::EGeo<9, 2, 8>>(V, d, bnd, E, s);
+    switch (shape) {
+        case 0: return energy_detail::launch_energy_impl<energy_detail::EGeo<9, 2, 8>>(vols, n, bnd, persistent, s);
+        case 1: return energy_detail::launch_energy_impl<energy_detail::EGeo<9, 1, 16>>(vols, n, bnd, persistent, s);
+        case 2: return energy_detail::launch_energy_impl<energy_detail::EGeo<9, 1, 8>>(vols, n, bnd, persistent, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace sal

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <new>
+
 #include "sal_internal.cuh"
 
 namespace sal {
@@ -121,8 +123,92 @@ sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, floa
 {
     if (p->precision != SAL_PREC_FP32)
         return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available in this build", p->precision);
-    cudaError_t e = sal::launch_energy_fp32(V, d, p->L, p->boundary, E, s);
+    const int shape = sal::autotune_lookup(p->L, p->precision, sal::size_class_of(d.T * d.X * d.Y));
+    sal::EVolDesc v{V, E, d.T, d.X, d.Y};
+    cudaError_t e = sal::launch_energy_fp32_batch(&v, 1, p->L, p->boundary, shape, false, s);
     return e == cudaSuccess ? SAL_OK : cuda_fail(e, "spectral energy launch");
+}
+
+// Workspace layout of a batch: per volume E [3N] floats, S_m [3N] floats and its [9][tiles]
+// reduction records, each 256-byte aligned; then n * 9 statistics.
+struct BatchLayout {
+    size_t E[SAL_BATCH_MAX], Sm[SAL_BATCH_MAX], part[SAL_BATCH_MAX], stats, total;
+};
+
+sal_status check_batch(const sal_volume *vols, int32_t n, const sal_params *p, bool need_ptrs)
+{
+    if (!vols) return fail(SAL_ERR_INVALID_ARG, "vols is NULL");
+    if (n < 1 || n > SAL_BATCH_MAX) return fail(SAL_ERR_INVALID_ARG, "batch size must be in [1, %d]", SAL_BATCH_MAX);
+    sal_status s = check_params(p);
+    if (s) return s;
+    if (p->precision != SAL_PREC_FP32)
+        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for batches in this build", p->precision);
+    for (int i = 0; i < n; ++i) {
+        s = check_dims(sal_dims{vols[i].T, vols[i].X, vols[i].Y});
+        if (s) return s;
+        if (need_ptrs && (!vols[i].V || !vols[i].S)) return fail(SAL_ERR_INVALID_ARG, "volume %d: NULL pointer", i);
+        if (need_ptrs && (!aligned16(vols[i].V) || !aligned16(vols[i].S)))
+            return fail(SAL_ERR_INVALID_ARG, "volume %d: pointers must be 16-byte aligned", i);
+    }
+    return SAL_OK;
+}
+
+BatchLayout batch_layout(const sal_volume *vols, int32_t n)
+{
+    BatchLayout b;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t N = (size_t)(vols[i].T * vols[i].X * vols[i].Y);
+        b.E[i] = off;
+        b.Sm[i] = round256(off + 3 * N * sizeof(float));
+        b.part[i] = round256(b.Sm[i] + 3 * N * sizeof(float));
+        off = round256(b.part[i] + 9 * (size_t)sal::dcs_num_tiles(sal_dims{vols[i].T, vols[i].X, vols[i].Y}) * sizeof(double));
+    }
+    b.stats = off;
+    b.total = round256(off + 9 * (size_t)n * sizeof(double));
+    return b;
+}
+
+void energy_descs(const sal_volume *vols, int32_t n, const BatchLayout &b, char *base, sal::EVolDesc *ev)
+{
+    for (int i = 0; i < n; ++i) ev[i] = sal::EVolDesc{vols[i].V, (float *)(base + b.E[i]), vols[i].T, vols[i].X, vols[i].Y};
+}
+
+int batch_shape(const sal_volume *vols, int32_t n, const sal_params *p)
+{
+    int64_t nmax = 0;
+    for (int i = 0; i < n; ++i) nmax = vols[i].T * vols[i].X * vols[i].Y > nmax ? vols[i].T * vols[i].X * vols[i].Y : nmax;
+    return sal::autotune_lookup(p->L, p->precision, sal::size_class_of(nmax));
+}
+
+// Enqueues the four launches of a batch on `s`.
+sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p, double *stats, char *base,
+                         const BatchLayout &b, cudaStream_t s)
+{
+    sal::EVolDesc ev[SAL_BATCH_MAX];
+    sal::DVolDesc dv[SAL_BATCH_MAX];
+    sal::BatchVolDesc bv[SAL_BATCH_MAX];
+    energy_descs(vols, n, b, base, ev);
+    for (int i = 0; i < n; ++i) {
+        float *Sm = (float *)(base + b.Sm[i]);
+        double *part = (double *)(base + b.part[i]);
+        dv[i] = sal::DVolDesc{ev[i].E, Sm, part, vols[i].T, vols[i].X, vols[i].Y};
+        bv[i] = sal::BatchVolDesc{Sm, vols[i].S, part, sal::dcs_num_tiles(sal_dims{vols[i].T, vols[i].X, vols[i].Y}),
+                                  vols[i].T * vols[i].X * vols[i].Y};
+    }
+    cudaError_t e = sal::launch_energy_fp32_batch(ev, n, p->L, p->boundary, batch_shape(vols, n, p), true, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched spectral energy launch");
+    e = sal::launch_dcs_items(dv, n, p, true, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched directional compare launch");
+    e = sal::launch_batch_stats_combine(bv, n, p, stats ? stats : (double *)(base + b.stats), s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched statistics / combine launch");
+    return SAL_OK;
+}
+
+sal_tile_choice choice_of(int L, int precision, int cls, int shape, float ms)
+{
+    const sal::TileShape t = sal::energy_shape(L, shape);
+    return sal_tile_choice{L, precision, cls, shape, t.bt, t.bx, t.by, ms};
 }
 
 }  // namespace
@@ -271,6 +357,183 @@ sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, floa
     if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");
     e = sal::launch_combine(Sm, st, dims, p, S, cs);
     if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+    return ok();
+}
+
+sal_status sal_batch_workspace_size(const sal_volume *vols, int32_t n, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_batch(vols, n, p, false);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = batch_layout(vols, n).total;
+    return ok();
+}
+
+sal_status sal_saliency_batched(const sal_volume *vols, int32_t n, const sal_params *p, double *stats, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    sal_status s = check_batch(vols, n, p, true);
+    if (s) return s;
+    if (!ws || !aligned16(ws) || (stats && !aligned16(stats)))
+        return fail(SAL_ERR_INVALID_ARG, "ws must be non-NULL and 16-byte aligned (stats too)");
+    const BatchLayout b = batch_layout(vols, n);
+    if (ws_bytes < b.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, b.total);
+    s = enqueue_batch(vols, n, p, stats, (char *)ws, b, (cudaStream_t)stream);
+    return s ? s : ok();
+}
+
+}  // extern "C"
+
+struct sal_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+sal_status sal_graph_create_batched(const sal_volume *vols, int32_t n, const sal_params *p, double *stats, void *ws,
+                                    size_t ws_bytes, void *stream, sal_graph **out)
+{
+    sal_status s = check_batch(vols, n, p, true);
+    if (s) return s;
+    if (!out) return fail(SAL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ws || !aligned16(ws) || (stats && !aligned16(stats)))
+        return fail(SAL_ERR_INVALID_ARG, "ws must be non-NULL and 16-byte aligned (stats too)");
+    const BatchLayout b = batch_layout(vols, n);
+    if (ws_bytes < b.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, b.total);
+    char *base = (char *)ws;
+    int64_t nmax = 0;
+    for (int i = 0; i < n; ++i) nmax = vols[i].T * vols[i].X * vols[i].Y > nmax ? vols[i].T * vols[i].X * vols[i].Y : nmax;
+    const int cls = sal::size_class_of(nmax);
+    cudaError_t e = cudaSuccess;
+    // first use for this (L, precision, size class): choose the tile shape on this batch
+    float cached_ms = 0.f;
+    if (!sal::autotune_get_ms(p->L, p->precision, cls, &cached_ms)) {
+        sal::EVolDesc ev[SAL_BATCH_MAX];
+        energy_descs(vols, n, b, base, ev);
+        int best = 0;
+        float ms = 0.f;
+        e = sal::autotune_run(ev, n, p->L, p->boundary, p->precision, (cudaStream_t)stream, &best, &ms);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune before capture");
+    }
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_fail(e, "begin capture");
+    }
+    s = enqueue_batch(vols, n, p, stats, base, b, cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (s) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "graph instantiate");
+    }
+    sal_graph *g = new (std::nothrow) sal_graph{graph, exec};
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(SAL_ERR_INTERNAL, "out of host memory");
+    }
+    *out = g;
+    return ok();
+}
+
+sal_status sal_graph_launch(sal_graph *g, void *stream)
+{
+    if (!g) return fail(SAL_ERR_INVALID_ARG, "graph is NULL");
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "graph launch");
+}
+
+sal_status sal_graph_destroy(sal_graph *g)
+{
+    if (!g) return ok();
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return ok();
+}
+
+sal_status sal_autotune(const float *V, sal_dims dims, const sal_params *p, float *E, void *stream, sal_tile_choice *out)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !E || !out) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    if (p->precision != SAL_PREC_FP32) return fail(SAL_ERR_UNSUPPORTED, "precision %d is not tunable in this build", p->precision);
+    sal::EVolDesc v{V, E, dims.T, dims.X, dims.Y};
+    int best = 0;
+    float ms = 0.f;
+    cudaError_t e = sal::autotune_run(&v, 1, p->L, p->boundary, p->precision, (cudaStream_t)stream, &best, &ms);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    *out = choice_of(p->L, p->precision, sal::size_class_of(dims.T * dims.X * dims.Y), best, ms);
+    return ok();
+}
+
+sal_status sal_autotune_batched(const sal_volume *vols, int32_t n, const sal_params *p, void *ws, size_t ws_bytes,
+                                void *stream, sal_tile_choice *out)
+{
+    sal_status s = check_batch(vols, n, p, true);
+    if (s) return s;
+    if (!ws || !out || !aligned16(ws)) return fail(SAL_ERR_INVALID_ARG, "ws and out must be non-NULL (ws 16-byte aligned)");
+    const BatchLayout b = batch_layout(vols, n);
+    if (ws_bytes < b.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, b.total);
+    sal::EVolDesc ev[SAL_BATCH_MAX];
+    energy_descs(vols, n, b, (char *)ws, ev);
+    int best = 0;
+    float ms = 0.f;
+    cudaError_t e = sal::autotune_run(ev, n, p->L, p->boundary, p->precision, (cudaStream_t)stream, &best, &ms);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    int64_t nmax = 0;
+    for (int i = 0; i < n; ++i) nmax = vols[i].T * vols[i].X * vols[i].Y > nmax ? vols[i].T * vols[i].X * vols[i].Y : nmax;
+    *out = choice_of(p->L, p->precision, sal::size_class_of(nmax), best, ms);
+    return ok();
+}
+
+sal_status sal_autotune_query(int32_t L, int32_t precision, int64_t n_vox, sal_tile_choice *out)
+{
+    sal_status s = check_L(L);
+    if (s) return s;
+    if (!out || precision < 0 || precision > 2 || n_vox < 0) return fail(SAL_ERR_INVALID_ARG, "bad argument");
+    const int cls = sal::size_class_of(n_vox);
+    const int shape = sal::autotune_lookup(L, precision, cls);
+    float ms = 0.f;
+    sal::autotune_get_ms(L, precision, cls, &ms);
+    *out = choice_of(L, precision, cls, shape, ms);
+    return ok();
+}
+
+sal_status sal_autotune_save(const char *path)
+{
+    if (!path) return fail(SAL_ERR_INVALID_ARG, "path is NULL");
+    return sal::autotune_save(path) == 0 ? ok() : fail(SAL_ERR_INVALID_ARG, "cannot write %s", path);
+}
+
+sal_status sal_autotune_load(const char *path)
+{
+    if (!path) return fail(SAL_ERR_INVALID_ARG, "path is NULL");
+    const int r = sal::autotune_load(path);
+    if (r == -1) return fail(SAL_ERR_INVALID_ARG, "cannot read %s", path);
+    if (r < 0) return fail(SAL_ERR_INVALID_ARG, "malformed autotune cache %s (nothing loaded)", path);
+    return ok();
+}
+
+sal_status sal_autotune_clear(void)
+{
+    sal::autotune_clear();
     return ok();
 }
 

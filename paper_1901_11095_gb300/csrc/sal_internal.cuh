@@ -29,26 +29,59 @@ struct SpecTables {
 void make_tables(int L, SpecTables *t);
 
 // Boundary extension of one coordinate onto 0..n-1 (REFLECT: whole-sample symmetric,
-// edge not repeated; PERIODIC: wrap).  Valid for any integer i.
+// edge not repeated; PERIODIC: wrap).  Valid for any integer i; coordinates at most one
+// reflection or wrap away take a division-free path.
 __host__ __device__ __forceinline__ int64_t ext_index(int64_t i, int64_t n, int bnd)
 {
     if (i >= 0 && i < n) return i;
     if (bnd == SAL_BND_PERIODIC) {
+        if (i < 0 && i >= -n) return i + n;
+        if (i >= n && i < 2 * n) return i - n;
         int64_t r = i % n;
         return r < 0 ? r + n : r;
     }
     if (n == 1) return 0;
+    if (i < 0 && i > -n) return -i;
+    if (i >= n && i <= 2 * n - 2) return 2 * (n - 1) - i;
     int64_t period = 2 * (n - 1);
     int64_t r = i % period;
     if (r < 0) r += period;
     return r < n ? r : period - r;
 }
 
+constexpr int kMaxBatch = SAL_BATCH_MAX;
+
+// One volume of a (possibly batched) spectral-energy launch.
+struct EVolDesc {
+    const float *V;
+    float *E;
+    int64_t T, X, Y;
+};
+
+// Tile shapes of the spectral-energy kernel that the autotuner chooses among.
+struct TileShape {
+    int bt, bx, by;
+};
+int energy_num_shapes(int L);
+TileShape energy_shape(int L, int idx);
+
 // Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_energy_fp32_batch(const EVolDesc *vols, int n, int L, int bnd, int shape_idx, bool persistent,
+                                     cudaStream_t s);
 cudaError_t launch_energy_fp32(const float *V, sal_dims d, int L, int bnd, float *E, cudaStream_t s);
 cudaError_t launch_local_spectra(const float *V, sal_dims d, int L, int bnd, const int64_t lo[3],
                                  const int64_t ext[3], float *mag, cudaStream_t s);
 cudaError_t launch_project(const float *mag, int64_t n, int L, float *E, cudaStream_t s);
+
+// One volume of a (possibly batched) directional-compare launch; `part` receives the
+// volume's [9][tiles] partial records.
+struct DVolDesc {
+    const float *E;
+    float *Sm;
+    double *part;
+    int64_t T, X, Y;
+};
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s);
 
 // Directional compare: number of per-CTA partial records written to the workspace.
 int64_t dcs_num_partials(sal_dims d);
@@ -57,6 +90,29 @@ cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *S
 // Fixed-scratch variant of the directional compare (no allocation by caller or library).
 int64_t dcs_num_tiles(sal_dims d);
 cudaError_t dcs_static_scratch(double **out);
+// Per-volume statistics and Eq. 6 for a batch (one launch each).
+struct BatchVolDesc {
+    const float *Sm;
+    float *S;
+    const double *part;
+    int64_t tiles, N;
+};
+cudaError_t launch_batch_stats_combine(const BatchVolDesc *vols, int n, const sal_params *p, double *stats,
+                                       cudaStream_t s);
+
+// Autotuner cache of spectral-energy tile shapes, keyed by (L, precision, size class).
+int size_class_of(int64_t n_vox);
+int autotune_lookup(int L, int precision, int size_class);
+bool autotune_get_ms(int L, int precision, int size_class, float *ms);
+void autotune_store(int L, int precision, int size_class, int shape, float ms);
+// Times every candidate shape on the given volumes (batched when n > 1), stores and
+// returns the fastest; synchronises the stream.
+cudaError_t autotune_run(const EVolDesc *vols, int n, int L, int bnd, int precision, cudaStream_t s, int *best,
+                         float *best_ms);
+int autotune_save(const char *path);
+int autotune_load(const char *path);
+void autotune_clear();
+
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s);
 
