@@ -69,7 +69,9 @@ typedef struct { int64_t T, X, Y; } sal_dims;
 
 typedef struct {
     int32_t L;          /* local cube side, odd, 3..15 (Sec. 2: "L defines the size of the local data cube") */
-    int32_t precision;  /* sal_precision of the DFT stage */
+    int32_t precision;  /* sal_precision of the DFT stage: FP32 on the CUDA cores (any L); the
+                           y-stage on the tensor cores with BF16 (any L) or TF32 (L <= 11)
+                           operands and FP32 accumulation; SAL_ERR_UNSUPPORTED otherwise */
     int32_t boundary;   /* sal_boundary */
     int32_t stencil;    /* sal_stencil */
     float sigma;        /* Gaussian width of the Eq. 5 weights, in voxels (> 0) */
@@ -239,6 +241,19 @@ SAL_API sal_status sal_autotune_query(int32_t L, int32_t precision, int64_t n_vo
 SAL_API sal_status sal_autotune_save(const char *path);
 SAL_API sal_status sal_autotune_load(const char *path);
 SAL_API sal_status sal_autotune_clear(void);
+
+/*
+ * Synchronises `stream`, then reads and clears the library's device status word on the
+ * current device: SAL_OK, or SAL_ERR_TIMEOUT when a bounded device-side wait of a
+ * tensor-core kernel (precision TF32 or BF16) ran out since the last call; the outputs of
+ * such a launch are undefined.
+ */
+SAL_API sal_status sal_device_status(void *stream);
+
+/* Test hook: while on, the tensor-core kernels withhold every product, so each of their
+ * bounded waits runs out (after about 20 ms) and sal_device_status reports
+ * SAL_ERR_TIMEOUT.  Off by default; never needed in normal use. */
+SAL_API sal_status sal_test_stall_tensor_cores(int32_t on);
 
 /* Static text for a status code. */
 SAL_API const char *sal_status_string(sal_status s);

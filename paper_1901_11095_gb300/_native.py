@@ -85,6 +85,8 @@ def lib():
             "sal_autotune_save": [ctypes.c_char_p],
             "sal_autotune_load": [ctypes.c_char_p],
             "sal_autotune_clear": [],
+            "sal_device_status": [vp],
+            "sal_test_stall_tensor_cores": [ctypes.c_int32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -110,4 +112,5 @@ def exported_symbols() -> list[str]:
             "sal_combine", "sal_saliency", "sal_batch_workspace_size", "sal_saliency_batched",
             "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",
             "sal_autotune_batched", "sal_autotune_query", "sal_autotune_save", "sal_autotune_load",
-            "sal_autotune_clear", "sal_status_string", "sal_last_error"]
+            "sal_autotune_clear", "sal_device_status", "sal_test_stall_tensor_cores", "sal_status_string",
+            "sal_last_error"]

@@ -272,3 +272,12 @@ def sal_autotune_load(path: str) -> None:
 
 def sal_autotune_clear() -> None:
     check(N.lib().sal_autotune_clear())
+
+
+def sal_device_status(stream=None) -> None:
+    """Raises SalError (SAL_ERR_TIMEOUT) if a tensor-core kernel's bounded wait ran out."""
+    check(N.lib().sal_device_status(_stream(stream)))
+
+
+def sal_test_stall_tensor_cores(on: bool) -> None:
+    check(N.lib().sal_test_stall_tensor_cores(1 if on else 0))

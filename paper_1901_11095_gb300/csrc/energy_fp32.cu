@@ -66,6 +66,37 @@ cudaError_t launch_energy_fp32_batch(const EVolDesc *vols, int n, int L, int bnd
     }
 }
 
+cudaError_t launch_energy_tc_l3(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l5(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l7(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l9(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l11(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l13(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+cudaError_t launch_energy_tc_l15(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
+
+bool energy_tc_supported(int L, int prec)
+{
+    if (prec == SAL_PREC_BF16) return L >= 3 && L <= 15 && (L & 1);
+    if (prec == SAL_PREC_TF32) return L >= 3 && L <= 11 && (L & 1);
+    return false;
+}
+
+cudaError_t launch_energy_tc(const EVolDesc *vols, int n, int L, int bnd, int prec, bool persistent,
+                             const TcControl &c, cudaStream_t s)
+{
+    if (!energy_tc_supported(L, prec)) return cudaErrorInvalidValue;
+    switch (L) {
+        case 3: return launch_energy_tc_l3(vols, n, bnd, prec, persistent, c, s);
+        case 5: return launch_energy_tc_l5(vols, n, bnd, prec, persistent, c, s);
+        case 7: return launch_energy_tc_l7(vols, n, bnd, prec, persistent, c, s);
+        case 9: return launch_energy_tc_l9(vols, n, bnd, prec, persistent, c, s);
+        case 11: return launch_energy_tc_l11(vols, n, bnd, prec, persistent, c, s);
+        case 13: return launch_energy_tc_l13(vols, n, bnd, prec, persistent, c, s);
+        case 15: return launch_energy_tc_l15(vols, n, bnd, prec, persistent, c, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_energy_fp32(const float *V, sal_dims d, int L, int bnd, float *E, cudaStream_t s)
 {
     EVolDesc v{V, E, d.T, d.X, d.Y};

@@ -346,23 +346,13 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, c
     }
 }
 
-// One output tile of one volume.  Every thread of the CTA calls it with the same tile.
+// Halo tile of V in shared memory; outside the volume the boundary extension supplies the
+// samples.  G provides BT, BX, BY, H, HX, PY, NV and NT.
 template <class G>
-__device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
-                                            int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
-                                            const SpecTables &tb, float *smem)
+__device__ __forceinline__ void stage_v(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                        int64_t t0, int64_t x0, int64_t y0, float *sV)
 {
-    constexpr int L = G::L, H = G::H, PY = G::PY;
-    float *sG1 = smem;
-    float2 *sG2 = reinterpret_cast<float2 *>(smem + G::NG1);
-    float *sV = smem + G::NG1;   // aliases sG2: dead once stage t is done
-
-    const int ty = (int)(tile % tiles_y);
-    const int tx = (int)((tile / tiles_y) % tiles_x);
-    const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
-    const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
-
-    // halo tile of V; outside the volume the boundary extension supplies the samples
+    constexpr int H = G::H, PY = G::PY;
     const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
                         y0 + G::BY + H <= Y;
     if (inside) {
@@ -382,12 +372,14 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
             sV[i] = __ldg(V + (gt * X + gx) * Y + gy);
         }
     }
-    __syncthreads();
+}
 
-    Tw<L> tw;
-    tw.load(tb);
-
-    // stage t: (t, x', y') -> G1 components [Re G1(0), Re G1(1), Im G1(1), ...]
+// Stage t: every (t, x', y') column of the halo tile -> G1 components
+// [Re G1(0), Re G1(1), Im G1(1), ..., Re G1(h), Im G1(h)] in sG1[(t, x')][component][y'].
+template <class G>
+__device__ __forceinline__ void t_stage(const float *sV, float *sG1, const Tw<G::L> &tw)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY;
     for (int i = threadIdx.x; i < G::BT * G::HX * PY; i += G::NT) {
         const int r = i / PY, yy = i - r * PY;
         const int t = r / G::HX, xx = r - t * G::HX;
@@ -417,6 +409,29 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
             o[(2 * mu) * PY] = -B;
         }
     }
+}
+
+// One output tile of one volume.  Every thread of the CTA calls it with the same tile.
+template <class G>
+__device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                            int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
+                                            const SpecTables &tb, float *smem)
+{
+    constexpr int L = G::L, H = G::H;
+    float *sG1 = smem;
+    float2 *sG2 = reinterpret_cast<float2 *>(smem + G::NG1);
+    float *sV = smem + G::NG1;   // aliases sG2: dead once stage t is done
+
+    const int ty = (int)(tile % tiles_y);
+    const int tx = (int)((tile / tiles_y) % tiles_x);
+    const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
+    const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
+
+    stage_v<G>(V, T, X, Y, bnd, t0, x0, y0, sV);
+    __syncthreads();
+    Tw<L> tw;
+    tw.load(tb);
+    t_stage<G>(sV, sG1, tw);
     __syncthreads();
 
     const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <new>
 
 #include "sal_internal.cuh"
@@ -36,6 +38,36 @@ void make_tables(int L, SpecTables *t)
     const double n3 = (double)L * L * L;
     t->escale = (float)(2.0 / ((n3 - 1.0) * n3));
 }
+
+// Status word the tensor-core kernels set when a bounded wait runs out (one per device).
+static __device__ int g_device_status;
+
+namespace {
+std::mutex g_status_mu;
+int *g_status_ptr[64] = {};
+std::atomic<int> g_stall{0};
+}  // namespace
+
+int *device_status_ptr()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+        g_status_ptr[dev] = static_cast<int *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+TcControl tc_control()
+{
+    const int stall = g_stall.load();
+    return TcControl{device_status_ptr(), stall, stall ? 20000000ull : 1000000000ull};
+}
+
+void set_test_stall(int on) { g_stall.store(on ? 1 : 0); }
 
 }  // namespace sal
 
@@ -121,8 +153,15 @@ size_t dcs_ws_bytes(sal_dims d) { return round256(9 * (size_t)sal::dcs_num_parti
 
 sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, float *E, cudaStream_t s)
 {
-    if (p->precision != SAL_PREC_FP32)
-        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available in this build", p->precision);
+    if (p->precision != SAL_PREC_FP32) {
+        if (!sal::energy_tc_supported(p->L, p->precision))
+            return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for L = %d", p->precision, p->L);
+        const sal::TcControl c = sal::tc_control();
+        if (!c.status) return fail(SAL_ERR_CUDA, "device status word unavailable");
+        sal::EVolDesc v{V, E, d.T, d.X, d.Y};
+        cudaError_t e = sal::launch_energy_tc(&v, 1, p->L, p->boundary, p->precision, false, c, s);
+        return e == cudaSuccess ? SAL_OK : cuda_fail(e, "tensor-core spectral energy launch");
+    }
     const int shape = sal::autotune_lookup(p->L, p->precision, sal::size_class_of(d.T * d.X * d.Y));
     sal::EVolDesc v{V, E, d.T, d.X, d.Y};
     cudaError_t e = sal::launch_energy_fp32_batch(&v, 1, p->L, p->boundary, shape, false, s);
@@ -141,8 +180,8 @@ sal_status check_batch(const sal_volume *vols, int32_t n, const sal_params *p, b
     if (n < 1 || n > SAL_BATCH_MAX) return fail(SAL_ERR_INVALID_ARG, "batch size must be in [1, %d]", SAL_BATCH_MAX);
     sal_status s = check_params(p);
     if (s) return s;
-    if (p->precision != SAL_PREC_FP32)
-        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for batches in this build", p->precision);
+    if (p->precision != SAL_PREC_FP32 && !sal::energy_tc_supported(p->L, p->precision))
+        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for L = %d", p->precision, p->L);
     for (int i = 0; i < n; ++i) {
         s = check_dims(sal_dims{vols[i].T, vols[i].X, vols[i].Y});
         if (s) return s;
@@ -196,7 +235,14 @@ sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p,
         bv[i] = sal::BatchVolDesc{Sm, vols[i].S, part, sal::dcs_num_tiles(sal_dims{vols[i].T, vols[i].X, vols[i].Y}),
                                   vols[i].T * vols[i].X * vols[i].Y};
     }
-    cudaError_t e = sal::launch_energy_fp32_batch(ev, n, p->L, p->boundary, batch_shape(vols, n, p), true, s);
+    cudaError_t e;
+    if (p->precision == SAL_PREC_FP32) {
+        e = sal::launch_energy_fp32_batch(ev, n, p->L, p->boundary, batch_shape(vols, n, p), true, s);
+    } else {
+        const sal::TcControl c = sal::tc_control();
+        if (!c.status) return fail(SAL_ERR_CUDA, "device status word unavailable");
+        e = sal::launch_energy_tc(ev, n, p->L, p->boundary, p->precision, true, c, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "batched spectral energy launch");
     e = sal::launch_dcs_items(dv, n, p, true, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched directional compare launch");
@@ -409,7 +455,7 @@ sal_status sal_graph_create_batched(const sal_volume *vols, int32_t n, const sal
     cudaError_t e = cudaSuccess;
     // first use for this (L, precision, size class): choose the tile shape on this batch
     float cached_ms = 0.f;
-    if (!sal::autotune_get_ms(p->L, p->precision, cls, &cached_ms)) {
+    if (p->precision == SAL_PREC_FP32 && !sal::autotune_get_ms(p->L, p->precision, cls, &cached_ms)) {
         sal::EVolDesc ev[SAL_BATCH_MAX];
         energy_descs(vols, n, b, base, ev);
         int best = 0;
@@ -473,7 +519,8 @@ sal_status sal_autotune(const float *V, sal_dims dims, const sal_params *p, floa
     if (s) return s;
     if (!V || !E || !out) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
     if (!aligned16(V) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
-    if (p->precision != SAL_PREC_FP32) return fail(SAL_ERR_UNSUPPORTED, "precision %d is not tunable in this build", p->precision);
+    if (p->precision != SAL_PREC_FP32)
+        return fail(SAL_ERR_UNSUPPORTED, "only the FP32 kernel has several tile shapes (precision %d)", p->precision);
     sal::EVolDesc v{V, E, dims.T, dims.X, dims.Y};
     int best = 0;
     float ms = 0.f;
@@ -488,6 +535,8 @@ sal_status sal_autotune_batched(const sal_volume *vols, int32_t n, const sal_par
 {
     sal_status s = check_batch(vols, n, p, true);
     if (s) return s;
+    if (p->precision != SAL_PREC_FP32)
+        return fail(SAL_ERR_UNSUPPORTED, "only the FP32 kernel has several tile shapes (precision %d)", p->precision);
     if (!ws || !out || !aligned16(ws)) return fail(SAL_ERR_INVALID_ARG, "ws and out must be non-NULL (ws 16-byte aligned)");
     const BatchLayout b = batch_layout(vols, n);
     if (ws_bytes < b.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, b.total);
@@ -534,6 +583,27 @@ sal_status sal_autotune_load(const char *path)
 sal_status sal_autotune_clear(void)
 {
     sal::autotune_clear();
+    return ok();
+}
+
+sal_status sal_device_status(void *stream)
+{
+    int *p = sal::device_status_ptr();
+    if (!p) return fail(SAL_ERR_CUDA, "device status word unavailable");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the status word");
+    int v = 0;
+    const int zero = 0;
+    e = cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(p, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    if (v == SAL_ERR_TIMEOUT) return fail(SAL_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    return v == 0 ? ok() : fail(SAL_ERR_INTERNAL, "device status %d", v);
+}
+
+sal_status sal_test_stall_tensor_cores(int32_t on)
+{
+    sal::set_test_stall(on);
     return ok();
 }
 

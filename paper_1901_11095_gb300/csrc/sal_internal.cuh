@@ -65,6 +65,20 @@ struct TileShape {
 int energy_num_shapes(int L);
 TileShape energy_shape(int L, int idx);
 
+// Control of the tensor-core kernels: where a timed-out wait is recorded, the test hook
+// that withholds every product, and the bound of one wait.
+struct TcControl {
+    int *status;
+    int stall;
+    unsigned long long limit_ns;
+};
+bool energy_tc_supported(int L, int prec);
+int *device_status_ptr();
+TcControl tc_control();
+void set_test_stall(int on);
+cudaError_t launch_energy_tc(const EVolDesc *vols, int n, int L, int bnd, int prec, bool persistent,
+                             const TcControl &c, cudaStream_t s);
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_energy_fp32_batch(const EVolDesc *vols, int n, int L, int bnd, int shape_idx, bool persistent,
                                      cudaStream_t s);
