@@ -101,7 +101,11 @@ __device__ __forceinline__ void put_pair(unsigned char *tile, int row, int j, fl
     if (G::OP::ESZ == 2) {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(re, im);
     } else {
-        *reinterpret_cast<float2 *>(p) = make_float2(re, im);   // the tensor core reads the TF32 bits
+        // round to the TF32 grid (nearest, ties away) instead of letting the unit truncate
+        uint32_t a, b;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(a) : "f"(re));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(im));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(a, b);
     }
 }
 
