@@ -278,6 +278,66 @@ def run_batch(args, rank: int, world: int) -> None:
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args) -> None:
+    """Precision sweep on a 256^3 volume: every precision at L = 5, 7, 9, 11, each a JSON line
+    with its speed and its error per map against the FP64 oracle at sampled voxels."""
+    import torch
+
+    import oracle
+    from paper_1901_11095_gb300 import api, synth
+
+    dev = torch.device("cuda:0")
+    shape = (256, 256, 256)
+    V_np = synth.make_volume(shape, seed=2)
+    V = torch.from_numpy(V_np).to(dev)
+    N = V_np.size
+    rng = np.random.default_rng(0)
+    coords = np.stack([rng.integers(0, s, 1500) for s in shape], axis=1)
+    faces = np.array([[0, 0, 0], [255, 255, 255], [0, 128, 255], [255, 0, 7]])
+    coords = np.concatenate([coords, faces]).astype(np.int64)
+    idx = torch.from_numpy(coords).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for L in (5, 7, 9, 11):
+        E_ref, Sm_ref = oracle.maps_at(V_np, coords, L)
+        S_fp32 = None
+        for prec in ("fp32", "tf32", "bf16"):
+            p = api.params(L=L, precision=prec)
+            E = torch.empty((3,) + shape, device=dev)
+            ws = torch.empty(api.sal_workspace_size(api.dims_of(V), p), device=dev, dtype=torch.uint8)
+            S = torch.empty_like(V)
+            Sm, st = api.sal_directional_compare(api.sal_spectral_energy(V, p, E=E), p)
+            for _ in range(2):
+                api.sal_saliency(V, p, S=S, ws=ws)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            for _ in range(args.steps):
+                api.sal_spectral_energy(V, p, E=E)
+            e1.record(stream)
+            for _ in range(args.steps):
+                api.sal_saliency(V, p, S=S, ws=ws)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            api.sal_device_status()
+            k1_ms = e0.elapsed_time(e1) / args.steps
+            path_ms = e1.elapsed_time(e2) / args.steps
+            err = {}
+            for m, name in enumerate("txy"):
+                e = E[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+                s_ = Sm[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+                err[f"E_{name}"] = float(np.abs(e - E_ref[m]).max() / np.abs(E_ref[m]).max())
+                err[f"S_{name}"] = float(np.abs(s_ - Sm_ref[m]).max() / np.abs(Sm_ref[m]).max())
+            if prec == "fp32":
+                S_fp32 = S.clone()
+            else:
+                err["S_vs_fp32_relL2"] = float(torch.linalg.vector_norm((S - S_fp32).double()) /
+                                               torch.linalg.vector_norm(S_fp32.double()))
+            print(json.dumps({"sweep": "precision", "volume": list(shape), "L": L, "precision": prec,
+                              "voxels_per_s": N / (path_ms / 1e3), "ms_per_step": path_ms,
+                              "spectral_energy_ms": k1_ms, "errors_vs_oracle_sampled": err,
+                              "samples": int(coords.shape[0])}), flush=True)
+
+
 def run_ours(args, rank: int, world: int) -> None:
     import torch
     import torch.distributed as dist
@@ -417,6 +477,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,6 +491,9 @@ def main():
     sys.path.insert(0, ROOT)
     import __graft_entry__
     __graft_entry__.build()
+    if args.sweep:
+        run_sweep(args)
+        return
     (run_batch if args.workload == "batch64" else run_ours)(args, rank, world)
     if world > 1:
         import torch.distributed as dist

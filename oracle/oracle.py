@@ -72,6 +72,19 @@ def _load():
         lib.oracle_saliency.argtypes = [f32p, L_, L_, L_, I_, I_, I_, D_, D_, D_, D_, D_, I_,
                                         f64p, f64p, f64p, f64p]
         lib.oracle_saliency.restype = I_
+        lib.oracle_conv3d.argtypes = [f64p, L_, L_, L_, I_, I_, f64p, f64p, I_, f64p]
+        lib.oracle_conv3d.restype = None
+        lib.oracle_gelu.argtypes = [D_]
+        lib.oracle_gelu.restype = D_
+        lib.oracle_gelu_grad.argtypes = [D_]
+        lib.oracle_gelu_grad.restype = D_
+        lib.oracle_conv3d_grad.argtypes = [f64p, L_, L_, L_, I_, I_, f64p, I_, f64p, f64p, f64p, f64p]
+        lib.oracle_conv3d_grad.restype = None
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_surrogate_forward.argtypes = [f64p, L_, L_, L_, I_, ip, f64p, I_, f64p, f64p]
+        lib.oracle_surrogate_forward.restype = I_
+        lib.oracle_surrogate_loss_grad.argtypes = [f64p, L_, L_, L_, I_, ip, f64p, I_, f64p, f64p, f64p]
+        lib.oracle_surrogate_loss_grad.restype = D_
         _lib = lib
     return _lib
 
@@ -200,3 +213,70 @@ def saliency(V, L=7, bnd=REFLECT, stencil=STENCIL_26, sigma=1.0, a=1 / 3, b=1 / 
     if rc:
         raise ValueError(f"oracle_saliency failed ({rc})")
     return (S, E, Sm, st.reshape(3, 3)) if full else S
+
+
+# ---- learned surrogate (plain FP64 reference of its layers) ----------------------------
+
+def conv3d(x, w, b=None, bnd=REFLECT):
+    """3x3x3 cross-correlation with bias: x [Cin][T][X][Y], w [Cout][Cin][3][3][3] -> [Cout][T][X][Y]."""
+    x, xp = _f64(x)
+    w, wp = _f64(w)
+    cout, cin = w.shape[0], w.shape[1]
+    if b is not None:
+        b, bp = _f64(b)
+    else:
+        bp = None
+    out, op = _f64(np.zeros((cout,) + x.shape[1:]))
+    _load().oracle_conv3d(xp, *x.shape[1:], cin, cout, wp, bp, bnd, op)
+    return out
+
+
+def gelu(v):
+    f = np.vectorize(_load().oracle_gelu)
+    return f(np.asarray(v, dtype=np.float64))
+
+
+def gelu_grad(v):
+    f = np.vectorize(_load().oracle_gelu_grad)
+    return f(np.asarray(v, dtype=np.float64))
+
+
+def conv3d_grad(x, w, gout, bnd=REFLECT, need_input_grad=True):
+    """(dW, db, dX) of conv3d given dL/dout."""
+    x, xp = _f64(x)
+    w, wp = _f64(w)
+    gout, gp = _f64(gout)
+    gw, gwp = _f64(np.zeros_like(w))
+    gb, gbp = _f64(np.zeros(w.shape[0]))
+    gin, gip = _f64(np.zeros_like(x))
+    _load().oracle_conv3d_grad(xp, *x.shape[1:], w.shape[1], w.shape[0], wp, bnd, gp, gwp, gbp,
+                               gip if need_input_grad else None)
+    return gw, gb, (gin if need_input_grad else None)
+
+
+def _widths(widths):
+    arr = (ctypes.c_int * len(widths))(*[int(v) for v in widths])
+    return arr
+
+
+def surrogate_forward(x, widths, params, bnd=REFLECT):
+    """Output [widths[-1]][T][X][Y] of the layer stack for input x [widths[0]][T][X][Y]."""
+    x, xp = _f64(x)
+    params, pp = _f64(params)
+    out, op = _f64(np.zeros((widths[-1],) + x.shape[1:]))
+    _load().oracle_surrogate_forward(xp, *x.shape[1:], len(widths) - 1, _widths(widths), pp, bnd, op, None)
+    return out
+
+
+def surrogate_loss_grad(x, widths, params, target, mask=None, bnd=REFLECT):
+    """(loss, grads) of 0.5 * sum mask * (out - target)^2; grads in the layout of params."""
+    x, xp = _f64(x)
+    params, pp = _f64(params)
+    target, tp = _f64(target)
+    mp = None
+    if mask is not None:
+        mask, mp = _f64(mask)
+    grads, gp = _f64(np.zeros_like(params))
+    loss = _load().oracle_surrogate_loss_grad(xp, *x.shape[1:], len(widths) - 1, _widths(widths), pp, bnd, tp,
+                                              mp, gp)
+    return loss, grads

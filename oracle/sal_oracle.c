@@ -476,3 +476,156 @@ int oracle_maps_at(const float *V, long T, long X, long Y, int L, int bnd, int s
     free(w);
     return 0;
 }
+
+/* ==== Learned surrogate: plain FP64 reference of its layers (test infrastructure) ====
+ * A 3x3x3 convolution (cross-correlation, as the layers compute it) with bias, the GELU
+ * activation x * Phi(x) (Phi the standard normal CDF, via erf), and the gradients of both
+ * by the chain rule.  Arrays are planar [C][T][X][Y]; weights [Cout][Cin][3][3][3].  Samples
+ * outside the volume come from the same boundary extension as the method (R5). */
+
+void oracle_conv3d(const double *in, long T, long X, long Y, int cin, int cout, const double *w,
+                   const double *b, int bnd, double *out)
+{
+    long N = T * X * Y;
+#pragma omp parallel for
+    for (long t = 0; t < T; ++t)
+        for (long x = 0; x < X; ++x)
+            for (long y = 0; y < Y; ++y)
+                for (int co = 0; co < cout; ++co) {
+                    double s = b ? b[co] : 0.0;
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int a = 0; a < 3; ++a)
+                            for (int c = 0; c < 3; ++c)
+                                for (int d = 0; d < 3; ++d) {
+                                    long tt = orc_ext_index(t + a - 1, T, bnd), xx = orc_ext_index(x + c - 1, X, bnd),
+                                         yy = orc_ext_index(y + d - 1, Y, bnd);
+                                    s += w[(((long)co * cin + ci) * 3 + a) * 9 + c * 3 + d] *
+                                         in[ci * N + (tt * X + xx) * Y + yy];
+                                }
+                    out[co * N + (t * X + x) * Y + y] = s;
+                }
+}
+
+double oracle_gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+double oracle_gelu_grad(double x)
+{
+    const double phi = exp(-0.5 * x * x) / sqrt(2.0 * ORC_PI);
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * phi;
+}
+
+/* Gradients of out = conv(in) w.r.t. weights, bias and input, given gout = dL/dout.
+ * gin may be NULL.  Accumulates nothing: every output is overwritten. */
+void oracle_conv3d_grad(const double *in, long T, long X, long Y, int cin, int cout, const double *w,
+                        int bnd, const double *gout, double *gw, double *gb, double *gin)
+{
+    long N = T * X * Y;
+    for (int i = 0; i < cout * cin * 27; ++i) gw[i] = 0.0;
+    for (int co = 0; co < cout; ++co) gb[co] = 0.0;
+    if (gin)
+        for (long i = 0; i < (long)cin * N; ++i) gin[i] = 0.0;
+    for (long t = 0; t < T; ++t)
+        for (long x = 0; x < X; ++x)
+            for (long y = 0; y < Y; ++y)
+                for (int co = 0; co < cout; ++co) {
+                    double g = gout[co * N + (t * X + x) * Y + y];
+                    gb[co] += g;
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int a = 0; a < 3; ++a)
+                            for (int c = 0; c < 3; ++c)
+                                for (int d = 0; d < 3; ++d) {
+                                    long tt = orc_ext_index(t + a - 1, T, bnd), xx = orc_ext_index(x + c - 1, X, bnd),
+                                         yy = orc_ext_index(y + d - 1, Y, bnd);
+                                    long wi = (((long)co * cin + ci) * 3 + a) * 9 + c * 3 + d;
+                                    long ii = ci * N + (tt * X + xx) * Y + yy;
+                                    gw[wi] += g * in[ii];
+                                    if (gin) gin[ii] += g * w[wi];
+                                }
+                }
+}
+
+/* The surrogate network: n layers of 3x3x3 convolution, GELU after all but the last.
+ * widths[0..n] are the channel counts (widths[0] = 1 input, widths[n] = 3 outputs);
+ * params holds, layer by layer, the weights then the biases.  acts (optional) receives
+ * every layer's pre-activation, [sum of widths[1..n]][N]. */
+int oracle_surrogate_forward(const double *x, long T, long X, long Y, int n, const int *widths,
+                             const double *params, int bnd, double *out, double *acts)
+{
+    long N = T * X * Y;
+    int wmax = 0;
+    for (int l = 0; l <= n; ++l) wmax = widths[l] > wmax ? widths[l] : wmax;
+    double *a = (double *)malloc(sizeof(double) * wmax * N), *z = (double *)malloc(sizeof(double) * wmax * N);
+    memcpy(a, x, sizeof(double) * widths[0] * N);
+    const double *p = params;
+    long aoff = 0;
+    for (int l = 0; l < n; ++l) {
+        const double *w = p, *b = p + (long)widths[l + 1] * widths[l] * 27;
+        p = b + widths[l + 1];
+        oracle_conv3d(a, T, X, Y, widths[l], widths[l + 1], w, b, bnd, z);
+        if (acts) memcpy(acts + aoff, z, sizeof(double) * widths[l + 1] * N);
+        aoff += (long)widths[l + 1] * N;
+        if (l + 1 < n) {
+            for (long i = 0; i < (long)widths[l + 1] * N; ++i) a[i] = oracle_gelu(z[i]);
+        } else {
+            memcpy(out, z, sizeof(double) * widths[l + 1] * N);
+        }
+    }
+    free(a);
+    free(z);
+    return 0;
+}
+
+/* Gradient of L = sum over outputs of 0.5 * mask * (out - target)^2 w.r.t. every parameter
+ * (same layout as params).  mask may be NULL (all ones).  Returns L. */
+double oracle_surrogate_loss_grad(const double *x, long T, long X, long Y, int n, const int *widths,
+                                  const double *params, int bnd, const double *target, const double *mask,
+                                  double *grads)
+{
+    long N = T * X * Y;
+    long tot = 0;
+    for (int l = 0; l < n; ++l) tot += widths[l + 1];
+    double *acts = (double *)malloc(sizeof(double) * tot * N);
+    double *out = (double *)malloc(sizeof(double) * widths[n] * N);
+    oracle_surrogate_forward(x, T, X, Y, n, widths, params, bnd, out, acts);
+    int wmax = 0;
+    for (int l = 0; l <= n; ++l) wmax = widths[l] > wmax ? widths[l] : wmax;
+    double *g = (double *)malloc(sizeof(double) * wmax * N), *gin = (double *)malloc(sizeof(double) * wmax * N);
+    double *a = (double *)malloc(sizeof(double) * wmax * N);
+    double loss = 0.0;
+    for (long i = 0; i < (long)widths[n] * N; ++i) {
+        double m = mask ? mask[i % N] : 1.0, d = out[i] - target[i];
+        loss += 0.5 * m * d * d;
+        g[i] = m * d;
+    }
+    /* parameter offsets per layer */
+    long offs[64];
+    long o = 0;
+    for (int l = 0; l < n; ++l) {
+        offs[l] = o;
+        o += (long)widths[l + 1] * widths[l] * 27 + widths[l + 1];
+    }
+    long aoff_end = tot * N;
+    for (int l = n - 1; l >= 0; --l) {
+        long aoff = aoff_end - (long)widths[l + 1] * N;      /* this layer's pre-activation */
+        /* the layer's input: x for l = 0, else GELU of the previous pre-activation */
+        if (l == 0) {
+            memcpy(a, x, sizeof(double) * widths[0] * N);
+        } else {
+            long poff = aoff - (long)widths[l] * N;
+            for (long i = 0; i < (long)widths[l] * N; ++i) a[i] = oracle_gelu(acts[poff + i]);
+        }
+        const double *w = params + offs[l];
+        double *gw = grads + offs[l], *gb = gw + (long)widths[l + 1] * widths[l] * 27;
+        oracle_conv3d_grad(a, T, X, Y, widths[l], widths[l + 1], w, bnd, g, gw, gb, l > 0 ? gin : NULL);
+        if (l > 0) {
+            long poff = aoff - (long)widths[l] * N;
+            for (long i = 0; i < (long)widths[l] * N; ++i) g[i] = gin[i] * oracle_gelu_grad(acts[poff + i]);
+        }
+        aoff_end = aoff;
+    }
+    free(acts);
+    free(out);
+    free(g);
+    free(gin);
+    free(a);
+    return loss;
+}
