@@ -242,6 +242,45 @@ SAL_API sal_status sal_autotune_save(const char *path);
 SAL_API sal_status sal_autotune_load(const char *path);
 SAL_API sal_status sal_autotune_clear(void);
 
+/* ---- Learned surrogate of the spectral energies ------------------------------------------
+ * SAL_SURR_LAYERS layers of 3x3x3 convolution (1 -> SAL_SURR_WIDTH -> ... -> 3 channels), GELU
+ * after all but the last, predicting E_t, E_x, E_y from the amplitudes.  Input and target are
+ * divided by the volume's RMS amplitude inside (E scales with the amplitude, so the network
+ * sees one scale).  Parameters: one flat FP32 array, layer by layer, weights
+ * [Cout][Cin][3][3][3] then biases [Cout]; the kernels round the weights to BF16 as they read
+ * them and accumulate in FP32.  The paper has no learned part: this is an added surrogate
+ * whose errors are measured against the method it imitates. */
+#define SAL_SURR_LAYERS 5
+#define SAL_SURR_WIDTH 24
+SAL_API sal_status sal_surrogate_param_count(int64_t *n);
+/* Workspace for sal_surrogate_forward (training = 0: BF16 activations, 48 B/voxel; training
+ * = 1: every FP32 activation kept for the backward pass, 972 B/voxel). */
+SAL_API sal_status sal_surrogate_workspace_size(sal_dims dims, int32_t training, size_t *bytes);
+/* E [3][T*X*Y] predicted from V (device pointers).  With training = 1 the activations stay in
+ * `ws` for sal_surrogate_backward. */
+SAL_API sal_status sal_surrogate_forward(const float *V, sal_dims dims, const sal_params *p, const float *params,
+                                         float *E, int32_t training, void *ws, size_t ws_bytes, void *stream);
+/* Gradient of L = 0.5 / count * sum (E_pred - E_target)^2 / rms^2 over voxels at least
+ * `margin` (>= SAL_SURR_LAYERS) from every face, for the activations of the last training
+ * forward in `ws`.  grads (FP32, param_count) is overwritten; *loss (device double) receives L. */
+SAL_API sal_status sal_surrogate_backward(const float *V, sal_dims dims, const sal_params *p, const float *params,
+                                          const float *E_target, int32_t margin, float *grads, double *loss,
+                                          void *ws, size_t ws_bytes, void *stream);
+/*
+ * Inference with the plain method as the judge and the fallback: E predicted for the whole
+ * volume, then, for every check block of 16 x 16 x 32 voxels, E computed exactly (FP32
+ * path) at 8 sample voxels; a block whose largest error, relative to each map's mean
+ * magnitude over all samples, exceeds `threshold` (e.g. 2e-2) is recomputed exactly.
+ * counts (device, 2 ints, nullable) receives (blocks recomputed, blocks checked).
+ */
+SAL_API sal_status sal_surrogate_infer_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes);
+SAL_API sal_status sal_surrogate_infer(const float *V, sal_dims dims, const sal_params *p, const float *params,
+                                       float *E, float threshold, int32_t *counts, void *ws, size_t ws_bytes,
+                                       void *stream);
+/* One Adam step (bias-corrected, step >= 1) on the FP32 parameters with moments m, v. */
+SAL_API sal_status sal_surrogate_adam_step(float *params, const float *grads, float *m, float *v, int32_t step,
+                                           float lr, float beta1, float beta2, float eps, void *stream);
+
 /*
  * Synchronises `stream`, then reads and clears the library's device status word on the
  * current device: SAL_OK, or SAL_ERR_TIMEOUT when a bounded device-side wait of a

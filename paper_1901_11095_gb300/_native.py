@@ -20,6 +20,7 @@ SAL_STENCIL_26, SAL_STENCIL_LINE = 0, 1
 SAL_STATS_LEN = 9
 SAL_DCS_STATIC_MAX_TILES = 131072
 SAL_BATCH_MAX = 128
+SAL_SURR_LAYERS, SAL_SURR_WIDTH = 5, 24
 
 
 class SalDims(ctypes.Structure):
@@ -86,6 +87,14 @@ def lib():
             "sal_autotune_load": [ctypes.c_char_p],
             "sal_autotune_clear": [],
             "sal_device_status": [vp],
+            "sal_surrogate_param_count": [ctypes.POINTER(ctypes.c_int64)],
+            "sal_surrogate_workspace_size": [SalDims, ctypes.c_int32, ctypes.POINTER(sz)],
+            "sal_surrogate_forward": [vp, SalDims, pp, vp, vp, ctypes.c_int32, vp, sz, vp],
+            "sal_surrogate_backward": [vp, SalDims, pp, vp, vp, ctypes.c_int32, vp, vp, vp, sz, vp],
+            "sal_surrogate_adam_step": [vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_float, vp],
+            "sal_surrogate_infer_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
+            "sal_surrogate_infer": [vp, SalDims, pp, vp, vp, ctypes.c_float, vp, vp, sz, vp],
             "sal_test_stall_tensor_cores": [ctypes.c_int32],
         }
         for name, args in sig.items():
@@ -112,5 +121,7 @@ def exported_symbols() -> list[str]:
             "sal_combine", "sal_saliency", "sal_batch_workspace_size", "sal_saliency_batched",
             "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",
             "sal_autotune_batched", "sal_autotune_query", "sal_autotune_save", "sal_autotune_load",
-            "sal_autotune_clear", "sal_device_status", "sal_test_stall_tensor_cores", "sal_status_string",
-            "sal_last_error"]
+            "sal_autotune_clear", "sal_device_status", "sal_test_stall_tensor_cores", "sal_surrogate_param_count",
+            "sal_surrogate_workspace_size", "sal_surrogate_forward", "sal_surrogate_backward",
+            "sal_surrogate_adam_step", "sal_surrogate_infer_workspace_size", "sal_surrogate_infer",
+            "sal_status_string", "sal_last_error"]

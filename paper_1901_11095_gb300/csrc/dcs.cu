@@ -434,7 +434,7 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     }
     const void *fn = p->stencil == SAL_STENCIL_26 ? (const void *)dcs_kernel<SAL_STENCIL_26>
                                                   : (const void *)dcs_kernel<SAL_STENCIL_LINE>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = total;
     if (persistent) {

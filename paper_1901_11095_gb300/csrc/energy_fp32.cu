@@ -74,6 +74,30 @@ cudaError_t launch_energy_tc_l11(const EVolDesc *vols, int n, int bnd, int prec,
 cudaError_t launch_energy_tc_l13(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
 cudaError_t launch_energy_tc_l15(const EVolDesc *vols, int n, int bnd, int prec, bool persistent, const TcControl &c, cudaStream_t s);
 
+cudaError_t launch_energy_fp32_list_l3(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l5(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l7(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l9(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l11(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l13(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+cudaError_t launch_energy_fp32_list_l15(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E, cudaStream_t s);
+
+// Shape-0 tiles of a device-side list (the surrogate's fallback).
+cudaError_t launch_energy_fp32_list(const float *V, sal_dims d, int L, int bnd, const int64_t *list, const int *count,
+                                    float *E, cudaStream_t s)
+{
+    switch (L) {
+        case 3: return launch_energy_fp32_list_l3(V, d, bnd, list, count, E, s);
+        case 5: return launch_energy_fp32_list_l5(V, d, bnd, list, count, E, s);
+        case 7: return launch_energy_fp32_list_l7(V, d, bnd, list, count, E, s);
+        case 9: return launch_energy_fp32_list_l9(V, d, bnd, list, count, E, s);
+        case 11: return launch_energy_fp32_list_l11(V, d, bnd, list, count, E, s);
+        case 13: return launch_energy_fp32_list_l13(V, d, bnd, list, count, E, s);
+        case 15: return launch_energy_fp32_list_l15(V, d, bnd, list, count, E, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 bool energy_tc_supported(int L, int prec)
 {
     if (prec == SAL_PREC_BF16) return L >= 3 && L <= 15 && (L & 1);

@@ -509,6 +509,23 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const __grid_constan
     }
 }
 
+// The same kernel over a device-side list of tiles of one volume (count read on the device),
+// e.g. the tiles that a check found wrong; the grid walks the list persistently.
+template <class G>
+__global__ void __launch_bounds__(G::NT) energy_fp32_list_kernel(const float *__restrict__ V, int64_t T, int64_t X,
+                                                                 int64_t Y, int bnd, int tiles_x, int tiles_y,
+                                                                 const int64_t *__restrict__ list,
+                                                                 const int *__restrict__ count, float *__restrict__ E,
+                                                                 const __grid_constant__ SpecTables tb)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int n = *count;
+    for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+        energy_tile<G>(V, T, X, Y, bnd, list[k], tiles_x, tiles_y, E, tb, smem);
+        __syncthreads();
+    }
+}
+
 template <class G>
 int64_t energy_tiles(int64_t T, int64_t X, int64_t Y, int *tx, int *ty)
 {
@@ -544,7 +561,7 @@ cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persis
     bt.total = total;
     if (total <= 0) return cudaSuccess;
     auto kern = energy_fp32_kernel<G>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaError_t e = set_smem(kern, G::SMEM);
     if (e != cudaSuccess) return e;
     int64_t grid = total;
     if (persistent) {
@@ -558,6 +575,27 @@ cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persis
     }
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
     kern<<<(unsigned)grid, G::NT, G::SMEM, s>>>(bt, tb);
+    return cudaGetLastError();
+}
+
+template <class G>
+cudaError_t launch_energy_list_impl(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count, float *E,
+                                    cudaStream_t s)
+{
+    SpecTables tb;
+    make_tables(G::L, &tb);
+    int tx, ty;
+    energy_tiles<G>(d.T, d.X, d.Y, &tx, &ty);
+    auto kern = energy_fp32_list_kernel<G>;
+    cudaError_t e = set_smem(kern, G::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, G::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(nsm * (per_sm > 0 ? per_sm : 1)), G::NT, G::SMEM, s>>>(V, d.T, d.X, d.Y, bnd, tx, ty, list, count, E,
+                                                                         tb);
     return cudaGetLastError();
 }
 

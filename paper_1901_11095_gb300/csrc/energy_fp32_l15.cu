@@ -13,4 +13,10 @@ cudaError_t launch_energy_fp32_l15(const EVolDesc *vols, int n, int bnd, int sha
     }
 }
 
+cudaError_t launch_energy_fp32_list_l15(const float *V, sal_dims d, int bnd, const int64_t *list, const int *count,
+                                        float *E, cudaStream_t s)
+{
+    return energy_detail::launch_energy_list_impl<energy_detail::EGeo<15, 1, 8>>(V, d, bnd, list, count, E, s);
+}
+
 }  // namespace sal

@@ -495,7 +495,7 @@ cudaError_t launch_energy_tc_impl(const EVolDesc *vols, int n, int bnd, bool per
     bt.total = total;
     if (total <= 0) return cudaSuccess;
     auto kern = energy_tc_kernel<G>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaError_t e = set_smem(kern, G::SMEM);
     if (e != cudaSuccess) return e;
     // one CTA per tile is far more than can be resident; walk the tiles persistently from
     // the resident CTAs (each holds its tensor memory for the whole launch)

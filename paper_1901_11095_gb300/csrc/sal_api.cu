@@ -586,6 +586,93 @@ sal_status sal_autotune_clear(void)
     return ok();
 }
 
+sal_status sal_surrogate_param_count(int64_t *n)
+{
+    if (!n) return fail(SAL_ERR_INVALID_ARG, "n is NULL");
+    *n = sal::surrogate_param_count();
+    return ok();
+}
+
+sal_status sal_surrogate_workspace_size(sal_dims dims, int32_t training, size_t *bytes)
+{
+    sal_status s = check_dims(dims);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = sal::surrogate_ws_bytes(dims, training != 0);
+    return ok();
+}
+
+sal_status sal_surrogate_forward(const float *V, sal_dims dims, const sal_params *p, const float *params, float *E,
+                                 int32_t training, void *ws, size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !params || !ws || (!E && !training)) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(params) || !aligned16(ws) || (E && !aligned16(E)))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const size_t need = sal::surrogate_ws_bytes(dims, training != 0);
+    if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = sal::surrogate_forward(V, dims, p->boundary, params, E, training != 0, ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_forward");
+}
+
+sal_status sal_surrogate_backward(const float *V, sal_dims dims, const sal_params *p, const float *params,
+                                  const float *E_target, int32_t margin, float *grads, double *loss, void *ws,
+                                  size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !params || !E_target || !grads || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (margin < SAL_SURR_LAYERS) return fail(SAL_ERR_INVALID_ARG, "margin must be >= %d", SAL_SURR_LAYERS);
+    if (dims.T <= 2 * margin || dims.X <= 2 * margin || dims.Y <= 2 * margin)
+        return fail(SAL_ERR_INVALID_ARG, "the margin leaves no voxel in the loss");
+    const size_t need = sal::surrogate_ws_bytes(dims, true);
+    if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = sal::surrogate_backward(V, dims, p->boundary, params, E_target, margin, grads, loss, ws,
+                                            (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_backward");
+}
+
+sal_status sal_surrogate_infer_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = sal::surrogate_infer_ws_bytes(dims, p->L);
+    return ok();
+}
+
+sal_status sal_surrogate_infer(const float *V, sal_dims dims, const sal_params *p, const float *params, float *E,
+                               float threshold, int32_t *counts, void *ws, size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V || !params || !E || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(E) || !aligned16(ws) || !aligned16(params))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    if (!(threshold >= 0.f)) return fail(SAL_ERR_INVALID_ARG, "threshold must be >= 0");
+    const size_t need = sal::surrogate_infer_ws_bytes(dims, p->L);
+    if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = sal::surrogate_infer(V, dims, p->L, p->boundary, params, E, threshold, counts, ws,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_infer");
+}
+
+sal_status sal_surrogate_adam_step(float *params, const float *grads, float *m, float *v, int32_t step, float lr,
+                                   float beta1, float beta2, float eps, void *stream)
+{
+    if (!params || !grads || !m || !v) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (step < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return fail(SAL_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    cudaError_t e = sal::surrogate_adam(params, grads, m, v, sal::surrogate_param_count(), step, lr, beta1, beta2, eps,
+                                        (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_adam_step");
+}
+
 sal_status sal_device_status(void *stream)
 {
     int *p = sal::device_status_ptr();

@@ -79,12 +79,30 @@ void set_test_stall(int on);
 cudaError_t launch_energy_tc(const EVolDesc *vols, int n, int L, int bnd, int prec, bool persistent,
                              const TcControl &c, cudaStream_t s);
 
+cudaError_t launch_energy_fp32_list(const float *V, sal_dims d, int L, int bnd, const int64_t *list, const int *count,
+                                    float *E, cudaStream_t s);
+
+// Opts a kernel into `bytes` of dynamic shared memory and asks for the largest shared-memory
+// carveout, so that several CTAs of a large-tile kernel can be resident on one SM.
+template <class F>
+inline cudaError_t set_smem(F fn, size_t bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_energy_fp32_batch(const EVolDesc *vols, int n, int L, int bnd, int shape_idx, bool persistent,
                                      cudaStream_t s);
 cudaError_t launch_energy_fp32(const float *V, sal_dims d, int L, int bnd, float *E, cudaStream_t s);
 cudaError_t launch_local_spectra(const float *V, sal_dims d, int L, int bnd, const int64_t lo[3],
                                  const int64_t ext[3], float *mag, cudaStream_t s);
+// E_m at a list of voxels coords[k] = (t, x, y) (device, [n][3]): E[m * n + k].
+cudaError_t launch_energy_points(const float *V, sal_dims d, int L, int bnd, const int64_t *coords, int64_t n, float *E,
+                                 cudaStream_t s);
 cudaError_t launch_project(const float *mag, int64_t n, int L, float *E, cudaStream_t s);
 
 // One volume of a (possibly batched) directional-compare launch; `part` receives the
@@ -126,6 +144,19 @@ cudaError_t autotune_run(const EVolDesc *vols, int n, int L, int bnd, int precis
 int autotune_save(const char *path);
 int autotune_load(const char *path);
 void autotune_clear();
+
+// Learned surrogate of the spectral energies.
+int64_t surrogate_param_count();
+size_t surrogate_ws_bytes(sal_dims d, bool training);
+cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *params, float *E, bool training,
+                              void *ws, cudaStream_t s);
+cudaError_t surrogate_backward(const float *V, sal_dims d, int bnd, const float *params, const float *Etarget,
+                               int margin, float *grads, double *loss, void *ws, cudaStream_t s);
+size_t surrogate_infer_ws_bytes(sal_dims d, int L);
+cudaError_t surrogate_infer(const float *V, sal_dims d, int L, int bnd, const float *params, float *E, float thr,
+                            int *counts, void *ws, cudaStream_t s);
+cudaError_t surrogate_adam(float *params, const float *grads, float *m, float *v, int64_t n, int step, float lr,
+                           float b1, float b2, float eps, cudaStream_t s);
 
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s);

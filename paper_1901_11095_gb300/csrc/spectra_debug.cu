@@ -9,10 +9,6 @@ namespace sal {
 
 namespace {
 
-struct Twiddles {
-    float cs[16], sn[16];
-};
-
 __device__ __forceinline__ int mod_l(int v, int L)
 {
     int r = v % L;
@@ -22,16 +18,32 @@ __device__ __forceinline__ int mod_l(int v, int L)
 // One CTA per voxel of the region; the three mode products run on the whole cube in
 // shared memory.  Samples are taken relative to the cube's centre sample, which changes
 // no off-DC coefficient and makes a constant cube's off-DC spectrum exactly zero.
+// POINTS = false: voxels of the box lt.. + et.. (C order), |F| written to `mag`;
+// POINTS = true: voxels coords[k] (t, x, y), E_m written to E[m * n + k] (Eq. 1-4 and the
+// non-DC mean), via the same spectrum.
+template <bool POINTS>
 __global__ void __launch_bounds__(256) local_spectra_kernel(const float *__restrict__ V, int64_t T, int64_t X,
                                                             int64_t Y, int L, int bnd, int64_t lt, int64_t lx,
                                                             int64_t ly, int64_t et, int64_t ex, int64_t ey,
-                                                            float *__restrict__ mag, const __grid_constant__ Twiddles tw)
+                                                            const int64_t *__restrict__ coords, int64_t npts,
+                                                            float *__restrict__ mag, float *__restrict__ Eout,
+                                                            const __grid_constant__ SpecTables tw)
 {
     extern __shared__ __align__(16) float2 dyn[];   // g1[n3], g2[n3], f[n3]
     __shared__ float red[8];
+    __shared__ float redE[8][3];
     const int64_t v = blockIdx.x;
-    const int64_t vy = v % ey, vx = (v / ey) % ex, vt = v / (ey * ex);
-    const int64_t t = lt + vt, x = lx + vx, y = ly + vy;
+    int64_t t, x, y;
+    if (POINTS) {
+        t = coords[3 * v];
+        x = coords[3 * v + 1];
+        y = coords[3 * v + 2];
+    } else {
+        const int64_t vy = v % ey, vx = (v / ey) % ex, vt = v / (ey * ex);
+        t = lt + vt;
+        x = lx + vx;
+        y = ly + vy;
+    }
     const int h = (L - 1) / 2, n3 = L * L * L;
     float2 *g1 = dyn, *g2 = dyn + n3;
     float *f = reinterpret_cast<float *>(dyn + 2 * n3);
@@ -81,7 +93,8 @@ __global__ void __launch_bounds__(256) local_spectra_kernel(const float *__restr
     __syncthreads();
     // stage y and magnitude
     const float inv = 1.f / (float)n3;
-    float *out = mag + v * n3;
+    float *out = POINTS ? nullptr : mag + v * n3;
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
     for (int i = threadIdx.x; i < n3; i += blockDim.x) {
         const int a = i / (L * L), b = (i / L) % L, c = i % L, om = c - h;
         float re = 0.f, im = 0.f;
@@ -91,9 +104,34 @@ __global__ void __launch_bounds__(256) local_spectra_kernel(const float *__restr
             re += z.x * tw.cs[k] + z.y * tw.sn[k];
             im += z.y * tw.cs[k] - z.x * tw.sn[k];
         }
-        out[i] = sqrtf(re * re + im * im) * inv;
+        const float m = sqrtf(re * re + im * im) * inv;
+        if (POINTS) {
+            const float *w = &tw.w[((abs(a - h) * kMaxHalf + abs(b - h)) * kMaxHalf + abs(om)) * 3];   // 0 at DC
+            e0 = fmaf(w[0], m, e0);
+            e1 = fmaf(w[1], m, e1);
+            e2 = fmaf(w[2], m, e2);
+        } else {
+            out[i] = m;
+        }
     }
-    if (threadIdx.x == 0) {
+    if (POINTS) {
+        for (int o = 16; o; o >>= 1) {
+            e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            redE[threadIdx.x >> 5][0] = e0;
+            redE[threadIdx.x >> 5][1] = e1;
+            redE[threadIdx.x >> 5][2] = e2;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            float s = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += redE[w][threadIdx.x];
+            Eout[threadIdx.x * npts + v] = s / (float)(n3 - 1);
+        }
+    } else if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         out[(h * L + h) * L + h] = fabsf(s) * inv;
@@ -141,16 +179,26 @@ cudaError_t launch_local_spectra(const float *V, sal_dims d, int L, int bnd, con
     if (n > 0x7fffffffLL) return cudaErrorInvalidValue;
     SpecTables tb;
     make_tables(L, &tb);
-    Twiddles tw;
-    for (int i = 0; i < 16; ++i) {
-        tw.cs[i] = tb.cs[i];
-        tw.sn[i] = tb.sn[i];
-    }
     const size_t smem = (size_t)L * L * L * (2 * sizeof(float2) + sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(local_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem(local_spectra_kernel<false>, smem);
     if (e != cudaSuccess) return e;
-    local_spectra_kernel<<<(unsigned)n, 256, smem, s>>>(V, d.T, d.X, d.Y, L, bnd, lo[0], lo[1], lo[2], ext[0], ext[1],
-                                                     ext[2], mag, tw);
+    local_spectra_kernel<false><<<(unsigned)n, 256, smem, s>>>(V, d.T, d.X, d.Y, L, bnd, lo[0], lo[1], lo[2], ext[0],
+                                                            ext[1], ext[2], nullptr, 0, mag, nullptr, tb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_points(const float *V, sal_dims d, int L, int bnd, const int64_t *coords, int64_t n, float *E,
+                                 cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    SpecTables tb;
+    make_tables(L, &tb);
+    const size_t smem = (size_t)L * L * L * (2 * sizeof(float2) + sizeof(float));
+    cudaError_t e = set_smem(local_spectra_kernel<true>, smem);
+    if (e != cudaSuccess) return e;
+    local_spectra_kernel<true><<<(unsigned)n, 256, smem, s>>>(V, d.T, d.X, d.Y, L, bnd, 0, 0, 0, 1, 1, 1, coords, n,
+                                                           nullptr, E, tb);
     return cudaGetLastError();
 }
 
