@@ -338,6 +338,95 @@ def run_sweep(args) -> None:
                               "samples": int(coords.shape[0])}), flush=True)
 
 
+def run_surrogate(args) -> None:
+    """The learned surrogate: trained on seeded 128^3 volumes labelled by the plain method,
+    then inference on the F3-shaped volume with the per-block fallback (threshold 2e-2).
+    Prints one JSON line: speed of the surrogate path and of the plain path, errors of the
+    surrogate against the plain GPU method, fraction of blocks recomputed."""
+    import torch
+
+    from paper_1901_11095_gb300 import api, surrogate, synth
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    p = api.params(L=args.L)
+    t0 = time.perf_counter()
+    vols, labels = [], []
+    for i in range(args.train_volumes):
+        V = torch.from_numpy(synth.make_volume((128, 128, 128), seed=100 + i, kind="f3")).to(dev)
+        vols.append(V)
+        labels.append(api.sal_spectral_energy(V, p))
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    model = surrogate.Surrogate(dev, seed=0)
+    t0 = time.perf_counter()
+    hist = surrogate.train(model, vols, labels, steps=args.train_steps, crop=48, lr=3e-3, lr_final=3e-4, seed=1,
+                           log_every=max(1, args.train_steps // 20))
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del vols, labels
+
+    shape, kind, seed = WORKLOADS["f3"]
+    V = torch.from_numpy(synth.make_volume(shape, seed=seed, kind=kind)).to(dev)
+    N = V.numel()
+    E_plain = api.sal_spectral_energy(V, p)
+    Sm, st = api.sal_directional_compare(E_plain, p)
+    S_plain = api.sal_combine(Sm, st, p)
+    E = torch.empty_like(E_plain)
+    S = torch.empty_like(V)
+    dcs_ws = torch.empty(api.sal_dcs_workspace_size(api.dims_of(V), p), device=dev, dtype=torch.uint8)
+
+    def surr_path(thr):
+        _, counts = model.infer(V, p, threshold=thr, E=E)
+        api.sal_directional_compare(E, p, Sm=Sm, stats=st, ws=dcs_ws)
+        api.sal_combine(Sm, st, p, S=S)
+        return counts
+
+    def plain_path():
+        api.sal_spectral_energy(V, p, E=E)
+        api.sal_directional_compare(E, p, Sm=Sm, stats=st, ws=dcs_ws)
+        api.sal_combine(Sm, st, p, S=S)
+
+    out = {"impl": "surrogate", "metric": "saliency voxels/s", "unit": "voxels/s", "data": "synthetic",
+           "config": {"workload": f"learned surrogate (5 x 3x3x3 conv, 24 channels, GELU, BF16 weights) trained on "
+                                  f"{args.train_volumes} seeded 128^3 F3-kind volumes (3 faults, dome) labelled by "
+                                  f"the plain FP32 method, "
+                                  f"inference on the F3-shaped {shape[0]}x{shape[1]}x{shape[2]} volume, L={args.L}"},
+           "training": {"volumes": args.train_volumes, "steps": args.train_steps, "crop": 48,
+                        "seconds": t_train, "label_seconds": t_data, "loss_first": hist[0][1],
+                        "loss_last": hist[-1][1]}}
+    for name, thr in (("fallback_2e-2", 2e-2), ("surrogate_only", 1e30)):
+        counts = surr_path(thr)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            counts = surr_path(thr)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        errE = [float((E[m] - E_plain[m]).abs().max() / E_plain[m].abs().max()) for m in range(3)]
+        errL2 = [float(torch.linalg.vector_norm((E[m] - E_plain[m]).double()) /
+                       torch.linalg.vector_norm(E_plain[m].double())) for m in range(3)]
+        errS = float(torch.linalg.vector_norm((S - S_plain).double()) / torch.linalg.vector_norm(S_plain.double()))
+        out[name] = {"voxels_per_s": N / (ms / 1e3), "ms_per_step": ms, "E_err_vs_plain_normwise": errE,
+                     "E_rel_l2_vs_plain": errL2,
+                     "S_rel_l2_vs_plain": errS, "blocks_recomputed": int(counts[0]), "blocks": int(counts[1])}
+    plain_path()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plain_path()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    out["plain_fp32"] = {"voxels_per_s": N / (ms / 1e3), "ms_per_step": ms}
+    out["value"] = out["fallback_2e-2"]["voxels_per_s"]
+    out["speedup_vs_plain"] = out["value"] / out["plain_fp32"]["voxels_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank: int, world: int) -> None:
     import torch
     import torch.distributed as dist
@@ -478,6 +567,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
+    ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and time its inference")
+    ap.add_argument("--train-volumes", type=int, default=200)
+    ap.add_argument("--train-steps", type=int, default=3000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -493,6 +585,9 @@ def main():
     __graft_entry__.build()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.surrogate:
+        run_surrogate(args)
         return
     (run_batch if args.workload == "batch64" else run_ours)(args, rank, world)
     if world > 1:

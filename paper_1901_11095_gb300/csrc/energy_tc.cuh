@@ -505,8 +505,19 @@ cudaError_t launch_energy_tc_impl(const EVolDesc *vols, int n, int bnd, bool per
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, G::SMEM);
     if (e != cudaSuccess) return e;
     (void)persistent;
-    // tensor memory of the resident CTAs of one SM must fit its 512 columns
+    // the occupancy query can answer for a smaller shared-memory carveout than the launch
+    // gets; size the persistent grid from the per-SM limits directly: shared memory (228 KB
+    // per SM, 1 KB reserved per CTA), registers, and the 512 tensor-memory columns
+    int smem_per_sm = 0, regs_per_sm = 0;
+    cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    int by_regs = 4;
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
+        by_regs = regs_per_sm / (((fa.numRegs + 7) / 8 * 8) * G::NT);
+    const int by_smem = smem_per_sm > 0 ? smem_per_sm / (int)(G::SMEM + 1024) : 1;
     const int by_tmem = 512 / G::TMEM_COLS;
+    per_sm = by_smem < by_regs ? by_smem : by_regs;
     if (per_sm > by_tmem) per_sm = by_tmem;
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > total) grid = total;
