@@ -41,23 +41,24 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
-def algorithmic_flops_per_voxel(L: int) -> int:
-    """FP32 flops per voxel of the fused energy stage as the algorithm defines it (FMA = 2).
+def algorithmic_flops_per_voxel(L: int, R: int = 4) -> float:
+    """FP32 flops per voxel of the fused energy stage as the kernel's algorithm defines it (FMA = 2).
 
-    Separable real-input DFT with the +-k folding (stage t on the real cube columns, stage
-    x on the mu >= 0 half, stage y per voxel), |F| (mul + fma + sqrt), the projection
-    weights (3 FMAs per (mu, |nu|, |omega|) group) and the final scale.  Each stage is
-    counted once per voxel, i.e. without the halo recomputation of a tiled kernel.
+    Stage t on the real cube columns and stage x on the mu >= 0 half, each once per voxel
+    column (no halo recomputation); stage y per line over strips of R windows: window 0 by
+    the +-k folded direct DFT, its rotation to the sliding phase, R - 1 sliding updates;
+    |F| = mul + add (or fma) + sqrt; 3 FMAs per (mu, |nu|, |omega|) weight group; final scale.
     """
     H = (L - 1) // 2
     real_pass = 5 * H + 4 * H * H                  # t stage, and x stage of mu = 0
     cplx_pass = 10 * H + 8 * H * H + 4 * H         # x stage of one mu > 0
-    cline = 10 * H + 4 + H * (8 * H + 13)          # y stage: one complex line (all omega)
-    rline = 4 * H + H * (4 * H + 4)                # y stage: the real (0, 0) line
+    rot = 1 if R > 1 else 0
+    cline = 10 * H + 4 + H * (8 * H + 9) + rot * 18 * H + (R - 1) * (9 + 25 * H)
+    rline = 4 * H + H * (4 * H + 4) + rot * 9 * H + (R - 1) * (2 + 12 * H)
     n_cl = H + H * (2 * H + 1)
     groups = H + H * (H + 1) + H * (H + 1) ** 2
     pair_adds = H * H * (H + 1)
-    y = n_cl * cline + rline + 6 * groups + pair_adds
+    y = (n_cl * cline + rline) / R + 6 * groups + pair_adds
     return real_pass + (real_pass + H * cplx_pass) + y + 3
 
 

@@ -104,76 +104,6 @@ __device__ __forceinline__ void stage_tile(const float *__restrict__ Em, float *
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// The same staging for the 26-neighbourhood, with its geometry fixed at compile time
-// (10 planes x 10 rows x 66 columns, pitch 72, column c stored at c + 3).
-__device__ __forceinline__ void stage_tile26(const float *__restrict__ Em, float *sE, int64_t T, int64_t X, int64_t Y,
-                                             int bnd, int64_t t0, int64_t x0, int64_t y0)
-{
-    constexpr int PX = DX + 2, PITCH = 72, OFF = 3, W = DY + 2, ROWS = (DT + 2) * PX;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool y_inside = y0 >= 1 && y0 + DY + 1 <= Y;
-#pragma unroll 2
-    for (int r = warp; r < ROWS; r += DNT / 32) {
-        const int a = r / PX, b = r - a * PX;
-        const int64_t gt = ext_index(t0 - 1 + a, T, bnd);
-        const int64_t gx = ext_index(x0 - 1 + b, X, bnd);
-        const float *rowp = Em + (gt * X + gx) * Y;
-        float *dst = sE + r * PITCH + OFF;
-        if (y_inside) {
-            const float *src = rowp + (y0 - 1);
-#pragma unroll
-            for (int c = lane; c < W; c += 32) cp_async4(dst + c, src + c);
-        } else {
-#pragma unroll
-            for (int c = lane; c < W; c += 32) cp_async4(dst + c, rowp + ext_index(y0 - 1 + c, Y, bnd));
-        }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// 26-neighbourhood: out[to][yo] = sum_o |c - g(o) n| for this thread's 4 x 4 block.
-__device__ __forceinline__ void dcs26(const float *sE, const Halo &hl, int tq, int x, int yq, const DcsConsts &k,
-                                      float (&out)[QT][QY])
-{
-    // halo indices: plane 4tq + p, row x + b, column 4yq + c (c = 0..5) at storage + off
-    const float *base = sE + (QT * tq) * hl.PP + x * hl.pitch + hl.off + QY * yq;
-    const float g[4] = {0.f, k.g[1], k.g[2], k.g[3]};
-    float cen[QT][QY];
-#pragma unroll
-    for (int to = 0; to < QT; ++to) {
-        const float *row = base + (to + 1) * hl.PP + hl.pitch + 1;
-#pragma unroll
-        for (int yo = 0; yo < QY; ++yo) {
-            cen[to][yo] = row[yo];
-            out[to][yo] = 0.f;
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < QT + 2; ++p)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const float *row = base + p * hl.PP + b * hl.pitch;
-            float w[QY + 2];
-            w[0] = row[0];
-            const float4 mid = *reinterpret_cast<const float4 *>(row + 1);
-            w[1] = mid.x; w[2] = mid.y; w[3] = mid.z; w[4] = mid.w;
-            w[5] = row[5];
-#pragma unroll
-            for (int to = 0; to < QT; ++to) {
-                const int dt = p - (to + 1);
-                if (dt < -1 || dt > 1) continue;
-#pragma unroll
-                for (int yo = 0; yo < QY; ++yo)
-#pragma unroll
-                    for (int cc = -1; cc <= 1; ++cc) {
-                        const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
-                        if (d2 == 0) continue;
-                        out[to][yo] += fabsf(fmaf(-g[d2], w[yo + 1 + cc], cen[to][yo]));
-                    }
-            }
-        }
-}
-
 // d x 1 line along axis m: out = sum_{q=1..h} |c - g(q) n(+q)| + |c - g(q) n(-q)|.
 __device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m, int tq, int x, int yq,
                                          const DcsConsts &k, float (&out)[QT][QY])
@@ -195,8 +125,8 @@ __device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m,
         }
 }
 
-// One map m of one output tile of one volume; writes the tile's (min, max, sum) record.
-template <int STENCIL>
+// Line stencil: one map m of one output tile of one volume; writes the tile's (min, max,
+// sum) record.
 __device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y, int bnd,
                                          int m, int64_t tile, int tiles_x, int tiles_y, float *__restrict__ Sm,
                                          double *__restrict__ partials, int64_t nparts, const DcsConsts &k, float *sE,
@@ -207,22 +137,16 @@ __device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T,
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
     const int64_t t0 = tt * DT, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
     const int64_t N = T * X * Y;
-    const Halo hl = halo_for(STENCIL, m, k.h);
+    const Halo hl = halo_for(SAL_STENCIL_LINE, m, k.h);
 
-    if (STENCIL == SAL_STENCIL_26)
-        stage_tile26(E + m * N, sE, T, X, Y, bnd, t0, x0, y0);
-    else
-        stage_tile(E + m * N, sE, hl, T, X, Y, bnd, t0, x0, y0);
+    stage_tile(E + m * N, sE, hl, T, X, Y, bnd, t0, x0, y0);
     __syncthreads();
 
     const int yq = threadIdx.x % (DY / QY);
     const int x = (threadIdx.x / (DY / QY)) % DX;
     const int tq = threadIdx.x / ((DY / QY) * DX);
     float out[QT][QY];
-    if (STENCIL == SAL_STENCIL_26)
-        dcs26(sE, hl, tq, x, yq, k, out);
-    else
-        dcs_line(sE, hl, m, tq, x, yq, k, out);
+    dcs_line(sE, hl, m, tq, x, yq, k, out);
 
     float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
     const int64_t gx = x0 + x, gy = y0 + QY * yq;
@@ -287,8 +211,8 @@ struct DBatch {
     DVol v[kMaxBatch];
 };
 
-template <int STENCIL>
-__global__ void __launch_bounds__(DNT) dcs_kernel(const __grid_constant__ DBatch bt, const __grid_constant__ DcsConsts k)
+__global__ void __launch_bounds__(DNT) dcs_line_kernel(const __grid_constant__ DBatch bt,
+                                                       const __grid_constant__ DcsConsts k)
 {
     extern __shared__ __align__(16) float sE[];
     __shared__ double red[DNT / 32][3];
@@ -301,8 +225,193 @@ __global__ void __launch_bounds__(DNT) dcs_kernel(const __grid_constant__ DBatch
         const DVol &v = bt.v[lo];
         const int64_t local = it - v.item0;
         const int m = (int)(local / v.tiles);
-        dcs_tile<STENCIL>(v.E, v.T, v.X, v.Y, bt.bnd, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm, v.part,
-                          v.tiles, k, sE, red);
+        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm, v.part, v.tiles, k,
+                 sE, red);
+        __syncthreads();
+    }
+}
+
+// ---- 26-neighbourhood, planes streamed along t ------------------------------------------
+// One work item = (volume, map, chunk of SC planes along t, 8 x 64 column block (x, y)).  The
+// CTA walks its chunk in steps of DT = 8 output planes.  The halo planes of E_m (10 rows x
+// 66 columns each) pass through a ring of RING plane slots in shared memory: the 8 planes of
+// the next step are copied asynchronously while the current step is computed, each halo
+// value is read once per chunk (plus the two boundary planes of the chunk), and the boundary
+// extension and index set-up are paid once per item instead of once per copy.
+constexpr int SC = 64;                          // output planes per chunk
+constexpr int RING = 18;                        // plane slots: 10 being read + 8 in flight
+constexpr int PROW = 72;                        // slot row pitch (floats); halo column c at c + 3
+constexpr int PSLOT = (DX + 2) * PROW;          // one plane slot (floats)
+constexpr int PEL = (DX + 2) * (DY + 2);        // halo elements of one plane
+constexpr int KEL = (PEL + DNT - 1) / DNT;      // copies per thread and plane
+constexpr size_t kSmem26 = (size_t)RING * PSLOT * sizeof(float);
+static_assert(SC % DT == 0, "a chunk is whole steps");
+static_assert(RING >= DT + 2 + DT, "ring holds a step's planes and the next step's");
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Reduces the CTA's (min, max, sum) into record `rec` of map m (FP64 across warps).
+__device__ __forceinline__ void write_record(float mn, float mx, float sm, double (*red)[3], double *__restrict__ part,
+                                             int m, int64_t nrec, int64_t rec)
+{
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    sm = warp_sum(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[warp][0] = mn;
+        red[warp][1] = mx;
+        red[warp][2] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int q = threadIdx.x;
+        double v = red[0][q];
+        for (int w = 1; w < DNT / 32; ++w) {
+            const double u = red[w][q];
+            v = q == 0 ? fmin(v, u) : (q == 1 ? fmax(v, u) : v + u);
+        }
+        part[(3 * m + q) * nrec + rec] = v;
+    }
+}
+
+__global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ DBatch bt, const __grid_constant__ DcsConsts k)
+{
+    extern __shared__ __align__(16) float sE[];
+    __shared__ double red[DNT / 32][3];
+    const float g1 = k.g[1], g2 = k.g[2], g3 = k.g[3];
+    const int tid = threadIdx.x;
+    const int yq = tid % (DY / QY), x = (tid / (DY / QY)) % DX, tq = tid / ((DY / QY) * DX);
+    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
+        int lo = 0, hi = bt.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        const DVol &v = bt.v[lo];
+        const int64_t local = it - v.item0;
+        const int m = (int)(local / v.tiles);
+        const int64_t rec = local - m * v.tiles;
+        const int ty = (int)(rec % v.tiles_y);
+        const int tx = (int)((rec / v.tiles_y) % v.tiles_x);
+        const int64_t ck = rec / ((int64_t)v.tiles_y * v.tiles_x);
+        const int64_t T = v.T, X = v.X, Y = v.Y, XY = X * Y;
+        const int64_t t0 = ck * SC, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
+        const float *Em = v.E + m * T * XY;
+        float *Sm = v.Sm + m * T * XY;
+
+        // this thread's copies within one plane: source offset in the plane, slot offset
+        int64_t goff[KEL];
+        int soff[KEL];
+#pragma unroll
+        for (int q = 0; q < KEL; ++q) {
+            const int e = tid + q * DNT;
+            const int b = e / (DY + 2), c = e - b * (DY + 2);
+            goff[q] = e < PEL ? ext_index(x0 - 1 + b, X, bt.bnd) * Y + ext_index(y0 - 1 + c, Y, bt.bnd) : 0;
+            soff[q] = e < PEL ? b * PROW + 3 + c : -1;
+        }
+        // copies halo planes r0 .. r1 - 1 of the chunk (plane r is t0 - 1 + r) into their slots
+        auto stage = [&](int r0, int r1) {
+            int slot = r0 % RING;
+            for (int r = r0; r < r1; ++r) {
+                const float *src = Em + ext_index(t0 - 1 + r, T, bt.bnd) * XY;
+                float *dst = sE + slot * PSLOT;
+#pragma unroll
+                for (int q = 0; q < KEL; ++q)
+                    if (soff[q] >= 0) cp_async4(dst + soff[q], src + goff[q]);
+                slot = slot + 1 == RING ? 0 : slot + 1;
+            }
+            cp_async_commit();
+        };
+
+        const int64_t left = T - t0;
+        const int nsteps = (int)(((left < SC ? left : SC) + DT - 1) / DT);
+        const int64_t gx = x0 + x, gy = y0 + QY * yq;
+        const bool vec = gy + QY <= Y && (Y & 3) == 0;
+        float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
+
+        stage(0, DT + 2);
+        for (int st = 0; st < nsteps; ++st) {
+            if (st + 1 < nsteps) {
+                stage(DT * st + DT + 2, DT * st + 2 * DT + 2);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+
+            // halo planes rb .. rb + 5 of this thread's 4 output planes, rows x .. x + 2,
+            // columns 4 yq .. 4 yq + 5 (stored at + 3)
+            const int rb = DT * st + QT * tq;
+            int sl[QT + 2];
+#pragma unroll
+            for (int p = 0; p < QT + 2; ++p) {
+                const int sp = (rb + p) % RING;
+                sl[p] = sp * PSLOT + x * PROW + QY * yq + 3;
+            }
+            float cen[QT][QY], out[QT][QY];
+#pragma unroll
+            for (int to = 0; to < QT; ++to) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(sE + sl[to + 1] + PROW + 1);
+                cen[to][0] = c4.x; cen[to][1] = c4.y; cen[to][2] = c4.z; cen[to][3] = c4.w;
+#pragma unroll
+                for (int yo = 0; yo < QY; ++yo) out[to][yo] = 0.f;
+            }
+#pragma unroll
+            for (int p = 0; p < QT + 2; ++p)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const float *row = sE + sl[p] + b * PROW;
+                    float w[QY + 2];
+                    w[0] = row[0];
+                    const float4 mid = *reinterpret_cast<const float4 *>(row + 1);
+                    w[1] = mid.x; w[2] = mid.y; w[3] = mid.z; w[4] = mid.w;
+                    w[5] = row[5];
+#pragma unroll
+                    for (int to = 0; to < QT; ++to) {
+                        const int dt = p - (to + 1);
+                        if (dt < -1 || dt > 1) continue;
+#pragma unroll
+                        for (int yo = 0; yo < QY; ++yo)
+#pragma unroll
+                            for (int cc = -1; cc <= 1; ++cc) {
+                                const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
+                                if (d2 == 0) continue;
+                                const float g = d2 == 1 ? g1 : (d2 == 2 ? g2 : g3);
+                                out[to][yo] += fabsf(fmaf(-g, w[yo + 1 + cc], cen[to][yo]));
+                            }
+                    }
+                }
+
+            if (gx < X) {
+#pragma unroll
+                for (int to = 0; to < QT; ++to) {
+                    const int64_t gt = t0 + rb + to;
+                    if (gt >= T) break;
+                    float *o = Sm + (gt * X + gx) * Y + gy;
+#pragma unroll
+                    for (int yo = 0; yo < QY; ++yo) {
+                        out[to][yo] *= k.invQ;
+                        if (gy + yo < Y) {
+                            mn = fminf(mn, out[to][yo]);
+                            mx = fmaxf(mx, out[to][yo]);
+                            sm += out[to][yo];
+                        }
+                    }
+                    if (vec) {
+                        *reinterpret_cast<float4 *>(o) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
+                    } else {
+#pragma unroll
+                        for (int yo = 0; yo < QY; ++yo)
+                            if (gy + yo < Y) o[yo] = out[to][yo];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        write_record(mn, mx, sm, red, v.part, m, v.tiles, rec);
         __syncthreads();
     }
 }
@@ -399,10 +508,20 @@ DcsConsts dcs_consts(const sal_params *p)
     return k;
 }
 
-// Launches the compare over n volumes (persistent grid when batched).
+int64_t dcs_num_records(sal_dims d, int stencil)
+{
+    int64_t nt, nx, ny;
+    dcs_tiles(d, &nt, &nx, &ny);
+    if (stencil == SAL_STENCIL_26) nt = (d.T + SC - 1) / SC;
+    return nt * nx * ny;
+}
+
+// Launches the compare over n volumes (persistent grid when batched; the 26-neighbourhood
+// kernel is always persistent).
 cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    const bool s26 = p->stencil == SAL_STENCIL_26;
     DBatch bt;
     bt.n = n;
     bt.bnd = p->boundary;
@@ -418,7 +537,7 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         v.T = d.T;
         v.X = d.X;
         v.Y = d.Y;
-        v.tiles = nt * nx * ny;
+        v.tiles = dcs_num_records(d, p->stencil);
         v.tiles_x = (int)nx;
         v.tiles_y = (int)ny;
         v.item0 = total;
@@ -427,17 +546,19 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     bt.total = total;
     const DcsConsts k = dcs_consts(p);
     const int h = (p->L - 1) / 2;
-    int smem = 0;
-    for (int m = 0; m < 3; ++m) {
-        const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
-        smem = f > smem ? f : smem;
+    int smem = (int)kSmem26;
+    if (!s26) {
+        smem = 0;
+        for (int m = 0; m < 3; ++m) {
+            const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
+            smem = f > smem ? f : smem;
+        }
     }
-    const void *fn = p->stencil == SAL_STENCIL_26 ? (const void *)dcs_kernel<SAL_STENCIL_26>
-                                                  : (const void *)dcs_kernel<SAL_STENCIL_LINE>;
+    const void *fn = s26 ? (const void *)dcs26_kernel : (const void *)dcs_line_kernel;
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = total;
-    if (persistent) {
+    if (persistent || s26) {
         int dev = 0, nsm = 0, per_sm = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -448,19 +569,17 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     }
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (p->stencil == SAL_STENCIL_26)
-        dcs_kernel<SAL_STENCIL_26><<<(unsigned)grid, DNT, smem, s>>>(bt, k);
+    if (s26)
+        dcs26_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
     else
-        dcs_kernel<SAL_STENCIL_LINE><<<(unsigned)grid, DNT, smem, s>>>(bt, k);
+        dcs_line_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials, double *stats,
                        cudaStream_t s)
 {
-    int64_t nt, nx, ny;
-    dcs_tiles(d, &nt, &nx, &ny);
-    const int64_t tiles = nt * nx * ny;
+    const int64_t tiles = dcs_num_records(d, p->stencil);
     if (3 * tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     DVolDesc v{E, Sm, partials, d.T, d.X, d.Y};
     cudaError_t e = launch_dcs_items(&v, 1, p, false, s);

@@ -43,7 +43,8 @@ struct EGeo {
     static constexpr int NG1 = (BT * HX * L * PY + 3) / 4 * 4;
     static constexpr int NG2 = ROWS * L * PY2;          // float2 of one mu-slice of G2
     static constexpr int NALIAS = (NV * 4 > NG2 * 8) ? NV : NG2 * 2;
-    static constexpr size_t SMEM = sizeof(float) * (size_t)(NG1 + NALIAS);
+    static constexpr int NW = ((H + 1) * (H + 1) * (H + 1) * 3 + 3) / 4 * 4;   // projection weights
+    static constexpr size_t SMEM = sizeof(float) * (size_t)(NG1 + NALIAS + NW);
     static constexpr int NZ = R + 2 * H;                // window of one thread's R outputs
 };
 
@@ -179,6 +180,119 @@ __device__ __forceinline__ void line_mags_real(const f2x (&Z)[NZ], int c, const 
     }
 }
 
+// P := P + d * e^{-i 2 pi k / L} for the twiddle index k (packed complex, dsw = (d.im, -d.re)).
+template <int L>
+__device__ __forceinline__ f2x rot_acc(f2x P, f2x d, f2x dsw, const Tw<L> &tw, int k)
+{
+    return fma2(dsw, tw.s2[k], fma2(d, tw.c2[k], P));
+}
+
+__device__ __forceinline__ f2x swapneg(f2x d) { return pk(hi(d), -lo(d)); }
+
+__device__ __forceinline__ float cabs2(f2x v)
+{
+    const f2x q = mul2(v, v);
+    return lo(q) + hi(q);
+}
+
+// Magnitudes of the R consecutive windows of one complex line, window r centred at
+// Z[H + r]: m[r][0] = |F_r(0)|, m[r][w] = |F_r(w)| + |F_r(-w)|.  Window 0 by the folded
+// direct DFT; the others by the sliding recurrence on P_r(w) = sum_{n=r}^{r+2h} Z[n]
+// e^{-i th w n} (|P_r| = |F_r|): P_{r+1} = P_r + (Z[r+2h+1] - Z[r]) e^{-i th w r}, the
+// twiddles of a whole period being equal.  P_0(w) = e^{-i th w h} F_0(w).
+template <int L, int R, int NZ>
+__device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
+{
+    constexpr int H = (L - 1) / 2;
+    const f2x z0 = Z[H];
+    const f2x m2 = pk(-2.f, -2.f);
+    f2x U[H + 1], D[H + 1];
+    f2x s = z0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const f2x p = add2(Z[H + k], Z[H - k]);
+        s = add2(s, p);
+        U[k] = fma2(z0, m2, p);
+        D[k] = sub2(Z[H + k], Z[H - k]);
+    }
+    f2x P[L];          // P[H + w] for w = -H..H
+    P[H] = s;
+    m[0][0] = sqrt_approx(cabs2(s));
+#pragma unroll
+    for (int w = 1; w <= H; ++w) {
+        f2x A = mul2(U[1], tw.c2[w % L]);
+        f2x B = mul2(D[1], tw.s2[w % L]);
+#pragma unroll
+        for (int k = 2; k <= H; ++k) {
+            A = fma2(U[k], tw.c2[(w * k) % L], A);
+            B = fma2(D[k], tw.s2[(w * k) % L], B);
+        }
+        const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+        const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
+        const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
+        m[0][w] = sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm));
+        if (R > 1) {
+            const f2x zero = pk(0.f, 0.f);
+            P[H + w] = rot_acc<L>(zero, Fp, swapneg(Fp), tw, (w * H) % L);
+            P[H - w] = rot_acc<L>(zero, Fm, swapneg(Fm), tw, (L - (w * H) % L) % L);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r + 1 < R; ++r) {
+        const f2x d = sub2(Z[r + 2 * H + 1], Z[r]);
+        const f2x dsw = swapneg(d);
+        P[H] = add2(P[H], d);
+#pragma unroll
+        for (int w = 1; w <= H; ++w) {
+            P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, (w * r) % L);
+            P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, (L - (w * r) % L) % L);
+        }
+        m[r + 1][0] = sqrt_approx(cabs2(P[H]));
+#pragma unroll
+        for (int w = 1; w <= H; ++w) m[r + 1][w] = sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w]));
+    }
+}
+
+// The same for the real mu = 0, nu = 0 line: m[r][w] = |F_r(w)| for w = 1..H only (the -w
+// point is the conjugate mirror, counted by the half-spectrum factor); m[r][0] unused.
+template <int L, int R, int NZ>
+__device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
+{
+    constexpr int H = (L - 1) / 2;
+    const float z0 = lo(Z[H]);
+    float U[H + 1], D[H + 1];
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        U[k] = fmaf(-2.f, z0, lo(Z[H + k]) + lo(Z[H - k]));
+        D[k] = lo(Z[H + k]) - lo(Z[H - k]);
+    }
+    f2x P[H + 1];
+#pragma unroll
+    for (int w = 1; w <= H; ++w) {
+        float A = 0.f, B = 0.f;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            A = fmaf(U[k], lo(tw.c2[(w * k) % L]), A);
+            B = fmaf(D[k], lo(tw.s2[(w * k) % L]), B);
+        }
+        const f2x F = pk(A, -B);                 // F(w) = A - iB
+        m[0][w] = sqrt_approx(fmaf(A, A, B * B));
+        if (R > 1) P[w] = rot_acc<L>(pk(0.f, 0.f), F, swapneg(F), tw, (w * H) % L);
+    }
+    m[0][0] = 0.f;
+#pragma unroll
+    for (int r = 0; r + 1 < R; ++r) {
+        const f2x d = pk(lo(Z[r + 2 * H + 1]) - lo(Z[r]), 0.f);
+        const f2x dsw = swapneg(d);
+#pragma unroll
+        for (int w = 1; w <= H; ++w) {
+            P[w] = rot_acc<L>(P[w], d, dsw, tw, (w * r) % L);
+            m[r + 1][w] = sqrt_approx(cabs2(P[w]));
+        }
+        m[r + 1][0] = 0.f;
+    }
+}
+
 template <class G>
 __device__ __forceinline__ void load_line(const float2 *sG2, int row, int nu, int j, f2x (&Z)[G::NZ])
 {
@@ -192,16 +306,28 @@ __device__ __forceinline__ void load_line(const float2 *sG2, int row, int nu, in
     }
 }
 
-// Projection weights of the (mu, |nu|) group for omega = 0..H, from the parameter bank.
+// Projection weights of the (mu, |nu|) group for omega = 0..H, from the shared copy
+// sW[((mu * (H+1) + nu) * (H+1) + omega) * 3 + m].
 template <class G>
-__device__ __forceinline__ void load_w(const SpecTables &tb, int mu, int nu, float (&w)[G::H + 1][3])
+__device__ __forceinline__ void load_w(const float *sW, int mu, int nu, float (&w)[G::H + 1][3])
 {
-    const float *src = &tb.w[(mu * kMaxHalf + nu) * kMaxHalf * 3];
+    const float *src = sW + ((mu * (G::H + 1) + nu) * (G::H + 1)) * 3;
 #pragma unroll
     for (int om = 0; om <= G::H; ++om) {
         w[om][0] = src[om * 3];
         w[om][1] = src[om * 3 + 1];
         w[om][2] = src[om * 3 + 2];
+    }
+}
+
+// Copies the weights of this cube size from the parameter bank into sW.
+template <class G>
+__device__ __forceinline__ void fill_w(float *sW, const SpecTables &tb)
+{
+    constexpr int HP = G::H + 1;
+    for (int e = threadIdx.x; e < HP * HP * HP * 3; e += G::NT) {
+        const int m = e % 3, om = (e / 3) % HP, nu = (e / (3 * HP)) % HP, mu = e / (3 * HP * HP);
+        sW[e] = tb.w[((mu * kMaxHalf + nu) * kMaxHalf + om) * 3 + m];
     }
 }
 
@@ -220,57 +346,58 @@ __device__ __forceinline__ void accum(const float (&m)[G::H + 1], const float (&
 
 // One complex line (weights of group (mu, nu)) for the thread's R outputs.
 template <class G>
-__device__ __forceinline__ void y_single(const float2 *sG2, int row, int j, int mu, int nu, const SpecTables &tb,
+__device__ __forceinline__ void y_single(const float2 *sG2, int row, int j, int mu, int nu, const float *sW,
                                          const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     f2x Z[G::NZ];
     load_line<G>(sG2, row, nu, j, Z);
     float w[G::H + 1][3];
-    load_w<G>(tb, mu, nu, w);
+    load_w<G>(sW, mu, nu, w);
+    float m[G::R][G::H + 1];
+    line_mags_strip<G::L, G::R>(Z, tw, m);
 #pragma unroll
-    for (int r = 0; r < G::R; ++r) {
-        float m[G::H + 1];
-        line_mags<G::L>(Z, r + G::H, tw, m);
-        accum<G>(m, w, 0, et[r], ex[r], ey[r]);
-    }
+    for (int r = 0; r < G::R; ++r) accum<G>(m[r], w, 0, et[r], ex[r], ey[r]);
 }
 
 // The +nu and -nu lines of one mu > 0, which share their weights.
 template <class G>
-__device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu, int nu, const SpecTables &tb,
+__device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu, int nu, const float *sW,
                                        const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
-    f2x Zp[G::NZ], Zm[G::NZ];
-    load_line<G>(sG2, row, nu, j, Zp);
-    load_line<G>(sG2, row, -nu, j, Zm);
     float w[G::H + 1][3];
-    load_w<G>(tb, mu, nu, w);
+    load_w<G>(sW, mu, nu, w);
+    float mp[G::R][G::H + 1], mm[G::R][G::H + 1];
+    {
+        f2x Z[G::NZ];
+        load_line<G>(sG2, row, nu, j, Z);
+        line_mags_strip<G::L, G::R>(Z, tw, mp);
+    }
+    {
+        f2x Z[G::NZ];
+        load_line<G>(sG2, row, -nu, j, Z);
+        line_mags_strip<G::L, G::R>(Z, tw, mm);
+    }
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
-        float mp[G::H + 1], mm[G::H + 1];
-        line_mags<G::L>(Zp, r + G::H, tw, mp);
-        line_mags<G::L>(Zm, r + G::H, tw, mm);
 #pragma unroll
-        for (int om = 0; om <= G::H; ++om) mp[om] += mm[om];
-        accum<G>(mp, w, 0, et[r], ex[r], ey[r]);
+        for (int om = 0; om <= G::H; ++om) mp[r][om] += mm[r][om];
+        accum<G>(mp[r], w, 0, et[r], ex[r], ey[r]);
     }
 }
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
 template <class G>
-__device__ __forceinline__ void y_real(const float2 *sG2, int row, int j, const SpecTables &tb, const Tw<G::L> &tw,
+__device__ __forceinline__ void y_real(const float2 *sG2, int row, int j, const float *sW, const Tw<G::L> &tw,
                                        float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     f2x Z[G::NZ];
     load_line<G>(sG2, row, 0, j, Z);
     float w[G::H + 1][3];
-    load_w<G>(tb, 0, 0, w);
+    load_w<G>(sW, 0, 0, w);
+    float m[G::R][G::H + 1];
+    line_mags_strip_real<G::L, G::R>(Z, tw, m);
 #pragma unroll
-    for (int r = 0; r < G::R; ++r) {
-        float m[G::H + 1];
-        line_mags_real<G::L>(Z, r + G::H, tw, m);
-        accum<G>(m, w, 1, et[r], ex[r], ey[r]);
-    }
+    for (int r = 0; r < G::R; ++r) accum<G>(m[r], w, 1, et[r], ex[r], ey[r]);
 }
 
 // x stage for one mu: G1[mu](x-h..x+h, y') -> G2[mu, nu](x, y') for the BT x BX x PY items.
@@ -421,7 +548,9 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
     float *sG1 = smem;
     float2 *sG2 = reinterpret_cast<float2 *>(smem + G::NG1);
     float *sV = smem + G::NG1;   // aliases sG2: dead once stage t is done
+    float *sW = smem + G::NG1 + G::NALIAS;
 
+    fill_w<G>(sW, tb);
     const int ty = (int)(tile % tiles_y);
     const int tx = (int)((tile / tiles_y) % tiles_x);
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
@@ -444,13 +573,13 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
         x_stage<G>(sG1, sG2, mu, tw);
         __syncthreads();
         if (mu == 0) {
-            y_real<G>(sG2, row, j, tb, tw, et, ex, ey);
+            y_real<G>(sG2, row, j, sW, tw, et, ex, ey);
 #pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_single<G>(sG2, row, j, 0, nu, tb, tw, et, ex, ey);
+            for (int nu = 1; nu <= H; ++nu) y_single<G>(sG2, row, j, 0, nu, sW, tw, et, ex, ey);
         } else {
-            y_single<G>(sG2, row, j, mu, 0, tb, tw, et, ex, ey);
+            y_single<G>(sG2, row, j, mu, 0, sW, tw, et, ex, ey);
 #pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_pair<G>(sG2, row, j, mu, nu, tb, tw, et, ex, ey);
+            for (int nu = 1; nu <= H; ++nu) y_pair<G>(sG2, row, j, mu, nu, sW, tw, et, ex, ey);
         }
         __syncthreads();
     }

@@ -58,7 +58,8 @@ struct TGeo {
     static constexpr int REF_BYTES = NPAIR * 128 * 8;
     static constexpr int XCH_BYTES = 64 * 3 * P * 4;
     static constexpr int OFF_A = NG1 * 4, OFF_B = OFF_A + AV_BYTES, OFF_REF = OFF_B + B_BYTES;
-    static constexpr int OFF_X = OFF_REF + REF_BYTES, OFF_BAR = OFF_X + XCH_BYTES;
+    static constexpr int NW = ((H + 1) * (H + 1) * (H + 1) * 3 + 3) / 4 * 4;
+    static constexpr int OFF_X = OFF_REF + REF_BYTES, OFF_W = OFF_X + XCH_BYTES, OFF_BAR = OFF_W + NW * 4;
     static constexpr size_t SMEM = OFF_BAR + 16;
     static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
     static_assert(N <= 256 && N % 16 == 0, "N of one product");
@@ -314,6 +315,8 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
     float *sV = reinterpret_cast<float *>(smem + G::OFF_A);   // aliases the operands until stage t is done
     float2 *ref = reinterpret_cast<float2 *>(smem + G::OFF_REF);
     float *xch = reinterpret_cast<float *>(smem + G::OFF_X);
+    float *sW = reinterpret_cast<float *>(smem + G::OFF_W);
+    fill_w<G>(sW, tb);
     const uint32_t bar = smem_u32(smem + G::OFF_BAR);
     const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(smem + G::OFF_B);
 
@@ -366,7 +369,7 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
             const int nu = nu_of_line(li, mu);
             const int anu = nu < 0 ? -nu : nu;
             float w[H + 1][3];
-            load_w<G>(tb, mu, valid ? anu : 0, w);
+            load_w<G>(sW, mu, valid ? anu : 0, w);
             const bool dc_line = mu == 0 && nu == 0;   // count omega > 0 only (its mirror is the factor 2)
             const float2 c = ref[pr * 128 + lane_row];
 #pragma unroll

@@ -232,7 +232,8 @@ sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p,
         float *Sm = (float *)(base + b.Sm[i]);
         double *part = (double *)(base + b.part[i]);
         dv[i] = sal::DVolDesc{ev[i].E, Sm, part, vols[i].T, vols[i].X, vols[i].Y};
-        bv[i] = sal::BatchVolDesc{Sm, vols[i].S, part, sal::dcs_num_tiles(sal_dims{vols[i].T, vols[i].X, vols[i].Y}),
+        bv[i] = sal::BatchVolDesc{Sm, vols[i].S, part,
+                                  sal::dcs_num_records(sal_dims{vols[i].T, vols[i].X, vols[i].Y}, p->stencil),
                                   vols[i].T * vols[i].X * vols[i].Y};
     }
     cudaError_t e;

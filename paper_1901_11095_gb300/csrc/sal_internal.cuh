@@ -115,8 +115,10 @@ struct DVolDesc {
 };
 cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s);
 
-// Directional compare: number of per-CTA partial records written to the workspace.
+// Directional compare: capacity of partial records in the workspace (per map, any stencil,
+// plus the first reduction pass), and the records one map of a launch writes.
 int64_t dcs_num_partials(sal_dims d);
+int64_t dcs_num_records(sal_dims d, int stencil);
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials,
                        double *stats, cudaStream_t s);
 // Fixed-scratch variant of the directional compare (no allocation by caller or library).

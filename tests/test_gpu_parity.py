@@ -122,11 +122,14 @@ def test_local_spectra_and_project_match_oracle(L, bnd):
         assert nerr(E[m], E_ref[m]) < TOL_MAP
 
 
-@pytest.mark.parametrize("stc,L,bnd,sigma", [("26", 7, "reflect", 1.0), ("line", 7, "periodic", 1.3),
-                                              ("line", 15, "reflect", 2.0), ("26", 5, "periodic", 0.6)])
-def test_directional_compare_matches_oracle(stc, L, bnd, sigma):
+@pytest.mark.parametrize("stc,L,bnd,sigma,shape", [
+    ("26", 7, "reflect", 1.0, (21, 19, 67)), ("line", 7, "periodic", 1.3, (21, 19, 67)),
+    ("line", 15, "reflect", 2.0, (21, 19, 67)), ("26", 5, "periodic", 0.6, (21, 19, 67)),
+    # several chunks of planes along t, the last one ragged; ragged x and y blocks
+    ("26", 7, "reflect", 1.0, (150, 11, 70)), ("26", 5, "periodic", 0.8, (129, 9, 131)),
+])
+def test_directional_compare_matches_oracle(stc, L, bnd, sigma, shape):
     rng = np.random.default_rng(5)
-    shape = (21, 19, 67)
     E = rng.uniform(0.0, 1.0, size=(3,) + shape).astype(np.float32)
     p = api.params(L=L, boundary=bnd, stencil=stc, sigma=sigma)
     Sm, st = api.sal_directional_compare(to_dev(E), p)
