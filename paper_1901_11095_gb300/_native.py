@@ -41,7 +41,7 @@ class SalVolume(ctypes.Structure):
 class SalTileChoice(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("size_class", ctypes.c_int32),
                 ("shape", ctypes.c_int32), ("bt", ctypes.c_int32), ("bx", ctypes.c_int32), ("by", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("mode", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class SalError(RuntimeError):

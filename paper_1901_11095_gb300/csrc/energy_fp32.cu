@@ -14,18 +14,19 @@ cudaError_t launch_energy_fp32_l15(const EVolDesc *vols, int n, int bnd, int sha
 namespace {
 struct ShapeList {
     int L;
-    TileShape s[3];
+    TileShape s[kMaxShapes];
 };
-// Candidate tile shapes (BT x BX x BY output voxels per CTA) per cube side; index 0 is the
-// default when the autotuner has not chosen.
+// Candidate tile shapes (BT x BX x BY output voxels per CTA, staging mode) per cube side;
+// index 0 is the default when the autotuner has not chosen.  The order must match the
+// switch of each energy_fp32_l*.cu.
 const ShapeList kShapes[] = {
-    {3, {{2, 8, 32}, {4, 8, 32}, {1, 16, 32}}},
-    {5, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
-    {7, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
-    {9, {{2, 8, 32}, {1, 16, 32}, {1, 8, 32}}},
-    {11, {{1, 8, 32}, {1, 16, 32}}},
-    {13, {{1, 8, 32}, {1, 16, 32}}},
-    {15, {{1, 8, 32}, {1, 16, 32}}},
+    {3, {{2, 8, 32, 0}, {4, 8, 32, 0}, {1, 16, 32, 0}}},
+    {5, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
+    {7, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}, {2, 8, 32, 1}, {2, 8, 32, 2}, {1, 16, 32, 2}}},
+    {9, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
+    {11, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
+    {13, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
+    {15, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
 };
 const ShapeList *shapes_of(int L)
 {
@@ -40,14 +41,14 @@ int energy_num_shapes(int L)
     const ShapeList *s = shapes_of(L);
     if (!s) return 0;
     int n = 0;
-    while (n < 3 && s->s[n].bt > 0) ++n;
+    while (n < kMaxShapes && s->s[n].bt > 0) ++n;
     return n;
 }
 
 TileShape energy_shape(int L, int idx)
 {
     const ShapeList *s = shapes_of(L);
-    if (!s || idx < 0 || idx >= energy_num_shapes(L)) return TileShape{0, 0, 0};
+    if (!s || idx < 0 || idx >= energy_num_shapes(L)) return TileShape{0, 0, 0, 0};
     return s->s[idx];
 }
 

@@ -28,9 +28,16 @@
 namespace sal {
 namespace energy_detail {
 
-template <int L_, int BT_, int BX_>
+// Tile geometry.  MODE selects how the intermediate spectra are held in shared memory:
+//   0: G1 of every mu, and the whole G2 slice of one mu (every nu line);
+//   1: G1 of every mu, and G2 only for the lines +|nu|, -|nu| of one (mu, |nu|) batch;
+//   2: G1 of one mu at a time (stage t rerun per mu from the staged V halo) and the
+//      G2 batch of mode 1.
+// Modes 1 and 2 trade some recomputation in stages t and x for a smaller footprint, i.e.
+// more resident CTAs per SM to hide the latencies of the y stage.
+template <int L_, int BT_, int BX_, int MODE_ = 0>
 struct EGeo {
-    static constexpr int L = L_, H = (L_ - 1) / 2, BT = BT_, BX = BX_;
+    static constexpr int L = L_, H = (L_ - 1) / 2, BT = BT_, BX = BX_, MODE = MODE_;
     static constexpr int BY = 32, R = 4, SY = BY / R;
     static constexpr int ROWS = BT * BX;               // output rows (t, x) per tile
     static constexpr int NT = ROWS * SY;                // threads
@@ -40,12 +47,20 @@ struct EGeo {
     // output rows an odd multiple of 16 bytes (conflict-free 128-bit shared loads)
     static constexpr int PY2 = ((PY / 2) % 2 == 0) ? PY + 2 : PY;
     static constexpr int NV = (BT + 2 * H) * HX * PY;   // floats of the V halo tile
+    static constexpr int NVR = (NV + 3) / 4 * 4;
     static constexpr int NG1 = (BT * HX * L * PY + 3) / 4 * 4;
     static constexpr int NG2 = ROWS * L * PY2;          // float2 of one mu-slice of G2
     static constexpr int NALIAS = (NV * 4 > NG2 * 8) ? NV : NG2 * 2;
     static constexpr int NW = ((H + 1) * (H + 1) * (H + 1) * 3 + 3) / 4 * 4;   // projection weights
-    static constexpr size_t SMEM = sizeof(float) * (size_t)(NG1 + NALIAS + NW);
     static constexpr int NZ = R + 2 * H;                // window of one thread's R outputs
+    // batched modes: G2 lines [s][row][y'] (s = 0: +|nu|, 1: -|nu|), row stride = PY2 float2
+    static constexpr int NG2B = 2 * ROWS * PY2;         // float2
+    static constexpr int NG1M = BT * HX * 2 * PY;       // floats: [(t, x')][re, im][y'] of one mu
+    static constexpr size_t SMEM =
+        sizeof(float) * (size_t)(MODE == 0   ? NG1 + NALIAS + NW
+                                 : MODE == 1 ? NG1 + (NVR > 2 * NG2B ? NVR : 2 * NG2B) + NW
+                                             : NVR + NG1M + 2 * NG2B + NW);
+    static_assert(MODE >= 0 && MODE <= 2, "tile mode");
 };
 
 // ---- packed pairs of floats -------------------------------------------------------------
@@ -293,11 +308,12 @@ __device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const T
     }
 }
 
+// The NZ samples of one G2 line behind this thread's R outputs (128-bit shared loads).
 template <class G>
-__device__ __forceinline__ void load_line(const float2 *sG2, int row, int nu, int j, f2x (&Z)[G::NZ])
+__device__ __forceinline__ void load_line(const float2 *line, int j, f2x (&Z)[G::NZ])
 {
     static_assert(G::NZ % 2 == 0, "even window");
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(sG2 + ((row * G::L + nu + G::H) * G::PY2 + G::R * j));
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(line + G::R * j);
 #pragma unroll
     for (int k = 0; k < G::NZ / 2; ++k) {
         const ulonglong2 v = p[k];
@@ -346,11 +362,11 @@ __device__ __forceinline__ void accum(const float (&m)[G::H + 1], const float (&
 
 // One complex line (weights of group (mu, nu)) for the thread's R outputs.
 template <class G>
-__device__ __forceinline__ void y_single(const float2 *sG2, int row, int j, int mu, int nu, const float *sW,
+__device__ __forceinline__ void y_single(const float2 *line, int j, int mu, int nu, const float *sW,
                                          const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     f2x Z[G::NZ];
-    load_line<G>(sG2, row, nu, j, Z);
+    load_line<G>(line, j, Z);
     float w[G::H + 1][3];
     load_w<G>(sW, mu, nu, w);
     float m[G::R][G::H + 1];
@@ -361,7 +377,7 @@ __device__ __forceinline__ void y_single(const float2 *sG2, int row, int j, int 
 
 // The +nu and -nu lines of one mu > 0, which share their weights.
 template <class G>
-__device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu, int nu, const float *sW,
+__device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j, int mu, int nu, const float *sW,
                                        const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     float w[G::H + 1][3];
@@ -369,12 +385,12 @@ __device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu
     float mp[G::R][G::H + 1], mm[G::R][G::H + 1];
     {
         f2x Z[G::NZ];
-        load_line<G>(sG2, row, nu, j, Z);
+        load_line<G>(lp, j, Z);
         line_mags_strip<G::L, G::R>(Z, tw, mp);
     }
     {
         f2x Z[G::NZ];
-        load_line<G>(sG2, row, -nu, j, Z);
+        load_line<G>(lm, j, Z);
         line_mags_strip<G::L, G::R>(Z, tw, mm);
     }
 #pragma unroll
@@ -387,11 +403,11 @@ __device__ __forceinline__ void y_pair(const float2 *sG2, int row, int j, int mu
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
 template <class G>
-__device__ __forceinline__ void y_real(const float2 *sG2, int row, int j, const float *sW, const Tw<G::L> &tw,
+__device__ __forceinline__ void y_real(const float2 *line, int j, const float *sW, const Tw<G::L> &tw,
                                        float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     f2x Z[G::NZ];
-    load_line<G>(sG2, row, 0, j, Z);
+    load_line<G>(line, j, Z);
     float w[G::H + 1][3];
     load_w<G>(sW, 0, 0, w);
     float m[G::R][G::H + 1];
@@ -538,6 +554,34 @@ __device__ __forceinline__ void t_stage(const float *sV, float *sG1, const Tw<G:
     }
 }
 
+// Writes this thread's R outputs of E_t, E_x, E_y (scaled by the mean's factor).
+template <class G>
+__device__ __forceinline__ void store_outputs(float *__restrict__ E, int64_t T, int64_t X, int64_t Y, int64_t t0,
+                                              int64_t x0, int64_t y0, int row, int j, float sc,
+                                              const float (&et)[G::R], const float (&ex)[G::R],
+                                              const float (&ey)[G::R])
+{
+    const int t = row / G::BX, x = row - t * G::BX;
+    const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + G::R * j;
+    if (gt >= T || gx >= X) return;
+    const int64_t N = T * X * Y;
+    float *e0 = E + (gt * X + gx) * Y + gy;
+    if (gy + G::R <= Y && (reinterpret_cast<uintptr_t>(e0) & 15) == 0 && (Y & 3) == 0) {
+        *reinterpret_cast<float4 *>(e0) = make_float4(et[0] * sc, et[1] * sc, et[2] * sc, et[3] * sc);
+        *reinterpret_cast<float4 *>(e0 + N) = make_float4(ex[0] * sc, ex[1] * sc, ex[2] * sc, ex[3] * sc);
+        *reinterpret_cast<float4 *>(e0 + 2 * N) = make_float4(ey[0] * sc, ey[1] * sc, ey[2] * sc, ey[3] * sc);
+    } else {
+#pragma unroll
+        for (int r = 0; r < G::R; ++r) {
+            if (gy + r < Y) {
+                e0[r] = et[r] * sc;
+                e0[r + N] = ex[r] * sc;
+                e0[r + 2 * N] = ey[r] * sc;
+            }
+        }
+    }
+}
+
 // One output tile of one volume.  Every thread of the CTA calls it with the same tile.
 template <class G>
 __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
@@ -572,38 +616,226 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
     for (int mu = 0; mu <= H; ++mu) {
         x_stage<G>(sG1, sG2, mu, tw);
         __syncthreads();
+        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
         if (mu == 0) {
-            y_real<G>(sG2, row, j, sW, tw, et, ex, ey);
+            y_real<G>(l0, j, sW, tw, et, ex, ey);
 #pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_single<G>(sG2, row, j, 0, nu, sW, tw, et, ex, ey);
+            for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
         } else {
-            y_single<G>(sG2, row, j, mu, 0, sW, tw, et, ex, ey);
+            y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
 #pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_pair<G>(sG2, row, j, mu, nu, sW, tw, et, ex, ey);
+            for (int nu = 1; nu <= H; ++nu)
+                y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
         }
         __syncthreads();
     }
 
-    const int t = row / G::BX, x = row - t * G::BX;
-    const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + G::R * j;
-    if (gt >= T || gx >= X) return;   // the last barrier of the tile is behind every thread
-    const int64_t N = T * X * Y;
-    float *e0 = E + (gt * X + gx) * Y + gy;
-    const float sc = tb.escale;
-    if (gy + G::R <= Y && (reinterpret_cast<uintptr_t>(e0) & 15) == 0 && (Y & 3) == 0) {
-        *reinterpret_cast<float4 *>(e0) = make_float4(et[0] * sc, et[1] * sc, et[2] * sc, et[3] * sc);
-        *reinterpret_cast<float4 *>(e0 + N) = make_float4(ex[0] * sc, ex[1] * sc, ex[2] * sc, ex[3] * sc);
-        *reinterpret_cast<float4 *>(e0 + 2 * N) = make_float4(ey[0] * sc, ey[1] * sc, ey[2] * sc, ey[3] * sc);
-    } else {
+    store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
+}
+
+// ---- batched modes (1, 2) -------------------------------------------------------------
+// Twiddles of one runtime frequency index a: c[k] = cos(2 pi a k / L), s[k] = sin(...),
+// k = 1..H, read from the parameter bank (a register array cannot be indexed at run time).
+template <int L>
+struct TwRow {
+    static constexpr int H = (L - 1) / 2;
+    float c[H + 1], s[H + 1];
+    __device__ __forceinline__ void load(const SpecTables &tb, int a)
+    {
+        int idx = 0;
 #pragma unroll
-        for (int r = 0; r < G::R; ++r) {
-            if (gy + r < Y) {
-                e0[r] = et[r] * sc;
-                e0[r + N] = ex[r] * sc;
-                e0[r + 2 * N] = ey[r] * sc;
+        for (int k = 1; k <= H; ++k) {
+            idx += a;
+            if (idx >= L) idx -= L;
+            c[k] = tb.cs[idx];
+            s[k] = tb.sn[idx];
+        }
+    }
+};
+
+// Stage t for one mu: G1(mu) of every (t, x', y') column of the tile into
+// sG1m[((t * HX + x') * 2 + part) * PY + y'] (part 0 = Re, 1 = Im; mu = 0 writes Re only).
+template <class G>
+__device__ __forceinline__ void t_stage_mu(const float *sV, float *sG1m, int mu, const TwRow<G::L> &tr)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY;
+    for (int i = threadIdx.x; i < G::BT * G::HX * PY; i += G::NT) {
+        const int r = i / PY, yy = i - r * PY;
+        const int t = r / G::HX, xx = r - t * G::HX;
+        float a[L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) a[k] = sV[((t + k) * G::HX + xx) * PY + yy];
+        float *o = sG1m + (2 * r) * PY + yy;
+        if (mu == 0) {
+            float sum = a[H];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) sum += a[H + k] + a[H - k];
+            o[0] = sum;
+        } else {
+            const float a0 = a[H];
+            float A = 0.f, B = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                A = fmaf(fmaf(-2.f, a0, a[H + k] + a[H - k]), tr.c[k], A);
+                B = fmaf(a[H + k] - a[H - k], tr.s[k], B);
+            }
+            o[0] = A;       // G1(mu) = A - iB
+            o[PY] = -B;
+        }
+    }
+}
+
+// Stage x for the lines nu = +a and nu = -a of one mu: reads G1(mu) at x' = x - h .. x + h
+// (column pointer g1 + (t * HX + x') * xs + y', real part at +ore, imaginary at +oim) and
+// writes G2 line s (0: +a, 1: -a) of output row `row` at sG2b[(s * ROWS + row) * PY2 + y'].
+// mu = 0 (real input) writes only line +a.
+template <class G>
+__device__ __forceinline__ void x_stage_b(const float *g1, int xs, int ore, int oim, float2 *sG2b, int mu, int a,
+                                          const TwRow<G::L> &tr)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY, NITEM = G::ROWS * PY;
+    for (int i = threadIdx.x; i < NITEM; i += G::NT) {
+        const int row = i / PY, yy = i - row * PY;
+        const int t = row / G::BX, x = row - t * G::BX;
+        const float *g = g1 + (t * G::HX + x) * xs + yy;
+        float2 *o = sG2b + row * G::PY2 + yy;
+        if (mu == 0) {
+            float z[L];
+#pragma unroll
+            for (int k = 0; k < L; ++k) z[k] = g[k * xs + ore];
+            if (a == 0) {
+                float sum = z[H];
+#pragma unroll
+                for (int k = 1; k <= H; ++k) sum += z[H + k] + z[H - k];
+                o[0] = make_float2(sum, 0.f);
+            } else {
+                const float z0 = z[H];
+                float A = 0.f, B = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(fmaf(-2.f, z0, z[H + k] + z[H - k]), tr.c[k], A);
+                    B = fmaf(z[H + k] - z[H - k], tr.s[k], B);
+                }
+                o[0] = make_float2(A, -B);
+            }
+        } else {
+            f2x z[L];
+#pragma unroll
+            for (int k = 0; k < L; ++k) z[k] = pk(g[k * xs + ore], g[k * xs + oim]);
+            f2x *o2 = reinterpret_cast<f2x *>(o);
+            if (a == 0) {
+                f2x sum = z[H];
+#pragma unroll
+                for (int k = 1; k <= H; ++k) sum = add2(sum, add2(z[H + k], z[H - k]));
+                o2[0] = sum;
+            } else {
+                const f2x m2 = pk(-2.f, -2.f), z0 = z[H];
+                f2x A = pk(0.f, 0.f), B = pk(0.f, 0.f);
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fma2(fma2(z0, m2, add2(z[H + k], z[H - k])), pk(tr.c[k], tr.c[k]), A);
+                    B = fma2(sub2(z[H + k], z[H - k]), pk(tr.s[k], tr.s[k]), B);
+                }
+                const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+                o2[0] = pk(ax + by, ay - bx);                 // G2(+a) = A - iB
+                o2[G::ROWS * G::PY2] = pk(ax - by, ay + bx);  // G2(-a) = A + iB
             }
         }
     }
+}
+
+// One output tile in a batched mode: per mu (and, in mode 2, its own stage t), per |nu|
+// batch the x stage of the lines +-|nu| into the small G2 buffer, then their y stage.
+template <class G>
+__device__ __forceinline__ void energy_tile_b(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                              int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
+                                              const SpecTables &tb, float *smem)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY;
+    float *sV, *sG1;
+    float2 *sG2b;
+    float *sW;
+    if (G::MODE == 1) {
+        sG1 = smem;
+        sV = smem + G::NG1;   // aliases the G2 batch: dead once stage t is done
+        sG2b = reinterpret_cast<float2 *>(smem + G::NG1);
+        sW = smem + G::NG1 + (G::NVR > 2 * G::NG2B ? G::NVR : 2 * G::NG2B);
+    } else {
+        sV = smem;
+        sG1 = smem + G::NVR;
+        sG2b = reinterpret_cast<float2 *>(smem + G::NVR + G::NG1M);
+        sW = smem + G::NVR + G::NG1M + 2 * G::NG2B;
+    }
+
+    fill_w<G>(sW, tb);
+    const int ty = (int)(tile % tiles_y);
+    const int tx = (int)((tile / tiles_y) % tiles_x);
+    const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
+    const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
+
+    stage_v<G>(V, T, X, Y, bnd, t0, x0, y0, sV);
+    __syncthreads();
+    Tw<L> tw;
+    tw.load(tb);
+    if (G::MODE == 1) {
+        t_stage<G>(sV, sG1, tw);
+        __syncthreads();
+    }
+
+    const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;
+    float et[G::R], ex[G::R], ey[G::R];
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
+    const float2 *lp = sG2b + row * G::PY2, *lm = lp + G::ROWS * G::PY2;
+
+#pragma unroll 1
+    for (int mu = 0; mu <= H; ++mu) {
+        int xs, ore, oim;
+        if (G::MODE == 1) {
+            xs = L * PY;
+            ore = mu == 0 ? 0 : (2 * mu - 1) * PY;
+            oim = 2 * mu * PY;
+        } else {
+            TwRow<L> trm;
+            trm.load(tb, mu);
+            t_stage_mu<G>(sV, sG1, mu, trm);
+            __syncthreads();
+            xs = 2 * PY;
+            ore = 0;
+            oim = PY;
+        }
+#pragma unroll 1
+        for (int a = 0; a <= H; ++a) {
+            TwRow<L> tr;
+            tr.load(tb, a);
+            x_stage_b<G>(sG1, xs, ore, oim, sG2b, mu, a, tr);
+            __syncthreads();
+            if (mu == 0) {
+                if (a == 0)
+                    y_real<G>(lp, j, sW, tw, et, ex, ey);
+                else
+                    y_single<G>(lp, j, 0, a, sW, tw, et, ex, ey);
+            } else {
+                if (a == 0)
+                    y_single<G>(lp, j, mu, 0, sW, tw, et, ex, ey);
+                else
+                    y_pair<G>(lp, lm, j, mu, a, sW, tw, et, ex, ey);
+            }
+            __syncthreads();
+        }
+    }
+    store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
+}
+
+template <class G>
+__device__ __forceinline__ void energy_tile_any(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                                int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
+                                                const SpecTables &tb, float *smem)
+{
+    if constexpr (G::MODE == 0)
+        energy_tile<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
+    else
+        energy_tile_b<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
 }
 
 // Volumes of one launch: a single volume, or a batch of uneven volumes walked by a
@@ -633,7 +865,7 @@ __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const __grid_constan
             if (bt.v[mid].tile0 <= k) lo = mid; else hi = mid - 1;
         }
         const EVol &v = bt.v[lo];
-        energy_tile<G>(v.V, v.T, v.X, v.Y, bt.bnd, k - v.tile0, v.tiles_x, v.tiles_y, v.E, tb, smem);
+        energy_tile_any<G>(v.V, v.T, v.X, v.Y, bt.bnd, k - v.tile0, v.tiles_x, v.tiles_y, v.E, tb, smem);
         __syncthreads();
     }
 }

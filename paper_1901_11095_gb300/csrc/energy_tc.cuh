@@ -41,7 +41,7 @@ struct TGeo {
     static constexpr int L = L_, H = (L_ - 1) / 2, BT = BT_, BX = BX_;
     static constexpr int BY = 32, P = 8, SEG = BY / P, ROWS = BT * BX;
     static_assert(ROWS * SEG == 64, "64 (row, segment) pairs fill one half of an M = 128 product");
-    static constexpr int NT = 128;
+    static constexpr int NT = 256;                                  // two warpgroups share the epilogue
     static constexpr int HX = BX + 2 * H, PY = BY + 2 * H;
     static constexpr int NV = (BT + 2 * H) * HX * PY;
     static constexpr int NG1 = (BT * HX * L * PY + 31) / 32 * 32;   // floats (128-byte multiple)
@@ -56,12 +56,19 @@ struct TGeo {
     static constexpr int AV_BYTES = (AV_RAW + 127) / 128 * 128;
     static constexpr int B_BYTES = (N * KP * OP::ESZ + 127) / 128 * 128;
     static constexpr int REF_BYTES = NPAIR * 128 * 8;
-    static constexpr int XCH_BYTES = 64 * 3 * P * 4;
+    // three partial sets meet the fourth at the end of a tile, in the stage-t buffer (free by
+    // then) where it fits, else in a region of their own
+    static constexpr int XCH_BYTES = 3 * 64 * 3 * P * 4;
+    static constexpr bool XCH_IN_G1 = XCH_BYTES <= NG1 * 4;
     static constexpr int OFF_A = NG1 * 4, OFF_B = OFF_A + AV_BYTES, OFF_REF = OFF_B + B_BYTES;
     static constexpr int NW = ((H + 1) * (H + 1) * (H + 1) * 3 + 3) / 4 * 4;
-    static constexpr int OFF_X = OFF_REF + REF_BYTES, OFF_W = OFF_X + XCH_BYTES, OFF_BAR = OFF_W + NW * 4;
+    static constexpr int OFF_X = XCH_IN_G1 ? 0 : OFF_REF + REF_BYTES;
+    static constexpr int OFF_W = OFF_REF + REF_BYTES + (XCH_IN_G1 ? 0 : XCH_BYTES), OFF_BAR = OFF_W + NW * 4;
     static constexpr size_t SMEM = OFF_BAR + 16;
-    static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    static constexpr int PPR = (256 / N < NPAIR) ? (256 / N > 0 ? 256 / N : 1) : NPAIR;  // products per round
+    static constexpr int TCOLS_RAW = PPR * N;
+    static constexpr int TMEM_COLS = TCOLS_RAW <= 32 ? 32 : TCOLS_RAW <= 64 ? 64 : TCOLS_RAW <= 128 ? 128
+                                     : TCOLS_RAW <= 256 ? 256 : 512;
     static_assert(N <= 256 && N % 16 == 0, "N of one product");
     static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
@@ -263,7 +270,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
 }
 
 template <class G>
-__device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, uint32_t bar)
+__device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t a_addr, uint32_t b_addr)
 {
     constexpr uint32_t idesc = instr_desc(G::OP::FMT, 128, G::N);
 #pragma unroll
@@ -280,6 +287,11 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t a_addr, uint32
                          " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                          "l"(da), "l"(db), "r"(idesc), "r"(acc));
     }
+}
+
+// Arrives on the mbarrier once every product issued so far by this thread has completed.
+__device__ __forceinline__ void commit_mma(uint32_t bar)
+{
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
@@ -335,10 +347,12 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
     for (int i = threadIdx.x; i < G::A_BYTES / 16; i += G::NT) reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
 
-    // this thread's tensor-memory lane = operand row: line half, output row, segment
-    const int lane_row = threadIdx.x;
+    // warpgroup g takes every other product of a round; within it, warp quarter q reads
+    // tensor-memory lanes 32q..32q+31 = operand rows: line half, output row, segment
+    const int g = threadIdx.x >> 7, q = (threadIdx.x >> 5) & 3;
+    const int lane_row = threadIdx.x & 127;
     const int half = lane_row >> 6, rs = lane_row & 63;
-    const uint32_t taddr = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
     float et[P], ex[P], ey[P];
 #pragma unroll
     for (int o = 0; o < P; ++o) et[o] = ex[o] = ey[o] = 0.f;
@@ -349,49 +363,69 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
         build_a<G>(sG1, sA, ref, mu, tw);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        const int nl = nlines(mu, L);
+        const int nl = nlines(mu, L), np = (nl + 1) / 2;
 #pragma unroll 1
-        for (int pr = 0; pr < (nl + 1) / 2; ++pr) {
+        for (int p0 = 0; p0 < np; p0 += G::PPR) {
+            const int pend = p0 + G::PPR < np ? p0 + G::PPR : np;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (threadIdx.x == 0 && !ctl.stall) issue_mma<G>(tmem, a_addr + pr * G::PAIR_BYTES, b_addr, bar);
+            if (threadIdx.x == 0 && !ctl.stall) {
+                for (int pr = p0; pr < pend; ++pr)
+                    issue_mma<G>(tmem + (uint32_t)((pr - p0) * G::N), a_addr + pr * G::PAIR_BYTES, b_addr);
+                commit_mma(bar);
+            }
             const bool done = mbar_wait(bar, phase, ctl.limit_ns);
             if (__syncthreads_or(!done)) {
                 ok = false;
-                // a product that was issued may still be in flight: give it one more bounded
+                // products that were issued may still be in flight: give them one more bounded
                 // wait before the caller releases the tensor memory
                 if (!ctl.stall) mbar_wait(bar, phase, ctl.limit_ns);
                 break;
             }
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int li = 2 * pr + half;
-            const bool valid = li < nl;
-            const int nu = nu_of_line(li, mu);
-            const int anu = nu < 0 ? -nu : nu;
-            float w[H + 1][3];
-            load_w<G>(sW, mu, valid ? anu : 0, w);
-            const bool dc_line = mu == 0 && nu == 0;   // count omega > 0 only (its mirror is the factor 2)
-            const float2 c = ref[pr * 128 + lane_row];
+#pragma unroll 1
+            for (int pr = p0 + g; pr < pend; pr += 2) {
+                const int li = 2 * pr + half;
+                const bool valid = li < nl;                    // uniform per warp
+                const int nu = nu_of_line(li, mu);
+                const int anu = nu < 0 ? -nu : nu;
+                const bool dc_line = mu == 0 && nu == 0;       // count omega > 0 only (its mirror is the factor 2)
+                const float2 c = ref[pr * 128 + lane_row];
+                // |F| summed over the signs of omega per (output, |omega|), then the weights
+                float ms[P][H + 1];
 #pragma unroll
-            for (int q = 0; q < L; ++q) {
-                float v[16];
-                tmem_ld16(taddr + 16 * q, v);
-                if (!valid) continue;
+                for (int o = 0; o < P; ++o)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int idx = 8 * q + u, o = idx / L, om = idx % L;
-                    float re = v[2 * u], im = v[2 * u + 1];
-                    if (om == H) {
-                        if (dc_line) continue;
-                        re = fmaf((float)L, c.x, re);
-                        im = fmaf((float)L, c.y, im);
+                    for (int aw = 0; aw <= H; ++aw) ms[o][aw] = 0.f;
+                const uint32_t taddr = tq + (uint32_t)((pr - p0) * G::N);
+#pragma unroll
+                for (int ch = 0; ch < L; ++ch) {
+                    float v[16];
+                    tmem_ld16(taddr + 16 * ch, v);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = 8 * ch + u, o = idx / L, om = idx % L;
+                        float re = v[2 * u], im = v[2 * u + 1];
+                        if (om == H) {
+                            re = fmaf((float)L, c.x, re);
+                            im = fmaf((float)L, c.y, im);
+                        }
+                        const float mag = sqrt_approx(fmaf(re, re, im * im));
+                        const int aw = om >= H ? om - H : H - om;
+                        ms[o][aw] += (dc_line && om <= H) ? 0.f : mag;
                     }
-                    if (dc_line && om < H) continue;
-                    const float mag = sqrt_approx(fmaf(re, re, im * im));
-                    const int aw = om >= H ? om - H : H - om;
-                    et[o] = fmaf(w[aw][0], mag, et[o]);
-                    ex[o] = fmaf(w[aw][1], mag, ex[o]);
-                    ey[o] = fmaf(w[aw][2], mag, ey[o]);
+                }
+                if (valid) {
+                    float w[H + 1][3];
+                    load_w<G>(sW, mu, anu, w);
+#pragma unroll
+                    for (int o = 0; o < P; ++o)
+#pragma unroll
+                        for (int aw = 0; aw <= H; ++aw) {
+                            et[o] = fmaf(w[aw][0], ms[o][aw], et[o]);
+                            ex[o] = fmaf(w[aw][1], ms[o][aw], ex[o]);
+                            ey[o] = fmaf(w[aw][2], ms[o][aw], ey[o]);
+                        }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -400,17 +434,19 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
     }
     if (!ok) return false;
 
-    // the two line halves of each (row, segment) meet in shared memory
-    if (half == 1) {
+    // four partial sets per (row, segment): two line halves x two warpgroups
+    const int set = g * 2 + half;   // 0 writes the result
+    if (set != 0) {
+        float *xs = xch + (set - 1) * (3 * P * 64);
 #pragma unroll
         for (int o = 0; o < P; ++o) {
-            xch[(0 * P + o) * 64 + rs] = et[o];
-            xch[(1 * P + o) * 64 + rs] = ex[o];
-            xch[(2 * P + o) * 64 + rs] = ey[o];
+            xs[(0 * P + o) * 64 + rs] = et[o];
+            xs[(1 * P + o) * 64 + rs] = ex[o];
+            xs[(2 * P + o) * 64 + rs] = ey[o];
         }
     }
     __syncthreads();
-    if (half == 0) {
+    if (set == 0) {
         const int row = rs / G::SEG, s = rs - row * G::SEG;
         const int t = row / G::BX, x = row - t * G::BX;
         const int64_t gt = t0 + t, gx = x0 + x, gy = y0 + P * s;
@@ -421,9 +457,17 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
 #pragma unroll
             for (int o = 0; o < P; ++o) {
                 if (gy + o >= Y) break;
-                e0[o] = (et[o] + xch[(0 * P + o) * 64 + rs]) * sc;
-                e0[o + N] = (ex[o] + xch[(1 * P + o) * 64 + rs]) * sc;
-                e0[o + 2 * N] = (ey[o] + xch[(2 * P + o) * 64 + rs]) * sc;
+                float a0 = et[o], a1 = ex[o], a2 = ey[o];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float *xs = xch + k * (3 * P * 64);
+                    a0 += xs[(0 * P + o) * 64 + rs];
+                    a1 += xs[(1 * P + o) * 64 + rs];
+                    a2 += xs[(2 * P + o) * 64 + rs];
+                }
+                e0[o] = a0 * sc;
+                e0[o + N] = a1 * sc;
+                e0[o + 2 * N] = a2 * sc;
             }
         }
     }
@@ -432,7 +476,7 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
 }
 
 template <class G>
-__global__ void __launch_bounds__(G::NT, 1) energy_tc_kernel(const __grid_constant__ EBatch bt,
+__global__ void __launch_bounds__(G::NT, 2) energy_tc_kernel(const __grid_constant__ EBatch bt,
                                                           const __grid_constant__ SpecTables tb, TcCtl ctl)
 {
     extern __shared__ __align__(128) float tc_smem_f[];

@@ -255,7 +255,7 @@ sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p,
 sal_tile_choice choice_of(int L, int precision, int cls, int shape, float ms)
 {
     const sal::TileShape t = sal::energy_shape(L, shape);
-    return sal_tile_choice{L, precision, cls, shape, t.bt, t.bx, t.by, ms};
+    return sal_tile_choice{L, precision, cls, shape, t.bt, t.bx, t.by, t.mode, ms};
 }
 
 }  // namespace

@@ -60,8 +60,9 @@ struct EVolDesc {
 
 // Tile shapes of the spectral-energy kernel that the autotuner chooses among.
 struct TileShape {
-    int bt, bx, by;
+    int bt, bx, by, mode;   // mode: how the spectra of a tile are held in shared memory (0, 1, 2)
 };
+constexpr int kMaxShapes = 6;
 int energy_num_shapes(int L);
 TileShape energy_shape(int L, int idx);
 
