@@ -463,20 +463,38 @@ __global__ void __launch_bounds__(256) combine_kernel(const float *__restrict__ 
         lo[m] = (float)l;
         al[m] = (float)(wts[m] * scale);
     }
-    const int64_t n4 = ((N & 3) == 0) ? N / 4 : 0;
+    // vector width: 4 when every plane starts on a 16-byte boundary (N % 4 == 0), else 2
+    // when N is even (planes 8-byte aligned), else scalar; the tail is scalar
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
-        const float4 s0 = __ldg(reinterpret_cast<const float4 *>(Sm) + i);
-        const float4 s1 = __ldg(reinterpret_cast<const float4 *>(Sm + N) + i);
-        const float4 s2 = __ldg(reinterpret_cast<const float4 *>(Sm + 2 * N) + i);
-        float4 o;
-        o.x = fmaf(al[2], s2.x - lo[2], fmaf(al[1], s1.x - lo[1], al[0] * (s0.x - lo[0])));
-        o.y = fmaf(al[2], s2.y - lo[2], fmaf(al[1], s1.y - lo[1], al[0] * (s0.y - lo[0])));
-        o.z = fmaf(al[2], s2.z - lo[2], fmaf(al[1], s1.z - lo[1], al[0] * (s0.z - lo[0])));
-        o.w = fmaf(al[2], s2.w - lo[2], fmaf(al[1], s1.w - lo[1], al[0] * (s0.w - lo[0])));
-        reinterpret_cast<float4 *>(S)[i] = o;
+    int64_t done = 0;
+    if ((N & 3) == 0) {
+        const int64_t n4 = N / 4;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 s0 = __ldg(reinterpret_cast<const float4 *>(Sm) + i);
+            const float4 s1 = __ldg(reinterpret_cast<const float4 *>(Sm + N) + i);
+            const float4 s2 = __ldg(reinterpret_cast<const float4 *>(Sm + 2 * N) + i);
+            float4 o;
+            o.x = fmaf(al[2], s2.x - lo[2], fmaf(al[1], s1.x - lo[1], al[0] * (s0.x - lo[0])));
+            o.y = fmaf(al[2], s2.y - lo[2], fmaf(al[1], s1.y - lo[1], al[0] * (s0.y - lo[0])));
+            o.z = fmaf(al[2], s2.z - lo[2], fmaf(al[1], s1.z - lo[1], al[0] * (s0.z - lo[0])));
+            o.w = fmaf(al[2], s2.w - lo[2], fmaf(al[1], s1.w - lo[1], al[0] * (s0.w - lo[0])));
+            reinterpret_cast<float4 *>(S)[i] = o;
+        }
+        done = 4 * n4;
+    } else if ((N & 1) == 0) {
+        const int64_t n2 = N / 2;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+            const float2 s0 = __ldg(reinterpret_cast<const float2 *>(Sm) + i);
+            const float2 s1 = __ldg(reinterpret_cast<const float2 *>(Sm + N) + i);
+            const float2 s2 = __ldg(reinterpret_cast<const float2 *>(Sm + 2 * N) + i);
+            float2 o;
+            o.x = fmaf(al[2], s2.x - lo[2], fmaf(al[1], s1.x - lo[1], al[0] * (s0.x - lo[0])));
+            o.y = fmaf(al[2], s2.y - lo[2], fmaf(al[1], s1.y - lo[1], al[0] * (s0.y - lo[0])));
+            reinterpret_cast<float2 *>(S)[i] = o;
+        }
+        done = 2 * n2;
     }
-    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride)
+    for (int64_t i = done + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride)
         S[i] = fmaf(al[2], Sm[2 * N + i] - lo[2], fmaf(al[1], Sm[N + i] - lo[1], al[0] * (Sm[i] - lo[0])));
 }
 
@@ -599,7 +617,7 @@ cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, con
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (N / 4 + 255) / 256;
+    int64_t blocks = (N / 2 + 255) / 256;
     const int64_t cap = (int64_t)nsm * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;

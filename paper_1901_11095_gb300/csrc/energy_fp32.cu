@@ -22,7 +22,7 @@ struct ShapeList {
 const ShapeList kShapes[] = {
     {3, {{2, 8, 32, 0}, {4, 8, 32, 0}, {1, 16, 32, 0}}},
     {5, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
-    {7, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}, {2, 8, 32, 1}, {2, 8, 32, 2}, {1, 16, 32, 2}}},
+    {7, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}, {2, 8, 32, 3}, {2, 8, 32, 2}, {1, 16, 32, 3}}},
     {9, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
     {11, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
     {13, {{1, 8, 32, 0}, {1, 16, 32, 0}}},

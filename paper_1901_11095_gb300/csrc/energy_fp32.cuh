@@ -33,6 +33,8 @@ namespace energy_detail {
 //   1: G1 of every mu, and G2 only for the lines +|nu|, -|nu| of one (mu, |nu|) batch;
 //   2: G1 of one mu at a time (stage t rerun per mu from the staged V halo) and the
 //      G2 batch of mode 1.
+//   3: as 0, in two regions that swap roles every tile, so that the V halo of the next tile
+//      is copied asynchronously (cp.async) while the current tile finishes.
 // Modes 1 and 2 trade some recomputation in stages t and x for a smaller footprint, i.e.
 // more resident CTAs per SM to hide the latencies of the y stage.
 template <int L_, int BT_, int BX_, int MODE_ = 0>
@@ -56,11 +58,15 @@ struct EGeo {
     // batched modes: G2 lines [s][row][y'] (s = 0: +|nu|, 1: -|nu|), row stride = PY2 float2
     static constexpr int NG2B = 2 * ROWS * PY2;         // float2
     static constexpr int NG1M = BT * HX * 2 * PY;       // floats: [(t, x')][re, im][y'] of one mu
+    // mode 3: each region holds G1, a G2 slice or a V halo tile
+    static constexpr int NREG_RAW = NG1 > 2 * NG2 ? (NG1 > NVR ? NG1 : NVR) : (2 * NG2 > NVR ? 2 * NG2 : NVR);
+    static constexpr int NREG = (NREG_RAW + 3) / 4 * 4;
     static constexpr size_t SMEM =
         sizeof(float) * (size_t)(MODE == 0   ? NG1 + NALIAS + NW
                                  : MODE == 1 ? NG1 + (NVR > 2 * NG2B ? NVR : 2 * NG2B) + NW
-                                             : NVR + NG1M + 2 * NG2B + NW);
-    static_assert(MODE >= 0 && MODE <= 2, "tile mode");
+                                 : MODE == 2 ? NVR + NG1M + 2 * NG2B + NW
+                                             : 2 * NREG + NW);
+    static_assert(MODE >= 0 && MODE <= 3, "tile mode");
 };
 
 // ---- packed pairs of floats -------------------------------------------------------------
@@ -838,6 +844,89 @@ __device__ __forceinline__ void energy_tile_any(const float *__restrict__ V, int
         energy_tile_b<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
 }
 
+// ---- mode 3: the next tile's V halo in flight while the current tile finishes -----------
+__device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Issues the asynchronous copies of one tile's V halo into sV (same layout as stage_v) and
+// commits them as one group.
+template <class G>
+__device__ __forceinline__ void stage_v_async(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                              int64_t t0, int64_t x0, int64_t y0, float *sV)
+{
+    constexpr int H = G::H, PY = G::PY;
+    const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
+                        y0 + G::BY + H <= Y;
+    if (inside) {
+        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            const int r = i / PY, yy = i - r * PY;
+            const int a = r / G::HX, xx = r - a * G::HX;
+            cp_async_f32(sV + i, src + ((int64_t)a * X + xx) * Y + yy);
+        }
+    } else {
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            const int r = i / PY, yy = i - r * PY;
+            const int a = r / G::HX, xx = r - a * G::HX;
+            const int64_t gt = ext_index(t0 - H + a, T, bnd);
+            const int64_t gx = ext_index(x0 - H + xx, X, bnd);
+            const int64_t gy = ext_index(y0 - H + yy, Y, bnd);
+            cp_async_f32(sV + i, V + (gt * X + gx) * Y + gy);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One tile of a volume: origin and the volume it belongs to.
+struct TileRef {
+    const float *V;
+    float *E;
+    int64_t T, X, Y, t0, x0, y0;
+};
+
+// One mode-3 tile.  Its V halo is in sV (copies complete and visible); sO is the other
+// region.  When `nx` is given, the next tile's V halo is copied into sO once G1 is dead.
+template <class G>
+__device__ __forceinline__ void energy_tile_pf(const TileRef &c, const TileRef *nx, int bnd, const SpecTables &tb,
+                                               float *sV, float *sO, const float *sW)
+{
+    constexpr int L = G::L, H = G::H;
+    float *sG1 = sO;
+    float2 *sG2 = reinterpret_cast<float2 *>(sV);   // V is dead once stage t is done
+    Tw<L> tw;
+    tw.load(tb);
+    t_stage<G>(sV, sG1, tw);
+    __syncthreads();
+
+    const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;
+    float et[G::R], ex[G::R], ey[G::R];
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
+
+#pragma unroll 1
+    for (int mu = 0; mu <= H; ++mu) {
+        x_stage<G>(sG1, sG2, mu, tw);
+        __syncthreads();
+        if (mu == H && nx) stage_v_async<G>(nx->V, nx->T, nx->X, nx->Y, bnd, nx->t0, nx->x0, nx->y0, sO);
+        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
+        if (mu == 0) {
+            y_real<G>(l0, j, sW, tw, et, ex, ey);
+#pragma unroll 1
+            for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
+        } else {
+            y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
+#pragma unroll 1
+            for (int nu = 1; nu <= H; ++nu)
+                y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
+        }
+        __syncthreads();
+    }
+    store_outputs<G>(c.E, c.T, c.X, c.Y, c.t0, c.x0, c.y0, row, j, tb.escale, et, ex, ey);
+}
+
 // Volumes of one launch: a single volume, or a batch of uneven volumes walked by a
 // persistent grid (tile k of the launch belongs to the volume whose tile0 range holds it).
 struct EVol {
@@ -854,19 +943,58 @@ struct EBatch {
 };
 
 template <class G>
+__device__ __forceinline__ TileRef locate_tile(const EBatch &bt, int64_t k)
+{
+    int lo = 0, hi = bt.n - 1;      // last volume whose first tile is <= k
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bt.v[mid].tile0 <= k) lo = mid; else hi = mid - 1;
+    }
+    const EVol &v = bt.v[lo];
+    const int64_t tile = k - v.tile0;
+    const int ty = (int)(tile % v.tiles_y);
+    const int tx = (int)((tile / v.tiles_y) % v.tiles_x);
+    const int64_t tt = tile / ((int64_t)v.tiles_y * v.tiles_x);
+    return TileRef{v.V, v.E, v.T, v.X, v.Y, tt * G::BT, (int64_t)tx * G::BX, (int64_t)ty * G::BY};
+}
+
+template <class G>
 __global__ void __launch_bounds__(G::NT) energy_fp32_kernel(const __grid_constant__ EBatch bt,
                                                             const __grid_constant__ SpecTables tb)
 {
     extern __shared__ __align__(16) float smem[];
-    for (int64_t k = blockIdx.x; k < bt.total; k += gridDim.x) {
-        int lo = 0, hi = bt.n - 1;      // last volume whose first tile is <= k
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bt.v[mid].tile0 <= k) lo = mid; else hi = mid - 1;
+    if constexpr (G::MODE == 3) {
+        // persistent walk with the next tile's halo prefetched; regions swap every tile
+        float *R0 = smem, *R1 = smem + G::NREG, *sW = smem + 2 * G::NREG;
+        fill_w<G>(sW, tb);
+        int64_t k = blockIdx.x;
+        if (k >= bt.total) return;
+        TileRef cur = locate_tile<G>(bt, k);
+        stage_v_async<G>(cur.V, cur.T, cur.X, cur.Y, bt.bnd, cur.t0, cur.x0, cur.y0, R0);
+        int p = 0;
+        for (; k < bt.total; k += gridDim.x) {
+            const int64_t kn = k + gridDim.x;
+            TileRef nxt = cur;
+            if (kn < bt.total) nxt = locate_tile<G>(bt, kn);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            energy_tile_pf<G>(cur, kn < bt.total ? &nxt : nullptr, bt.bnd, tb, p ? R1 : R0, p ? R0 : R1, sW);
+            __syncthreads();
+            cur = nxt;
+            p ^= 1;
         }
-        const EVol &v = bt.v[lo];
-        energy_tile_any<G>(v.V, v.T, v.X, v.Y, bt.bnd, k - v.tile0, v.tiles_x, v.tiles_y, v.E, tb, smem);
-        __syncthreads();
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+        for (int64_t k = blockIdx.x; k < bt.total; k += gridDim.x) {
+            int lo = 0, hi = bt.n - 1;      // last volume whose first tile is <= k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bt.v[mid].tile0 <= k) lo = mid; else hi = mid - 1;
+            }
+            const EVol &v = bt.v[lo];
+            energy_tile_any<G>(v.V, v.T, v.X, v.Y, bt.bnd, k - v.tile0, v.tiles_x, v.tiles_y, v.E, tb, smem);
+            __syncthreads();
+        }
     }
 }
 
@@ -925,12 +1053,26 @@ cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persis
     cudaError_t e = set_smem(kern, G::SMEM);
     if (e != cudaSuccess) return e;
     int64_t grid = total;
-    if (persistent) {
+    if (persistent || G::MODE == 3) {
         int dev = 0, nsm = 0, per_sm = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, G::SMEM);
         if (e != cudaSuccess) return e;
+        // the occupancy query can answer for a smaller carveout than the launch gets: take
+        // the larger of it and the per-SM shared-memory and register limits
+        int smem_sm = 0, regs_sm = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0) {
+            const int by_smem = smem_sm / (int)(G::SMEM + 1024);
+            const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * G::NT);
+            const int by_threads = 2048 / G::NT;
+            int lim = by_smem < by_regs ? by_smem : by_regs;
+            lim = lim < by_threads ? lim : by_threads;
+            if (lim > per_sm) per_sm = lim;
+        }
         const int64_t resident = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
         if (grid > resident) grid = resident;
     }

@@ -10,9 +10,9 @@ cudaError_t launch_energy_fp32_l7(const EVolDesc *vols, int n, int bnd, int shap
         case 0: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 2, 8>>(vols, n, bnd, persistent, s);
         case 1: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 1, 16>>(vols, n, bnd, persistent, s);
         case 2: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 1, 8>>(vols, n, bnd, persistent, s);
-        case 3: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 2, 8, 1>>(vols, n, bnd, persistent, s);
+        case 3: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 2, 8, 3>>(vols, n, bnd, persistent, s);
         case 4: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 2, 8, 2>>(vols, n, bnd, persistent, s);
-        case 5: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 1, 16, 2>>(vols, n, bnd, persistent, s);
+        case 5: return energy_detail::launch_energy_impl<energy_detail::EGeo<7, 1, 16, 3>>(vols, n, bnd, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }
