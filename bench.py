@@ -40,6 +40,15 @@ WORKLOADS = {
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
+# DRAM bytes (read + write) of one spectral-energy launch, from one ncu capture of the same
+# kernel build (dram__bytes_read.sum + dram__bytes_write.sum on the 462 x 951 x 160 slab,
+# scaled to the full volume by the voxel count), keyed by (workload, L, precision).  Only
+# the default tile shape; any other configuration reports null.
+ENERGY_TRAFFIC = {
+    ("f3", 7, "fp32"): (4.365e9, "profiles/energy_fp32_L7_slab_462x951x160.md: "
+                                 "(282.9 MB + 789.9 MB) on the slab x 4.0687"),
+}
+
 
 def algorithmic_flops_per_voxel(L: int, R: int = 4) -> float:
     """FP32 flops per voxel of the fused energy stage as the kernel's algorithm defines it (FMA = 2).
@@ -529,6 +538,7 @@ def run_ours(args, rank: int, world: int) -> None:
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
     k4_gbs = 16 * N / (statistics.mean(k4) / 1e3) / 1e9
+    traffic = ENERGY_TRAFFIC.get((args.workload, args.L, args.precision))
     out = {
         "metric": "saliency voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -536,7 +546,8 @@ def run_ours(args, rank: int, world: int) -> None:
         "config": workload_config(args),
         "roofline": {"bound": "alu", "kernel": "spectral energy (fused local DFT, projections, mean)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                     "traffic": None,
+                     "traffic": traffic[0] if traffic else None,
+                     "traffic_source": traffic[1] if traffic else None,
                      "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
                                     f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
                      "flops_per_voxel": algorithmic_flops_per_voxel(args.L)},
