@@ -149,6 +149,34 @@ SAL_API sal_status sal_saliency(const float *V, sal_dims dims, const sal_params 
                         double *stats, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * The whole method of Fig. 1 on a volume in HOST memory: copies V_host to the device,
+ * computes S as sal_saliency does, and copies S back to S_host.  Successive calls on the
+ * same workspace overlap: the copy of the next call's V, this call's kernels and the copy
+ * of the previous call's S run on separate streams (V and S are double-buffered inside the
+ * workspace), so a sequence of calls runs at the speed of the kernels when the copies are
+ * shorter.
+ *   V_host, S_host: host memory, T*X*Y floats each; page-locked memory (cudaHostAlloc,
+ *     cudaHostRegister) is needed for the overlap, pageable memory works but copies
+ *     synchronously.  V_host may be reused as soon as the stream has passed the copy
+ *     (the library does not read it later).
+ *   stats: device, SAL_STATS_LEN doubles, or NULL.
+ *   ws: device workspace of sal_host_workspace_size bytes, owned by the caller; one
+ *     sequence of calls per workspace at a time (the library keeps, per workspace pointer,
+ *     the parity of its double buffers and the events that order them).
+ *   done_event: a cudaEvent_t created by the caller, or NULL.  If NULL, `stream` waits for
+ *     the copy of S (S_host is ready once `stream` completes).  Otherwise the event is
+ *     recorded after the copy of S and `stream` does not wait for it, so the next call's
+ *     kernels can run during this copy; S_host is ready once the event completes.
+ * Not for use during stream capture.  Errors as sal_saliency; SAL_ERR_CUDA for a failed
+ * copy, stream or event call.
+ */
+SAL_API sal_status sal_host_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes);
+SAL_API sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_params *p, float *S_host,
+                                     double *stats, void *ws, size_t ws_bytes, void *stream, void *done_event);
+/* Waits for and destroys the streams and events kept for workspace ws (none: no-op). */
+SAL_API sal_status sal_host_release(void *ws);
+
+/*
  * Directional compare for callers that cannot allocate device memory.
  *
  * The same computation and kernels as sal_directional_compare, but without a workspace

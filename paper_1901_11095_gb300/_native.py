@@ -73,6 +73,9 @@ def lib():
             "sal_directional_compare_static": [vp, SalDims, pp, vp, vp, vp],
             "sal_combine": [vp, vp, SalDims, pp, vp, vp],
             "sal_saliency": [vp, SalDims, pp, vp, vp, vp, sz, vp],
+            "sal_host_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
+            "sal_saliency_host": [vp, SalDims, pp, vp, vp, vp, sz, vp, vp],
+            "sal_host_release": [vp],
             "sal_batch_workspace_size": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, ctypes.POINTER(sz)],
             "sal_saliency_batched": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, vp, vp, sz, vp],
             "sal_graph_create_batched": [ctypes.POINTER(SalVolume), ctypes.c_int32, pp, vp, vp, sz, vp,
@@ -118,7 +121,8 @@ def check(status: int) -> None:
 def exported_symbols() -> list[str]:
     return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
             "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_directional_compare_static",
-            "sal_combine", "sal_saliency", "sal_batch_workspace_size", "sal_saliency_batched",
+            "sal_combine", "sal_saliency", "sal_host_workspace_size", "sal_saliency_host", "sal_host_release",
+            "sal_batch_workspace_size", "sal_saliency_batched",
             "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",
             "sal_autotune_batched", "sal_autotune_query", "sal_autotune_save", "sal_autotune_load",
             "sal_autotune_clear", "sal_device_status", "sal_test_stall_tensor_cores", "sal_surrogate_param_count",

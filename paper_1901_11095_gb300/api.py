@@ -159,6 +159,53 @@ def sal_saliency(V: torch.Tensor, p: SalParams, S: torch.Tensor | None = None, s
     return S, stats
 
 
+def _host(t: torch.Tensor, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be torch.float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def sal_host_workspace_size(dims: SalDims, p: SalParams) -> int:
+    n = ctypes.c_size_t()
+    check(N.lib().sal_host_workspace_size(dims, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_saliency_host(V_host: torch.Tensor, p: SalParams, S_host: torch.Tensor | None = None,
+                      stats: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
+                      done_event=None, device=None) -> torch.Tensor:
+    """The whole method on a volume in host memory (pin it for overlap): V_host -> S_host.
+
+    The library copies V in, runs the kernels and copies S out; successive calls on the same
+    workspace overlap their copies with each other's kernels.  With `done_event` (a
+    torch.cuda.Event) S_host is ready when the event completes; otherwise when `stream` does.
+    """
+    dims = SalDims(*[int(v) for v in V_host.shape])
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if S_host is None:
+        S_host = torch.empty(tuple(V_host.shape), dtype=torch.float32, pin_memory=V_host.is_pinned())
+    if ws is None:
+        ws = torch.empty(sal_host_workspace_size(dims, p), device=dev, dtype=torch.uint8)
+    sp = _dev(stats, torch.float64, "stats") if stats is not None else None
+    ev = None
+    if done_event is not None:
+        if not done_event.cuda_event:
+            done_event.record(stream if stream is not None else torch.cuda.current_stream(dev))
+        ev = done_event.cuda_event
+    check(N.lib().sal_saliency_host(_host(V_host, "V_host"), dims, ctypes.byref(p), _host(S_host, "S_host"), sp,
+                                    _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream), ev))
+    return S_host
+
+
+def sal_host_release(ws: torch.Tensor) -> None:
+    """Releases the streams and events the library keeps for this workspace."""
+    check(N.lib().sal_host_release(_dev(ws, torch.uint8, "ws")))
+
+
 def _volumes(Vs, Ss):
     arr = (SalVolume * len(Vs))()
     for i, (V, S) in enumerate(zip(Vs, Ss)):

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 
@@ -166,6 +167,65 @@ sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, floa
     sal::EVolDesc v{V, E, d.T, d.X, d.Y};
     cudaError_t e = sal::launch_energy_fp32_batch(&v, 1, p->L, p->boundary, shape, false, s);
     return e == cudaSuccess ? SAL_OK : cuda_fail(e, "spectral energy launch");
+}
+
+// Workspace of the host-buffer entry point: two V buffers, E, S_m, two S buffers, the
+// reduction partials and the statistics, each 256-byte aligned.
+struct HostLayout {
+    size_t V[2], E, Sm, S[2], partials, stats, total;
+};
+
+HostLayout host_layout(sal_dims d)
+{
+    const size_t N = (size_t)(d.T * d.X * d.Y), f = sizeof(float);
+    HostLayout h;
+    h.V[0] = 0;
+    h.V[1] = round256(h.V[0] + N * f);
+    h.E = round256(h.V[1] + N * f);
+    h.Sm = round256(h.E + 3 * N * f);
+    h.S[0] = round256(h.Sm + 3 * N * f);
+    h.S[1] = round256(h.S[0] + N * f);
+    h.partials = round256(h.S[1] + N * f);
+    h.stats = round256(h.partials + 9 * (size_t)sal::dcs_num_partials(d) * sizeof(double));
+    h.total = round256(h.stats + SAL_STATS_LEN * sizeof(double));
+    return h;
+}
+
+// Streams and events that order the calls on one workspace: the V copy of a call waits for
+// the kernels of the call that last read the same V buffer, the combine of a call for the
+// copy-back of the call that last wrote the same S buffer.
+struct HostPipe {
+    int dev = -1;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t v_free[2] = {nullptr, nullptr}, s_free[2] = {nullptr, nullptr};
+    cudaEvent_t v_ready = nullptr, s_ready = nullptr, s_done = nullptr;
+    int parity = 0;
+};
+std::mutex g_pipe_mu;
+std::map<const void *, HostPipe> g_pipes;
+
+cudaError_t pipe_create(HostPipe &hp, int dev)
+{
+    hp.dev = dev;
+    cudaError_t e = cudaStreamCreateWithFlags(&hp.h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp.d2h, cudaStreamNonBlocking);
+    cudaEvent_t *evs[] = {&hp.v_free[0], &hp.v_free[1], &hp.s_free[0], &hp.s_free[1], &hp.v_ready, &hp.s_ready,
+                          &hp.s_done};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    return e;
+}
+
+void pipe_destroy(HostPipe &hp)
+{
+    if (hp.h2d) cudaStreamSynchronize(hp.h2d);
+    if (hp.d2h) cudaStreamSynchronize(hp.d2h);
+    cudaEvent_t evs[] = {hp.v_free[0], hp.v_free[1], hp.s_free[0], hp.s_free[1], hp.v_ready, hp.s_ready, hp.s_done};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (hp.h2d) cudaStreamDestroy(hp.h2d);
+    if (hp.d2h) cudaStreamDestroy(hp.d2h);
+    hp = HostPipe{};
 }
 
 // Workspace layout of a batch: per volume E [3N] floats, S_m [3N] floats and its [9][tiles]
@@ -404,6 +464,97 @@ sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, floa
     if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");
     e = sal::launch_combine(Sm, st, dims, p, S, cs);
     if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+    return ok();
+}
+
+sal_status sal_host_workspace_size(sal_dims dims, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = host_layout(dims).total;
+    return ok();
+}
+
+sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_params *p, float *S_host, double *stats,
+                             void *ws, size_t ws_bytes, void *stream, void *done_event)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V_host || !S_host || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(ws) || (stats && !aligned16(stats)))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    if (p->precision != SAL_PREC_FP32 && !sal::energy_tc_supported(p->L, p->precision))
+        return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for L = %d", p->precision, p->L);
+    const HostLayout h = host_layout(dims);
+    if (ws_bytes < h.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, h.total);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+    std::lock_guard<std::mutex> lock(g_pipe_mu);
+    HostPipe &hp = g_pipes[ws];
+    if (hp.dev < 0) {
+        e = pipe_create(hp, dev);
+        if (e != cudaSuccess) {
+            pipe_destroy(hp);
+            g_pipes.erase(ws);
+            return cuda_fail(e, "stream / event creation");
+        }
+    } else if (hp.dev != dev) {
+        return fail(SAL_ERR_INVALID_ARG, "workspace was first used on device %d, not %d", hp.dev, dev);
+    }
+    const int b = hp.parity;
+    char *base = (char *)ws;
+    float *Vd = (float *)(base + h.V[b]), *Sd = (float *)(base + h.S[b]);
+    float *E = (float *)(base + h.E), *Sm = (float *)(base + h.Sm);
+    double *part = (double *)(base + h.partials);
+    double *st = stats ? stats : (double *)(base + h.stats);
+    const size_t bytes = (size_t)(dims.T * dims.X * dims.Y) * sizeof(float);
+    cudaStream_t cs = (cudaStream_t)stream;
+
+    // host -> device, once the kernels of the call that last read this V buffer are done
+    e = cudaStreamWaitEvent(hp.h2d, hp.v_free[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Vd, V_host, bytes, cudaMemcpyHostToDevice, hp.h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(hp.v_ready, hp.h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hp.v_ready, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
+    s = energy_dispatch(Vd, dims, p, E, cs);
+    if (s) return s;
+    e = cudaEventRecord(hp.v_free[b], cs);
+    if (e == cudaSuccess) e = sal::launch_dcs(E, dims, p, Sm, part, st, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");
+    // S buffer b is free once the copy-back of the call that last wrote it is done
+    e = cudaStreamWaitEvent(cs, hp.s_free[b], 0);
+    if (e == cudaSuccess) e = sal::launch_combine(Sm, st, dims, p, Sd, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+    e = cudaEventRecord(hp.s_ready, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.d2h, hp.s_ready, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S_host, Sd, bytes, cudaMemcpyDeviceToHost, hp.d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(hp.s_free[b], hp.d2h);
+    if (e == cudaSuccess) {
+        if (done_event) {
+            e = cudaEventRecord((cudaEvent_t)done_event, hp.d2h);
+        } else {
+            e = cudaEventRecord(hp.s_done, hp.d2h);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hp.s_done, 0);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy of S to the host");
+    hp.parity ^= 1;
+    return ok();
+}
+
+sal_status sal_host_release(void *ws)
+{
+    if (!ws) return fail(SAL_ERR_INVALID_ARG, "ws is NULL");
+    std::lock_guard<std::mutex> lock(g_pipe_mu);
+    auto it = g_pipes.find(ws);
+    if (it == g_pipes.end()) return ok();
+    pipe_destroy(it->second);
+    g_pipes.erase(it);
     return ok();
 }
 

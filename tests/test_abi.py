@@ -88,3 +88,18 @@ def test_bad_dims_and_pointers_rejected(lib):
 def test_status_strings(lib):
     for s in range(7):
         assert lib.sal_status_string(s).decode().startswith("SAL_")
+
+
+def test_host_entry_argument_checks(lib):
+    p = _p(lib)
+    d = N.SalDims(8, 8, 8)
+    n = ctypes.c_size_t()
+    assert lib.sal_host_workspace_size(d, ctypes.byref(p), ctypes.byref(n)) == 0
+    # two V, E, S_m and two S buffers (10 N floats) plus the reduction records
+    assert n.value >= 40 * 8 ** 3 and n.value % 256 == 0
+    assert lib.sal_saliency_host(None, d, ctypes.byref(p), None, None, None, 0, None, None) == N.SAL_ERR_INVALID_ARG
+    buf = (ctypes.c_float * 512)()
+    # a workspace below the queried size is refused before any copy or launch
+    assert lib.sal_saliency_host(buf, d, ctypes.byref(p), buf, None, 256, 16, None, None) == N.SAL_ERR_WORKSPACE
+    assert lib.sal_host_release(None) == N.SAL_ERR_INVALID_ARG
+    assert lib.sal_host_release(256) == N.SAL_OK          # never used: nothing to release
