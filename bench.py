@@ -50,17 +50,20 @@ ENERGY_TRAFFIC = {
 }
 
 
-def algorithmic_flops_per_voxel(L: int, R: int = 4) -> float:
+def algorithmic_flops_per_voxel(L: int, R: int = 4, BX: int = 8) -> float:
     """FP32 flops per voxel of the fused energy stage as the kernel's algorithm defines it (FMA = 2).
 
-    Stage t on the real cube columns and stage x on the mu >= 0 half, each once per voxel
-    column (no halo recomputation); stage y per line over strips of R windows: window 0 by
-    the +-k folded direct DFT, its rotation to the sliding phase, R - 1 sliding updates;
-    |F| = mul + add (or fma) + sqrt; 3 FMAs per (mu, |nu|, |omega|) weight group; final scale.
+    Stage t on the real cube columns, once per voxel column (no halo recomputation).  Stage
+    x on the mu >= 0 half over runs of BX outputs along x: output 0 by the +-k folded direct
+    DFT and its rotation to the sliding phase, BX - 1 sliding updates.  Stage y per line over
+    strips of R windows the same way, plus |F| = mul + add (or fma) + sqrt; 3 FMAs per
+    (mu, |nu|, |omega|) weight group; final scale.
     """
     H = (L - 1) // 2
-    real_pass = 5 * H + 4 * H * H                  # t stage, and x stage of mu = 0
-    cplx_pass = 10 * H + 8 * H * H + 4 * H         # x stage of one mu > 0
+    real_pass = 5 * H + 4 * H * H                  # t stage, and the direct x output of mu = 0
+    cplx_pass = 10 * H + 8 * H * H + 4 * H         # the direct x output of one mu > 0
+    x_real = (real_pass + 7 * H + (BX - 1) * (2 + 4 * H)) / BX
+    x_cplx = (cplx_pass + 18 * H + (BX - 1) * (5 + 16 * H)) / BX
     rot = 1 if R > 1 else 0
     cline = 10 * H + 4 + H * (8 * H + 9) + rot * 18 * H + (R - 1) * (9 + 25 * H)
     rline = 4 * H + H * (4 * H + 4) + rot * 9 * H + (R - 1) * (2 + 12 * H)
@@ -68,7 +71,7 @@ def algorithmic_flops_per_voxel(L: int, R: int = 4) -> float:
     groups = H + H * (H + 1) + H * (H + 1) ** 2
     pair_adds = H * H * (H + 1)
     y = (n_cl * cline + rline) / R + 6 * groups + pair_adds
-    return real_pass + (real_pass + H * cplx_pass) + y + 3
+    return real_pass + (x_real + H * x_cplx) + y + 3
 
 
 def load_peaks() -> dict:

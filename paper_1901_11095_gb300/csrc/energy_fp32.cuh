@@ -495,6 +495,122 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, c
     }
 }
 
+// Stage x by a sliding recurrence along x: one thread per (t, y') column of the tile walks
+// the BX output positions.  Window 0 by the folded direct DFT (centred phase); window r >= 1
+// by P_r(nu) = P_{r-1}(nu) + (z[r+2h] - z[r-1]) e^{-i th nu (r-1)}, starting from
+// P_0(nu) = e^{-i th nu h} F_0(nu); P_r(nu) = e^{-i th nu (r+h)} F_r(nu).  That unit factor
+// depends on (nu, x) only, the same for every y' of a G2 line, so the y transform carries it
+// unchanged into F and |F| does not see it.  mu = 0 (real input) writes lines nu = 0..h.
+template <class G>
+__device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY, BX = G::BX, NZX = BX + 2 * H;
+    constexpr int XS = L * PY;           // G1 stride between x'
+    constexpr int RS = L * G::PY2;       // G2 stride between output rows x
+    for (int i = threadIdx.x; i < G::BT * PY; i += G::NT) {
+        const int t = i / PY, yy = i - t * PY;
+        const float *g = sG1 + (t * G::HX * L) * PY + yy;
+        float2 *o = sG2 + ((t * BX) * L + H) * G::PY2 + yy;   // line nu = 0 of output row (t, x = 0)
+        if (mu == 0) {
+            float z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
+            const float z0 = z[H];
+            float sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const float p = z[H + k] + z[H - k];
+                sum += p;
+                U[k] = fmaf(-2.f, z0, p);
+                D[k] = z[H + k] - z[H - k];
+            }
+            o[0] = make_float2(sum, 0.f);
+            float pr[H + 1], pi[H + 1];
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                float A = 0.f, B = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
+                    B = fmaf(D[k], lo(tw.s2[(nu * k) % L]), B);
+                }
+                o[nu * G::PY2] = make_float2(A, -B);   // F_0(nu) = A - iB
+                // P_0 = F_0 e^{-i th nu h}: (A - iB)(c - is) = (Ac - Bs) - i(As + Bc)
+                const int k = (nu * H) % L;
+                const float c = lo(tw.c2[k]), sn = lo(tw.s2[k]);
+                pr[nu] = fmaf(A, c, -B * sn);
+                pi[nu] = -fmaf(A, sn, B * c);
+            }
+#pragma unroll
+            for (int r = 1; r < BX; ++r) {
+                const float d = z[r + 2 * H] - z[r - 1];
+                sum += d;
+                float2 *orow = o + r * RS;
+                orow[0] = make_float2(sum, 0.f);
+#pragma unroll
+                for (int nu = 1; nu <= H; ++nu) {
+                    const int k = (nu * (r - 1)) % L;
+                    pr[nu] = fmaf(d, lo(tw.c2[k]), pr[nu]);    // + d e^{-i th k}
+                    pi[nu] = fmaf(-d, lo(tw.s2[k]), pi[nu]);
+                    orow[nu * G::PY2] = make_float2(pr[nu], pi[nu]);
+                }
+            }
+        } else {
+            const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
+            const f2x m2 = pk(-2.f, -2.f), zero = pk(0.f, 0.f);
+            f2x z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = pk(g[n * XS + cre], g[n * XS + cim]);
+            const f2x z0 = z[H];
+            f2x sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const f2x p = add2(z[H + k], z[H - k]);
+                sum = add2(sum, p);
+                U[k] = fma2(z0, m2, p);
+                D[k] = sub2(z[H + k], z[H - k]);
+            }
+            f2x *o2 = reinterpret_cast<f2x *>(o);
+            o2[0] = sum;
+            f2x Pp[H + 1], Pm[H + 1];   // P(+nu), P(-nu)
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                f2x A = mul2(U[1], tw.c2[nu % L]);
+                f2x B = mul2(D[1], tw.s2[nu % L]);
+#pragma unroll
+                for (int k = 2; k <= H; ++k) {
+                    A = fma2(U[k], tw.c2[(nu * k) % L], A);
+                    B = fma2(D[k], tw.s2[(nu * k) % L], B);
+                }
+                const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+                const f2x Fp = pk(ax + by, ay - bx);   // F_0(+nu) = A - iB
+                const f2x Fm = pk(ax - by, ay + bx);   // F_0(-nu) = A + iB
+                o2[nu * G::PY2] = Fp;
+                o2[-nu * G::PY2] = Fm;
+                const int k = (nu * H) % L;
+                Pp[nu] = rot_acc<L>(zero, Fp, swapneg(Fp), tw, k);
+                Pm[nu] = rot_acc<L>(zero, Fm, swapneg(Fm), tw, (L - k) % L);
+            }
+#pragma unroll
+            for (int r = 1; r < BX; ++r) {
+                const f2x d = sub2(z[r + 2 * H], z[r - 1]);
+                const f2x dsw = swapneg(d);
+                sum = add2(sum, d);
+                f2x *orow = o2 + r * RS;
+                orow[0] = sum;
+#pragma unroll
+                for (int nu = 1; nu <= H; ++nu) {
+                    const int k = (nu * (r - 1)) % L;
+                    Pp[nu] = rot_acc<L>(Pp[nu], d, dsw, tw, k);
+                    Pm[nu] = rot_acc<L>(Pm[nu], d, dsw, tw, (L - k) % L);
+                    orow[nu * G::PY2] = Pp[nu];
+                    orow[-nu * G::PY2] = Pm[nu];
+                }
+            }
+        }
+    }
+}
+
 // Halo tile of V in shared memory; outside the volume the boundary extension supplies the
 // samples.  G provides BT, BX, BY, H, HX, PY, NV and NT.
 template <class G>
@@ -620,7 +736,7 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
 
 #pragma unroll 1
     for (int mu = 0; mu <= H; ++mu) {
-        x_stage<G>(sG1, sG2, mu, tw);
+        x_stage_slide<G>(sG1, sG2, mu, tw);
         __syncthreads();
         const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
         if (mu == 0) {
@@ -908,7 +1024,7 @@ __device__ __forceinline__ void energy_tile_pf(const TileRef &c, const TileRef *
 
 #pragma unroll 1
     for (int mu = 0; mu <= H; ++mu) {
-        x_stage<G>(sG1, sG2, mu, tw);
+        x_stage_slide<G>(sG1, sG2, mu, tw);
         __syncthreads();
         if (mu == H && nx) stage_v_async<G>(nx->V, nx->T, nx->X, nx->Y, bnd, nx->t0, nx->x0, nx->y0, sO);
         const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row

@@ -73,18 +73,22 @@ def test_autotune_single_volume_and_identical_results():
     c = api.sal_autotune(V, p)
     assert c["ms"] > 0 and c["shape"] >= 0
     got = api.sal_spectral_energy(V, p)                 # now with the tuned tile shape
-    assert torch.equal(got, ref)                         # every tile shape computes the same values
+    # every tile shape computes the same values up to the rounding of its sliding steps
+    assert float((got - ref).abs().max()) <= 5e-6 * float(ref.abs().max())
     api.sal_autotune_clear()
 
 
 @pytest.mark.parametrize("L", [3, 7])
-def test_every_tile_shape_and_mode_gives_identical_energies(L, tmp_path):
-    """Each candidate (tile shape, staging mode) is forced through a cache file; the kernels
-    differ only in how work is split and staged, so the energies must agree bit for bit."""
+def test_every_tile_shape_and_mode_agrees(L, tmp_path):
+    """Each candidate (tile shape, staging mode) is forced through a cache file.  The kernels
+    differ in how work is split and staged and in where the sliding recurrence along x
+    restarts (every BX outputs), so the energies agree to a few FP32 roundings; candidates
+    with the same x tile width and the sliding x stage (modes 0 and 3) agree bit for bit."""
     V = torch.from_numpy(synth.make_volume((19, 37, 75), seed=8)).to(DEV)
     p = api.params(L=L)
     api.sal_autotune_clear()
     ref = api.sal_spectral_energy(V, p)
+    ref_shape = api.sal_autotune_query(L, 0, V.numel())
     shape = 0
     while True:
         f = tmp_path / f"cache_{L}_{shape}.txt"
@@ -93,8 +97,12 @@ def test_every_tile_shape_and_mode_gives_identical_energies(L, tmp_path):
             api.sal_autotune_load(str(f))
         except N.SalError:
             break                                         # past the last candidate
-        assert api.sal_autotune_query(L, 0, V.numel())["shape"] == shape
-        assert torch.equal(api.sal_spectral_energy(V, p), ref), f"shape {shape}"
+        c = api.sal_autotune_query(L, 0, V.numel())
+        assert c["shape"] == shape
+        got = api.sal_spectral_energy(V, p)
+        assert float((got - ref).abs().max()) <= 5e-6 * float(ref.abs().max()), f"shape {shape}"
+        if c["bx"] == ref_shape["bx"] and c["mode"] in (0, 3):
+            assert torch.equal(got, ref), f"shape {shape}"
         shape += 1
     api.sal_autotune_clear()
     assert shape >= 2
