@@ -55,18 +55,17 @@ def algorithmic_flops_per_voxel(L: int, R: int = 4, BX: int = 8) -> float:
 
     Stage t on the real cube columns, once per voxel column (no halo recomputation).  Stage
     x on the mu >= 0 half over runs of BX outputs along x: output 0 by the +-k folded direct
-    DFT and its rotation to the sliding phase, BX - 1 sliding updates.  Stage y per line over
-    strips of R windows the same way, plus |F| = mul + add (or fma) + sqrt; 3 FMAs per
-    (mu, |nu|, |omega|) weight group; final scale.
+    DFT, BX - 1 sliding updates (started in the phase of the direct output, so without a
+    rotation).  Stage y per line over strips of R windows the same way, plus |F| = mul + add
+    (or fma) + sqrt; 3 FMAs per (mu, |nu|, |omega|) weight group; final scale.
     """
     H = (L - 1) // 2
     real_pass = 5 * H + 4 * H * H                  # t stage, and the direct x output of mu = 0
     cplx_pass = 10 * H + 8 * H * H + 4 * H         # the direct x output of one mu > 0
-    x_real = (real_pass + 7 * H + (BX - 1) * (2 + 4 * H)) / BX
-    x_cplx = (cplx_pass + 18 * H + (BX - 1) * (5 + 16 * H)) / BX
-    rot = 1 if R > 1 else 0
-    cline = 10 * H + 4 + H * (8 * H + 9) + rot * 18 * H + (R - 1) * (9 + 25 * H)
-    rline = 4 * H + H * (4 * H + 4) + rot * 9 * H + (R - 1) * (2 + 12 * H)
+    x_real = (real_pass + (BX - 1) * (2 + 4 * H)) / BX
+    x_cplx = (cplx_pass + (BX - 1) * (5 + 16 * H)) / BX
+    cline = 10 * H + 4 + H * (8 * H + 9) + (R - 1) * (9 + 25 * H)
+    rline = 4 * H + H * (4 * H + 4) + (R - 1) * (2 + 12 * H)
     n_cl = H + H * (2 * H + 1)
     groups = H + H * (H + 1) + H * (H + 1) ** 2
     pair_adds = H * H * (H + 1)
@@ -525,7 +524,7 @@ def run_ours(args, rank: int, world: int) -> None:
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    n_e2e = max(1, min(args.steps, 5))
+    n_e2e = max(1, args.steps)
     last = None
     for _ in range(n_e2e):
         last = e2e_step()
@@ -545,7 +544,9 @@ def run_ours(args, rank: int, world: int) -> None:
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
     k1_ms = statistics.mean(k1)
-    flops = algorithmic_flops_per_voxel(args.L) * N
+    tile = api.sal_autotune_query(args.L, p.precision, N)     # the tile shape the launches used
+    fpv = algorithmic_flops_per_voxel(args.L, BX=int(tile["bx"]))
+    flops = fpv * N
     achieved = flops / (k1_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
@@ -562,7 +563,7 @@ def run_ours(args, rank: int, world: int) -> None:
                      "traffic_source": traffic[1] if traffic else None,
                      "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
                                     f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
-                     "flops_per_voxel": algorithmic_flops_per_voxel(args.L)},
+                     "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]]},
         "kernels_ms": {"spectral_energy": k1_ms, "directional_compare_and_stats": statistics.mean(k2),
                        "combine": statistics.mean(k4)},
         "hbm_stages": {"directional_compare_GBs": k2_gbs, "combine_GBs": k4_gbs, "peak_GBs": hbm,

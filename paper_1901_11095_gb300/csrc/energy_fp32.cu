@@ -17,16 +17,17 @@ struct ShapeList {
     TileShape s[kMaxShapes];
 };
 // Candidate tile shapes (BT x BX x BY output voxels per CTA, staging mode) per cube side;
-// index 0 is the default when the autotuner has not chosen.  The order must match the
+// index 0 is the default when the autotuner has not chosen: the fastest on a 256^3 volume
+// (and, for L = 7, on the 462 x 951 x 651 volume) in a measured sweep of the candidates.  The order must match the
 // switch of each energy_fp32_l*.cu.
 const ShapeList kShapes[] = {
-    {3, {{2, 8, 32, 0}, {4, 8, 32, 0}, {1, 16, 32, 0}}},
-    {5, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
-    {7, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}, {2, 8, 32, 3}, {2, 8, 32, 2}, {1, 16, 32, 3}}},
-    {9, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
-    {11, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
-    {13, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
-    {15, {{1, 8, 32, 0}, {1, 16, 32, 0}}},
+    {3, {{2, 8, 32, 0}, {4, 8, 32, 0}, {2, 16, 32, 0}}},
+    {5, {{2, 8, 32, 0}, {1, 8, 32, 0}, {2, 16, 32, 0}}},
+    {7, {{2, 8, 32, 0}, {2, 16, 32, 0}, {2, 8, 32, 3}, {1, 16, 32, 0}, {2, 8, 32, 2}}},
+    {9, {{2, 8, 32, 0}, {2, 16, 32, 0}, {1, 16, 32, 0}}},
+    {11, {{2, 16, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
+    {13, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
+    {15, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
 };
 const ShapeList *shapes_of(int L)
 {

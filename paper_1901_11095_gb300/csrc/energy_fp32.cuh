@@ -210,6 +210,13 @@ __device__ __forceinline__ f2x rot_acc(f2x P, f2x d, f2x dsw, const Tw<L> &tw, i
 
 __device__ __forceinline__ f2x swapneg(f2x d) { return pk(hi(d), -lo(d)); }
 
+// Twiddle index of w * j modulo L in 0..L-1 for any sign of j (compile-time when w, j are).
+template <int L>
+__host__ __device__ constexpr int tw_index(int w, int j)
+{
+    return ((w * j) % L + L) % L;
+}
+
 __device__ __forceinline__ float cabs2(f2x v)
 {
     const f2x q = mul2(v, v);
@@ -218,9 +225,9 @@ __device__ __forceinline__ float cabs2(f2x v)
 
 // Magnitudes of the R consecutive windows of one complex line, window r centred at
 // Z[H + r]: m[r][0] = |F_r(0)|, m[r][w] = |F_r(w)| + |F_r(-w)|.  Window 0 by the folded
-// direct DFT; the others by the sliding recurrence on P_r(w) = sum_{n=r}^{r+2h} Z[n]
-// e^{-i th w n} (|P_r| = |F_r|): P_{r+1} = P_r + (Z[r+2h+1] - Z[r]) e^{-i th w r}, the
-// twiddles of a whole period being equal.  P_0(w) = e^{-i th w h} F_0(w).
+// direct DFT; the others by a sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w)
+// (|Q_r| = |F_r|): Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the
+// twiddles of a whole period are equal; Q_0 = F_0 needs no rotation.
 template <int L, int R, int NZ>
 __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
 {
@@ -252,11 +259,8 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
         const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
         const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
         m[0][w] = sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm));
-        if (R > 1) {
-            const f2x zero = pk(0.f, 0.f);
-            P[H + w] = rot_acc<L>(zero, Fp, swapneg(Fp), tw, (w * H) % L);
-            P[H - w] = rot_acc<L>(zero, Fm, swapneg(Fm), tw, (L - (w * H) % L) % L);
-        }
+        P[H + w] = Fp;
+        P[H - w] = Fm;
     }
 #pragma unroll
     for (int r = 0; r + 1 < R; ++r) {
@@ -265,8 +269,8 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
         P[H] = add2(P[H], d);
 #pragma unroll
         for (int w = 1; w <= H; ++w) {
-            P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, (w * r) % L);
-            P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, (L - (w * r) % L) % L);
+            P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, tw_index<L>(w, r - H));
+            P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, tw_index<L>(-w, r - H));
         }
         m[r + 1][0] = sqrt_approx(cabs2(P[H]));
 #pragma unroll
@@ -298,7 +302,7 @@ __device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const T
         }
         const f2x F = pk(A, -B);                 // F(w) = A - iB
         m[0][w] = sqrt_approx(fmaf(A, A, B * B));
-        if (R > 1) P[w] = rot_acc<L>(pk(0.f, 0.f), F, swapneg(F), tw, (w * H) % L);
+        P[w] = F;
     }
     m[0][0] = 0.f;
 #pragma unroll
@@ -307,7 +311,7 @@ __device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const T
         const f2x dsw = swapneg(d);
 #pragma unroll
         for (int w = 1; w <= H; ++w) {
-            P[w] = rot_acc<L>(P[w], d, dsw, tw, (w * r) % L);
+            P[w] = rot_acc<L>(P[w], d, dsw, tw, tw_index<L>(w, r - H));
             m[r + 1][w] = sqrt_approx(cabs2(P[w]));
         }
         m[r + 1][0] = 0.f;
@@ -496,11 +500,11 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, c
 }
 
 // Stage x by a sliding recurrence along x: one thread per (t, y') column of the tile walks
-// the BX output positions.  Window 0 by the folded direct DFT (centred phase); window r >= 1
-// by P_r(nu) = P_{r-1}(nu) + (z[r+2h] - z[r-1]) e^{-i th nu (r-1)}, starting from
-// P_0(nu) = e^{-i th nu h} F_0(nu); P_r(nu) = e^{-i th nu (r+h)} F_r(nu).  That unit factor
-// depends on (nu, x) only, the same for every y' of a G2 line, so the y transform carries it
-// unchanged into F and |F| does not see it.  mu = 0 (real input) writes lines nu = 0..h.
+// the BX output positions.  Window 0 by the folded direct DFT; window r >= 1 by
+// Q_r(nu) = Q_{r-1}(nu) + (z[r+2h] - z[r-1]) e^{-i th nu (r-1-h)} with Q_0 = F_0, so that
+// Q_r(nu) = e^{-i th nu r} F_r(nu).  That unit factor depends on (nu, x) only, the same for
+// every y' of a G2 line, so the y transform carries it unchanged into F and |F| does not
+// see it.  mu = 0 (real input) writes lines nu = 0..h.
 template <class G>
 __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
 {
@@ -534,12 +538,9 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
                     A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
                     B = fmaf(D[k], lo(tw.s2[(nu * k) % L]), B);
                 }
-                o[nu * G::PY2] = make_float2(A, -B);   // F_0(nu) = A - iB
-                // P_0 = F_0 e^{-i th nu h}: (A - iB)(c - is) = (Ac - Bs) - i(As + Bc)
-                const int k = (nu * H) % L;
-                const float c = lo(tw.c2[k]), sn = lo(tw.s2[k]);
-                pr[nu] = fmaf(A, c, -B * sn);
-                pi[nu] = -fmaf(A, sn, B * c);
+                o[nu * G::PY2] = make_float2(A, -B);   // F_0(nu) = A - iB = Q_0(nu)
+                pr[nu] = A;
+                pi[nu] = -B;
             }
 #pragma unroll
             for (int r = 1; r < BX; ++r) {
@@ -549,7 +550,7 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
                 orow[0] = make_float2(sum, 0.f);
 #pragma unroll
                 for (int nu = 1; nu <= H; ++nu) {
-                    const int k = (nu * (r - 1)) % L;
+                    const int k = tw_index<L>(nu, r - 1 - H);
                     pr[nu] = fmaf(d, lo(tw.c2[k]), pr[nu]);    // + d e^{-i th k}
                     pi[nu] = fmaf(-d, lo(tw.s2[k]), pi[nu]);
                     orow[nu * G::PY2] = make_float2(pr[nu], pi[nu]);
@@ -557,7 +558,7 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
             }
         } else {
             const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
-            const f2x m2 = pk(-2.f, -2.f), zero = pk(0.f, 0.f);
+            const f2x m2 = pk(-2.f, -2.f);
             f2x z[NZX];
 #pragma unroll
             for (int n = 0; n < NZX; ++n) z[n] = pk(g[n * XS + cre], g[n * XS + cim]);
@@ -587,9 +588,8 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
                 const f2x Fm = pk(ax - by, ay + bx);   // F_0(-nu) = A + iB
                 o2[nu * G::PY2] = Fp;
                 o2[-nu * G::PY2] = Fm;
-                const int k = (nu * H) % L;
-                Pp[nu] = rot_acc<L>(zero, Fp, swapneg(Fp), tw, k);
-                Pm[nu] = rot_acc<L>(zero, Fm, swapneg(Fm), tw, (L - k) % L);
+                Pp[nu] = Fp;
+                Pm[nu] = Fm;
             }
 #pragma unroll
             for (int r = 1; r < BX; ++r) {
@@ -600,7 +600,7 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
                 orow[0] = sum;
 #pragma unroll
                 for (int nu = 1; nu <= H; ++nu) {
-                    const int k = (nu * (r - 1)) % L;
+                    const int k = tw_index<L>(nu, r - 1 - H);
                     Pp[nu] = rot_acc<L>(Pp[nu], d, dsw, tw, k);
                     Pm[nu] = rot_acc<L>(Pm[nu], d, dsw, tw, (L - k) % L);
                     orow[nu * G::PY2] = Pp[nu];
@@ -1161,7 +1161,20 @@ cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persis
         v.X = vols[i].X;
         v.Y = vols[i].Y;
         v.tile0 = total;
-        total += energy_tiles<G>(v.T, v.X, v.Y, &v.tiles_x, &v.tiles_y);
+        const int64_t tiles = energy_tiles<G>(v.T, v.X, v.Y, &v.tiles_x, &v.tiles_y);
+        if (vols[i].t_hi >= 0) {
+            // a range of output planes: tiles are numbered t-major, so the range is contiguous
+            if (n != 1 || vols[i].t_lo < 0 || vols[i].t_lo % G::BT != 0 || vols[i].t_hi > v.T ||
+                (vols[i].t_hi % G::BT != 0 && vols[i].t_hi != v.T))
+                return cudaErrorInvalidValue;
+            const int64_t per_t = (int64_t)v.tiles_x * v.tiles_y;
+            const int64_t k0 = vols[i].t_lo / G::BT * per_t;
+            const int64_t k1 = (vols[i].t_hi + G::BT - 1) / G::BT * per_t;
+            v.tile0 = -k0;                        // launch tile k is volume tile k + k0
+            total = k1 > k0 ? k1 - k0 : 0;
+        } else {
+            total += tiles;
+        }
     }
     bt.total = total;
     if (total <= 0) return cudaSuccess;

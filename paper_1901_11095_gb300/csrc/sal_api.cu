@@ -194,11 +194,14 @@ HostLayout host_layout(sal_dims d)
 // Streams and events that order the calls on one workspace: the V copy of a call waits for
 // the kernels of the call that last read the same V buffer, the combine of a call for the
 // copy-back of the call that last wrote the same S buffer.
+constexpr int kHostChunks = 4;   // pieces of V (along t) whose copies overlap the first kernels
+
 struct HostPipe {
     int dev = -1;
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t v_free[2] = {nullptr, nullptr}, s_free[2] = {nullptr, nullptr};
     cudaEvent_t v_ready = nullptr, s_ready = nullptr, s_done = nullptr;
+    cudaEvent_t chunk[kHostChunks] = {};
     int parity = 0;
 };
 std::mutex g_pipe_mu;
@@ -213,6 +216,8 @@ cudaError_t pipe_create(HostPipe &hp, int dev)
                           &hp.s_done};
     for (cudaEvent_t *ev : evs)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (cudaEvent_t &ev : hp.chunk)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     return e;
 }
 
@@ -222,6 +227,8 @@ void pipe_destroy(HostPipe &hp)
     if (hp.d2h) cudaStreamSynchronize(hp.d2h);
     cudaEvent_t evs[] = {hp.v_free[0], hp.v_free[1], hp.s_free[0], hp.s_free[1], hp.v_ready, hp.s_ready, hp.s_done};
     for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : hp.chunk)
         if (ev) cudaEventDestroy(ev);
     if (hp.h2d) cudaStreamDestroy(hp.h2d);
     if (hp.d2h) cudaStreamDestroy(hp.d2h);
@@ -517,12 +524,43 @@ sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_param
 
     // host -> device, once the kernels of the call that last read this V buffer are done
     e = cudaStreamWaitEvent(hp.h2d, hp.v_free[b], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Vd, V_host, bytes, cudaMemcpyHostToDevice, hp.h2d);
-    if (e == cudaSuccess) e = cudaEventRecord(hp.v_ready, hp.h2d);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hp.v_ready, 0);
     if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
-    s = energy_dispatch(Vd, dims, p, E, cs);
-    if (s) return s;
+    const int64_t XY = dims.X * dims.Y;
+    if (p->precision == SAL_PREC_FP32 && dims.T >= 64) {
+        // V in pieces of whole planes (multiples of 16, so of every tile height); the energies
+        // of a piece's output planes start once it and the next piece (its halo) are in
+        int64_t lo[kHostChunks + 1];
+        int64_t ct = (dims.T + kHostChunks - 1) / kHostChunks;
+        ct = (ct + 15) / 16 * 16;
+        int nch = 0;
+        for (int64_t t = 0; t < dims.T && nch < kHostChunks; t += ct) lo[nch++] = t;
+        lo[nch] = dims.T;
+        for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+            e = cudaMemcpyAsync(Vd + lo[c] * XY, V_host + lo[c] * XY, (size_t)((lo[c + 1] - lo[c]) * XY) * sizeof(float),
+                                cudaMemcpyHostToDevice, hp.h2d);
+            if (e == cudaSuccess) e = cudaEventRecord(hp.chunk[c], hp.h2d);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
+        const int shape = sal::autotune_lookup(p->L, p->precision, sal::size_class_of(dims.T * XY));
+        for (int c = 0; c < nch; ++c) {
+            e = cudaStreamWaitEvent(cs, hp.chunk[c], 0);
+            if (e == cudaSuccess && c + 1 < nch) e = cudaStreamWaitEvent(cs, hp.chunk[c + 1], 0);
+            // a periodic extension reads the far end of the volume at the first and last planes
+            if (e == cudaSuccess && c == 0 && p->boundary == SAL_BND_PERIODIC)
+                e = cudaStreamWaitEvent(cs, hp.chunk[nch - 1], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "stream wait");
+            sal::EVolDesc v{Vd, E, dims.T, dims.X, dims.Y, lo[c], lo[c + 1]};
+            e = sal::launch_energy_fp32_batch(&v, 1, p->L, p->boundary, shape, false, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "spectral energy launch");
+        }
+    } else {
+        e = cudaMemcpyAsync(Vd, V_host, bytes, cudaMemcpyHostToDevice, hp.h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(hp.v_ready, hp.h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hp.v_ready, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
+        s = energy_dispatch(Vd, dims, p, E, cs);
+        if (s) return s;
+    }
     e = cudaEventRecord(hp.v_free[b], cs);
     if (e == cudaSuccess) e = sal::launch_dcs(E, dims, p, Sm, part, st, cs);
     if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");

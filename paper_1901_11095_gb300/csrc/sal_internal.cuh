@@ -56,11 +56,14 @@ struct EVolDesc {
     const float *V;
     float *E;
     int64_t T, X, Y;
+    // FP32 kernel, single volume only: compute the output planes [t_lo, t_hi) (both multiples
+    // of every candidate BT, or t_hi = T); t_hi < 0 means the whole volume
+    int64_t t_lo = 0, t_hi = -1;
 };
 
 // Tile shapes of the spectral-energy kernel that the autotuner chooses among.
 struct TileShape {
-    int bt, bx, by, mode;   // mode: how the spectra of a tile are held in shared memory (0, 1, 2)
+    int bt, bx, by, mode;   // mode: how the spectra of a tile are held in shared memory (0..3)
 };
 constexpr int kMaxShapes = 6;
 int energy_num_shapes(int L);

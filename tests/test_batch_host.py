@@ -56,12 +56,12 @@ def test_autotune_cache_roundtrip_and_corrupt_file(lib, tmp_path):
     assert lib.sal_autotune_clear() == 0
     c = N.SalTileChoice()
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0
-    assert (c.shape, c.ms) == (0, 0.0) and (c.bt, c.bx, c.by) == (2, 8, 32)
+    assert (c.shape, c.ms) == (0, 0.0) and (c.bt, c.bx, c.by, c.mode) == (2, 8, 32, 0)
     good = tmp_path / "tune.txt"
     good.write_text("# sal autotune cache v1: L precision size_class shape ms\n7 0 1 2 31.5\n5 0 0 1 0.25\n")
     assert lib.sal_autotune_load(str(good).encode()) == 0
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0
-    assert (c.shape, c.bt, c.bx, c.by, c.size_class) == (2, 1, 8, 32, 1) and abs(c.ms - 31.5) < 1e-5
+    assert (c.shape, c.bt, c.bx, c.by, c.mode, c.size_class) == (2, 2, 8, 32, 3, 1) and abs(c.ms - 31.5) < 1e-5
     assert lib.sal_autotune_query(7, 0, 1000, ctypes.byref(c)) == 0 and c.shape == 0   # other size class
     saved = tmp_path / "saved.txt"
     assert lib.sal_autotune_save(str(saved).encode()) == 0

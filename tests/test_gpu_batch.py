@@ -44,9 +44,9 @@ def test_graph_replays_the_batch():
     vols = _batch(n=12, seed=3)
     Vs = [torch.from_numpy(v).to(DEV) for v in vols]
     p = api.params(L=7)
-    ref, _ = api.sal_saliency_batched(Vs, p)
     stats = torch.empty((len(Vs), 9), dtype=torch.float64, device=DEV)
     g = api.SalGraph(Vs, p, stats=stats)              # runs the autotuner first (empty cache)
+    ref, _ = api.sal_saliency_batched(Vs, p)          # the same (tuned) tile shape, outside the graph
     for _ in range(3):
         for S in g.Ss:
             S.fill_(float("nan"))

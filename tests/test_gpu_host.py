@@ -30,6 +30,17 @@ def test_host_call_equals_device_call(pinned):
     assert torch.equal(stats, st_ref)
 
 
+@pytest.mark.parametrize("bnd", ["reflect", "periodic"])
+def test_host_call_in_pieces_equals_device_call(bnd):
+    """T >= 64: V is copied in pieces of planes and the energies of each piece start once it
+    and its halo are on the device; the result must match the whole-volume call exactly."""
+    Vh = torch.from_numpy(synth.make_volume((150, 21, 45), seed=22)).pin_memory()
+    p = api.params(L=7, boundary=bnd)
+    Sh = api.sal_saliency_host(Vh, p)
+    torch.cuda.synchronize()
+    assert torch.equal(Sh, _device_result(Vh, p))
+
+
 def test_overlapped_sequence_keeps_every_result():
     """Consecutive calls on one workspace with done events: each call's S must be its own
     volume's result although V and S buffers alternate and copies overlap kernels."""
