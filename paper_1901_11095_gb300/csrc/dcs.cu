@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
         const int64_t left = T - t0;
         const int nsteps = (int)(((left < SC ? left : SC) + DT - 1) / DT);
         const int64_t gx = x0 + x, gy = y0 + QY * yq;
-        const bool vec = gy + QY <= Y && (Y & 3) == 0;
         float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
 
         stage(0, DT + 2);
@@ -386,26 +385,48 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
                 }
 
             if (gx < X) {
+                const bool full = gy + QY <= Y && t0 + rb + QT <= T;   // the whole 4 x 4 block is inside
+                float *o = Sm + ((t0 + rb) * X + gx) * Y + gy;
+                const int64_t plane = X * Y;
+                if (full) {
 #pragma unroll
-                for (int to = 0; to < QT; ++to) {
-                    const int64_t gt = t0 + rb + to;
-                    if (gt >= T) break;
-                    float *o = Sm + (gt * X + gx) * Y + gy;
+                    for (int to = 0; to < QT; ++to) {
 #pragma unroll
-                    for (int yo = 0; yo < QY; ++yo) {
-                        out[to][yo] *= k.invQ;
-                        if (gy + yo < Y) {
+                        for (int yo = 0; yo < QY; ++yo) {
+                            out[to][yo] *= k.invQ;
                             mn = fminf(mn, out[to][yo]);
                             mx = fmaxf(mx, out[to][yo]);
                             sm += out[to][yo];
                         }
+                        // widest aligned stores for this row start
+                        float *q = o + to * plane;
+                        const unsigned a = (unsigned)(reinterpret_cast<uintptr_t>(q) & 15);
+                        if (a == 0) {
+                            *reinterpret_cast<float4 *>(q) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
+                        } else if (a == 8) {
+                            *reinterpret_cast<float2 *>(q) = make_float2(out[to][0], out[to][1]);
+                            *reinterpret_cast<float2 *>(q + 2) = make_float2(out[to][2], out[to][3]);
+                        } else {   // 4 or 12: q + 1 is 8-byte aligned
+                            q[0] = out[to][0];
+                            *reinterpret_cast<float2 *>(q + 1) = make_float2(out[to][1], out[to][2]);
+                            q[3] = out[to][3];
+                        }
                     }
-                    if (vec) {
-                        *reinterpret_cast<float4 *>(o) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
-                    } else {
+                } else {
 #pragma unroll
-                        for (int yo = 0; yo < QY; ++yo)
-                            if (gy + yo < Y) o[yo] = out[to][yo];
+                    for (int to = 0; to < QT; ++to) {
+                        const int64_t gt = t0 + rb + to;
+                        if (gt >= T) break;
+#pragma unroll
+                        for (int yo = 0; yo < QY; ++yo) {
+                            out[to][yo] *= k.invQ;
+                            if (gy + yo < Y) {
+                                mn = fminf(mn, out[to][yo]);
+                                mx = fmaxf(mx, out[to][yo]);
+                                sm += out[to][yo];
+                                o[to * plane + yo] = out[to][yo];
+                            }
+                        }
                     }
                 }
             }

@@ -37,10 +37,11 @@ namespace energy_detail {
 //      is copied asynchronously (cp.async) while the current tile finishes.
 // Modes 1 and 2 trade some recomputation in stages t and x for a smaller footprint, i.e.
 // more resident CTAs per SM to hide the latencies of the y stage.
-template <int L_, int BT_, int BX_, int MODE_ = 0>
+template <int L_, int BT_, int BX_, int MODE_ = 0, int R_ = 4>
 struct EGeo {
     static constexpr int L = L_, H = (L_ - 1) / 2, BT = BT_, BX = BX_, MODE = MODE_;
-    static constexpr int BY = 32, R = 4, SY = BY / R;
+    static constexpr int BY = 32, R = R_, SY = BY / R;     // R consecutive outputs along y per thread
+    static_assert(R == 4 || R == 8, "strip of 4 or 8 outputs");
     static constexpr int ROWS = BT * BX;               // output rows (t, x) per tile
     static constexpr int NT = ROWS * SY;                // threads
     static constexpr int HX = BX + 2 * H;               // halo rows along x
@@ -689,9 +690,14 @@ __device__ __forceinline__ void store_outputs(float *__restrict__ E, int64_t T, 
     const int64_t N = T * X * Y;
     float *e0 = E + (gt * X + gx) * Y + gy;
     if (gy + G::R <= Y && (reinterpret_cast<uintptr_t>(e0) & 15) == 0 && (Y & 3) == 0) {
-        *reinterpret_cast<float4 *>(e0) = make_float4(et[0] * sc, et[1] * sc, et[2] * sc, et[3] * sc);
-        *reinterpret_cast<float4 *>(e0 + N) = make_float4(ex[0] * sc, ex[1] * sc, ex[2] * sc, ex[3] * sc);
-        *reinterpret_cast<float4 *>(e0 + 2 * N) = make_float4(ey[0] * sc, ey[1] * sc, ey[2] * sc, ey[3] * sc);
+#pragma unroll
+        for (int c = 0; c < G::R; c += 4) {
+            *reinterpret_cast<float4 *>(e0 + c) = make_float4(et[c] * sc, et[c + 1] * sc, et[c + 2] * sc, et[c + 3] * sc);
+            *reinterpret_cast<float4 *>(e0 + c + N) =
+                make_float4(ex[c] * sc, ex[c + 1] * sc, ex[c + 2] * sc, ex[c + 3] * sc);
+            *reinterpret_cast<float4 *>(e0 + c + 2 * N) =
+                make_float4(ey[c] * sc, ey[c + 1] * sc, ey[c + 2] * sc, ey[c + 3] * sc);
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < G::R; ++r) {
@@ -1145,7 +1151,6 @@ int64_t energy_tiles(int64_t T, int64_t X, int64_t Y, int *tx, int *ty)
 template <class G>
 cudaError_t launch_energy_impl(const EVolDesc *vols, int n, int bnd, bool persistent, cudaStream_t s)
 {
-    static_assert(G::R == 4, "four outputs per thread along y");
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     SpecTables tb;
     make_tables(G::L, &tb);
