@@ -388,8 +388,10 @@ def run_surrogate(args) -> None:
     S = torch.empty_like(V)
     dcs_ws = torch.empty(api.sal_dcs_workspace_size(api.dims_of(V), p), device=dev, dtype=torch.uint8)
 
-    def surr_path(thr):
-        _, counts = model.infer(V, p, threshold=thr, E=E)
+    p_tc = api.params(L=args.L, precision="bf16")    # hidden layers on the tensor cores
+
+    def surr_path(thr, pp=p):
+        _, counts = model.infer(V, pp, threshold=thr, E=E)
         api.sal_directional_compare(E, p, Sm=Sm, stats=st, ws=dcs_ws)
         api.sal_combine(Sm, st, p, S=S)
         return counts
@@ -407,13 +409,14 @@ def run_surrogate(args) -> None:
            "training": {"volumes": args.train_volumes, "steps": args.train_steps, "crop": 48,
                         "seconds": t_train, "label_seconds": t_data, "loss_first": hist[0][1],
                         "loss_last": hist[-1][1]}}
-    for name, thr in (("fallback_2e-2", 2e-2), ("surrogate_only", 1e30)):
-        counts = surr_path(thr)
+    for name, thr, pp in (("fallback_2e-2", 2e-2, p), ("surrogate_only", 1e30, p),
+                          ("fallback_2e-2_tensor_cores", 2e-2, p_tc), ("surrogate_only_tensor_cores", 1e30, p_tc)):
+        counts = surr_path(thr, pp)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            counts = surr_path(thr)
+            counts = surr_path(thr, pp)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / args.steps
@@ -434,6 +437,21 @@ def run_surrogate(args) -> None:
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
     out["plain_fp32"] = {"voxels_per_s": N / (ms / 1e3), "ms_per_step": ms}
+    # the network alone (5 convolution layers, no check, no compare / combine)
+    for name, pp in (("forward_cuda_cores", p), ("forward_tensor_cores", p_tc)):
+        model.forward(V, E=E, p=pp)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            model.forward(V, E=E, p=pp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        macs = 27 * (1 * 24 + 3 * 24 * 24 + 24 * 3)
+        out[name] = {"ms": ms, "voxels_per_s": N / (ms / 1e3), "macs_per_voxel": macs,
+                     "tflops": 2 * macs * N / (ms / 1e3) / 1e12}
+    api.sal_device_status()
     out["value"] = out["fallback_2e-2"]["voxels_per_s"]
     out["speedup_vs_plain"] = out["value"] / out["plain_fp32"]["voxels_per_s"]
     print(json.dumps(out), flush=True)

@@ -287,7 +287,11 @@ SAL_API sal_status sal_surrogate_param_count(int64_t *n);
  * = 1: every FP32 activation kept for the backward pass, 972 B/voxel). */
 SAL_API sal_status sal_surrogate_workspace_size(sal_dims dims, int32_t training, size_t *bytes);
 /* E [3][T*X*Y] predicted from V (device pointers).  With training = 1 the activations stay in
- * `ws` for sal_surrogate_backward. */
+ * `ws` for sal_surrogate_backward (FP32 activations, CUDA cores).  With training = 0 the
+ * activations are BF16; p->precision = SAL_PREC_BF16 then runs the three hidden 24 -> 24
+ * layers as tcgen05 products (BF16 operands, FP32 accumulation; bounded waits, a timeout
+ * reported by sal_device_status), any other precision keeps every layer on the CUDA cores.
+ * sal_surrogate_infer follows the same rule. */
 SAL_API sal_status sal_surrogate_forward(const float *V, sal_dims dims, const sal_params *p, const float *params,
                                          float *E, int32_t training, void *ws, size_t ws_bytes, void *stream);
 /* Gradient of L = 0.5 / count * sum (E_pred - E_target)^2 / rms^2 over voxels at least

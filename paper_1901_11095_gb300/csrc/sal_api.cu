@@ -803,7 +803,10 @@ sal_status sal_surrogate_forward(const float *V, sal_dims dims, const sal_params
         return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
     const size_t need = sal::surrogate_ws_bytes(dims, training != 0);
     if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
-    cudaError_t e = sal::surrogate_forward(V, dims, p->boundary, params, E, training != 0, ws, (cudaStream_t)stream);
+    const sal::TcControl c = sal::tc_control();
+    if (!training && p->precision == SAL_PREC_BF16 && !c.status) return fail(SAL_ERR_CUDA, "device status word unavailable");
+    cudaError_t e = sal::surrogate_forward(V, dims, p->boundary, params, E, training != 0, ws, (cudaStream_t)stream,
+                                           p->precision, &c);
     return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_forward");
 }
 
@@ -847,8 +850,10 @@ sal_status sal_surrogate_infer(const float *V, sal_dims dims, const sal_params *
     if (!(threshold >= 0.f)) return fail(SAL_ERR_INVALID_ARG, "threshold must be >= 0");
     const size_t need = sal::surrogate_infer_ws_bytes(dims, p->L);
     if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    const sal::TcControl c = sal::tc_control();
+    if (p->precision == SAL_PREC_BF16 && !c.status) return fail(SAL_ERR_CUDA, "device status word unavailable");
     cudaError_t e = sal::surrogate_infer(V, dims, p->L, p->boundary, params, E, threshold, counts, ws,
-                                         (cudaStream_t)stream);
+                                         (cudaStream_t)stream, p->precision, &c);
     return e == cudaSuccess ? ok() : cuda_fail(e, "sal_surrogate_infer");
 }
 

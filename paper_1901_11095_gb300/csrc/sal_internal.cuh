@@ -155,12 +155,12 @@ void autotune_clear();
 int64_t surrogate_param_count();
 size_t surrogate_ws_bytes(sal_dims d, bool training);
 cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *params, float *E, bool training,
-                              void *ws, cudaStream_t s);
+                              void *ws, cudaStream_t s, int prec = SAL_PREC_FP32, const TcControl *tc = nullptr);
 cudaError_t surrogate_backward(const float *V, sal_dims d, int bnd, const float *params, const float *Etarget,
                                int margin, float *grads, double *loss, void *ws, cudaStream_t s);
 size_t surrogate_infer_ws_bytes(sal_dims d, int L);
 cudaError_t surrogate_infer(const float *V, sal_dims d, int L, int bnd, const float *params, float *E, float thr,
-                            int *counts, void *ws, cudaStream_t s);
+                            int *counts, void *ws, cudaStream_t s, int prec = SAL_PREC_FP32, const TcControl *tc = nullptr);
 cudaError_t surrogate_adam(float *params, const float *grads, float *m, float *v, int64_t n, int step, float lr,
                            float b1, float b2, float eps, cudaStream_t s);
 

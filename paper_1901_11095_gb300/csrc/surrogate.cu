@@ -14,6 +14,7 @@
 // result is exact.
 #include <cuda_bf16.h>
 
+#include "energy_tc.cuh"   // tcgen05 helpers: descriptors, bounded mbarrier wait, tensor-memory load
 #include "sal_internal.cuh"
 
 namespace sal {
@@ -45,8 +46,10 @@ enum { FWD_HIDDEN = 0, FWD_OUTPUT = 1, BWD_DATA = 2 };
 //   FWD_OUTPUT: (conv(in) + b) * out_scale stored as float
 //   BWD_DATA:   in = dL/dz of the next layer, weights transposed and flipped (the adjoint),
 //               samples outside the volume are zero; out = result * gelu'(zprev)
-// Weights are the FP32 master parameters rounded to BF16 as they are staged.
-template <int CI, int CO, typename TIN, typename TOUT, int MODE>
+// Weights are the FP32 master parameters rounded to BF16 as they are staged.  ILV: BF16
+// activations (input or output) are interleaved [voxel][channel] instead of planar
+// [channel][voxel] (the layout of the tensor-core layers).
+template <int CI, int CO, typename TIN, typename TOUT, int MODE, bool ILV = false>
 __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, int64_t T, int64_t X, int64_t Y,
                                                    int bnd, const float *__restrict__ in_scale_p,
                                                    const float *__restrict__ w, const float *__restrict__ b,
@@ -87,7 +90,9 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
                         ? ldf(in + (c0 + c) * N + (gt0 * X + gx0) * Y + gy0) : 0.f;
             } else {
                 const int64_t gt = ext_index(gt0, T, bnd), gx = ext_index(gx0, X, bnd), gy = ext_index(gy0, Y, bnd);
-                v = ldf(in + (c0 + c) * N + (gt * X + gx) * Y + gy) * in_scale;
+                const int64_t vox = (gt * X + gx) * Y + gy;
+                const bool ilv_in = ILV && sizeof(TIN) == 2;
+                v = ldf(in + (ilv_in ? vox * CI + (c0 + c) : (c0 + c) * N + vox)) * in_scale;
             }
             xs[e] = v;
         }
@@ -130,7 +135,8 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
             const float z = acc[o][r];
             if (MODE == FWD_HIDDEN) {
                 if (zout) zout[o * N + v] = z;
-                stf(out + o * N + v, gelu(z));
+                const bool ilv_out = ILV && sizeof(TOUT) == 2;
+                stf(out + (ilv_out ? v * CO + o : o * N + v), gelu(z));
             } else if (MODE == FWD_OUTPUT) {
                 stf(out + o * N + v, z * out_scale);
             } else {
@@ -368,7 +374,7 @@ void conv_tiles(sal_dims d, int *tx, int *ty, int64_t *n)
     *n = nt * nx * ny;
 }
 
-template <int CI, int CO, typename TIN, typename TOUT, int MODE>
+template <int CI, int CO, typename TIN, typename TOUT, int MODE, bool ILV = false>
 cudaError_t launch_conv(const TIN *in, sal_dims d, int bnd, const float *in_scale, const float *w, const float *b,
                         float *zout, TOUT *out, const float *out_scale, const float *zprev, cudaStream_t s)
 {
@@ -377,7 +383,7 @@ cudaError_t launch_conv(const TIN *in, sal_dims d, int bnd, const float *in_scal
     conv_tiles(d, &tx, &ty, &n);
     if (n > 0x7fffffffLL) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * ((size_t)CO * CI * 27 + (size_t)CC * HN);
-    auto k = conv_kernel<CI, CO, TIN, TOUT, MODE>;
+    auto k = conv_kernel<CI, CO, TIN, TOUT, MODE, ILV>;
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<(unsigned)n, SNT, smem, s>>>(in, d.T, d.X, d.Y, bnd, in_scale, w, b, zout, out, out_scale, zprev, tx, ty);
@@ -402,6 +408,213 @@ cudaError_t launch_wgrad(const float *a, const float *a_scale, const float *g, s
     if (gx > n) gx = n;
     dim3 grid((unsigned)gx, (CI + CC - 1) / CC);
     k<<<grid, SNT, smem, s>>>(a, a_scale, g, d.T, d.X, d.Y, bnd, tx, ty, n, dw, db);
+    return cudaGetLastError();
+}
+
+// ---- hidden 24 -> 24 layers on the tensor cores (inference) --------------------------------
+// Implicit GEMM per tap: for an output line (t, x, y0 .. y0 + 127),
+//     D[y][o] += sum_c A_tap[y][c] W[o][c][tap],  A_tap[y][c] = act[t + dt][x + dx][y + dy][c],
+// 27 taps x 2 products of K = 16 (channels 0..15, 16..31 with 24..31 zero), M = 128, N = 32
+// (outputs 24..31 zero), BF16 operands, FP32 accumulation in tensor memory.  The halo of the
+// line (3 x 3 lines x 130 rows x 32 channels) sits in shared memory as [line][channel group
+// of 8][y][8 channels], i.e. K-major core matrices of 8 rows x 16 bytes with the 8-row groups
+// 128 bytes apart and the channel groups 130 x 16 bytes apart: the operand of every tap is
+// the same buffer at another start address, so no operand is rebuilt per tap.  Two halo
+// buffers and two accumulators let the next line's copies and the previous line's epilogue
+// (bias, GELU, BF16, store) run while a line's products execute.  Activations interleaved
+// [voxel][24] BF16.  Every wait is bounded; on expiry the status word gets SAL_ERR_TIMEOUT.
+constexpr int TCY = 128, TCH = TCY + 2;                     // outputs per line tile, halo rows
+constexpr int TC_LINE = 4 * TCH * 16;                       // bytes of one halo line
+constexpr int TC_HALO = 9 * TC_LINE;                        // bytes of one halo buffer
+constexpr int TC_WB = 27 * 2 * 1024;                        // B operands [tap][k-step][32 x 16 BF16]
+constexpr int TC_NT = 256;
+constexpr size_t TC_SMEM = (size_t)TC_WB + 2 * TC_HALO + 64;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Copies the halo of line tile k (t, x, y0) into buf (channel groups 0..2; group 3 stays zero).
+__device__ __forceinline__ void tc_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
+                                         int bnd, int64_t k, int64_t ny, unsigned char *buf)
+{
+    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+    const int64_t y0 = yb * TCY;
+    for (int e = threadIdx.x; e < 9 * TCH * 3; e += TC_NT) {
+        const int line = e / (TCH * 3), r = e - line * (TCH * 3);
+        const int yy = r / 3, kc = r - yy * 3;
+        const int64_t gt = ext_index(tl + line / 3 - 1, T, bnd), gx = ext_index(xl + line % 3 - 1, X, bnd);
+        const int64_t gy = ext_index(y0 - 1 + yy, Y, bnd);
+        cp_async16(buf + line * TC_LINE + kc * (TCH * 16) + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem), "l"(a), "l"(b),
+                 "r"(idesc), "r"(acc));
+}
+
+// Bias, GELU, BF16 and store of one line tile's accumulator (tensor-memory columns col0..+31).
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int col0, int64_t k, int64_t X, int64_t Y, int64_t ny,
+                                            const float *sb, __nv_bfloat16 *__restrict__ out)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
+    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+    float v[16];
+    energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(col0 + 16 * h), v);
+    const int64_t y = yb * TCY + 32 * q + (threadIdx.x & 31);
+    if (y >= Y) return;
+    __nv_bfloat16 *o = out + ((tl * X + xl) * Y + y) * kWidth + 16 * h;
+    const int nc = h == 0 ? 16 : kWidth - 16;
+    uint32_t pk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float a = gelu(v[2 * j] + sb[16 * h + 2 * j]);
+        const float b = gelu(v[2 * j + 1] + sb[16 * h + 2 * j + 1]);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(a, b);
+        pk[j] = *reinterpret_cast<const uint32_t *>(&p2);
+    }
+    *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    if (nc == 16) *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+__global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
+                                                             int64_t X, int64_t Y, int bnd,
+                                                             const float *__restrict__ w, const float *__restrict__ b,
+                                                             __nv_bfloat16 *__restrict__ out, int *status, int stall,
+                                                             uint64_t limit_ns)
+{
+    using energy_detail::smem_u32;
+    extern __shared__ __align__(128) unsigned char tc_sm[];
+    unsigned char *sW = tc_sm;
+    auto sH = [&](int bi) { return tc_sm + TC_WB + bi * TC_HALO; };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tc_sm + TC_WB + 2 * TC_HALO);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    __shared__ float sb[32];
+
+    // B operands: element (o, c) of tap / k-step at core-matrix offset, BF16-rounded weights
+    for (int e = threadIdx.x; e < 27 * 2 * 32 * 16; e += TC_NT) {
+        const int kk = e & 15, n = (e >> 4) & 31, ts = e >> 9, tap = ts >> 1, ks = ts & 1;
+        const int c = ks * 16 + kk;
+        const float v = (n < kWidth && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(sW + ts * 1024 + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
+            __float2bfloat16_rn(v);
+    }
+    if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < kWidth ? b[threadIdx.x] : 0.f;
+    // channel group 3 (channels 24..31) of both halo buffers is zero for good
+    for (int e = threadIdx.x; e < 2 * 9 * TCH; e += TC_NT) {
+        const int bi = e / (9 * TCH), r = e - bi * 9 * TCH, line = r / TCH, yy = r - line * TCH;
+        *reinterpret_cast<uint4 *>(sH(bi) + line * TC_LINE + 3 * (TCH * 16) + yy * 16) = make_uint4(0, 0, 0, 0);
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny;
+    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, 32);
+    uint32_t phases = 0u;   // bit b: parity of the next completion of barrier b
+    bool ok = true;
+    int64_t prev = -1;
+    const int64_t k0 = blockIdx.x;
+    if (k0 < ntiles) tc_stage(in, T, X, Y, bnd, k0, ny, sH(0));
+    int i = 0;
+    for (int64_t k = k0; k < ntiles && ok; k += gridDim.x, ++i) {
+        const int bi = i & 1;
+        // this line's halo is in: make the copies visible to the tensor cores
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0 && !stall) {
+            const uint32_t hb = smem_u32(sH(bi)), wb = smem_u32(sW);
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dt = tap / 9, dx = (tap / 3) % 3, dy = tap % 3;
+                const uint32_t ab = hb + (dt * 3 + dx) * TC_LINE + dy * 16;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ad = energy_detail::smem_desc(ab + ks * 2 * (TCH * 16), TCH * 16, 128);
+                    const uint64_t bd = energy_detail::smem_desc(wb + (tap * 2 + ks) * 1024, 128, 256);
+                    tc_mma_bf16(tmem + 32 * bi, ad, bd, idesc, (tap | ks) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[bi]))
+                         : "memory");
+        }
+        // the previous line: its products must be done before its halo buffer is refilled
+        // and its accumulator read
+        if (prev >= 0) {
+            const bool done = energy_detail::mbar_wait(smem_u32(&bars[bi ^ 1]), (phases >> (bi ^ 1)) & 1u, limit_ns);
+            if (__syncthreads_or(!done)) {
+                ok = false;
+                break;
+            }
+            phases ^= 1u << (bi ^ 1);
+        }
+        const int64_t kn = k + gridDim.x;
+        if (kn < ntiles) tc_stage(in, T, X, Y, bnd, kn, ny, sH(bi ^ 1));
+        if (prev >= 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_epilogue(tmem, 32 * (bi ^ 1), prev, X, Y, ny, sb, out);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        prev = k;
+    }
+    if (ok && prev >= 0) {
+        const int bi = (i - 1) & 1;
+        const bool done = energy_detail::mbar_wait(smem_u32(&bars[bi]), (phases >> bi) & 1u, limit_ns);
+        if (__syncthreads_or(!done)) {
+            ok = false;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_epilogue(tmem, 32 * bi, prev, X, Y, ny, sb, out);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
+        // products that were issued may still be in flight: one more bounded wait on each
+        // barrier before the tensor memory is released
+        if (!stall) {
+            energy_detail::mbar_wait(smem_u32(&bars[0]), phases & 1u, limit_ns);
+            energy_detail::mbar_wait(smem_u32(&bars[1]), (phases >> 1) & 1u, limit_ns);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+cudaError_t launch_conv24_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const float *w, const float *b,
+                             __nv_bfloat16 *out, const TcControl &c, cudaStream_t s)
+{
+    const int64_t ny = (d.Y + TCY - 1) / TCY, ntiles = d.T * d.X * ny;
+    if (ntiles <= 0) return cudaSuccess;
+    cudaError_t e = set_smem(conv24_tc_kernel, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = ntiles < nsm ? ntiles : nsm;   // one CTA per SM (shared memory), persistent
+    conv24_tc_kernel<<<(unsigned)grid, TC_NT, TC_SMEM, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, c.status, c.stall,
+                                                            c.limit_ns);
     return cudaGetLastError();
 }
 
@@ -465,7 +678,7 @@ float *Bg(float *grads, int l) { return grads + param_offset(l) + (int64_t)kWidt
 }  // namespace
 
 cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *params, float *E, bool training,
-                              void *ws, cudaStream_t s)
+                              void *ws, cudaStream_t s, int prec, const TcControl *tc)
 {
     const int64_t N = d.T * d.X * d.Y;
     SurrWs w = carve(ws);
@@ -475,6 +688,17 @@ cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *
     rms_kernel<<<1, 1, 0, s>>>(w.sumsq, N, w.scale);
     SAL_TRY(cudaGetLastError());
     const float *P = params;
+    if (!training && prec == SAL_PREC_BF16) {
+        // hidden 24 -> 24 layers on the tensor cores; activations interleaved [voxel][24]
+        if (!tc || !tc->status) return cudaErrorInvalidValue;
+        __nv_bfloat16 *a0 = (__nv_bfloat16 *)w.data, *a1 = a0 + (int64_t)kWidth * N;
+        SAL_TRY((launch_conv<1, kWidth, float, __nv_bfloat16, FWD_HIDDEN, true>(V, d, bnd, w.scale, Wp(P, 0), Bp(P, 0), nullptr, a0, nullptr, nullptr, s)));
+        SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 1), Bp(P, 1), a1, *tc, s));
+        SAL_TRY(launch_conv24_tc(a1, d, bnd, Wp(P, 2), Bp(P, 2), a0, *tc, s));
+        SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 3), Bp(P, 3), a1, *tc, s));
+        SAL_TRY((launch_conv<kWidth, 3, __nv_bfloat16, float, FWD_OUTPUT, true>(a1, d, bnd, nullptr, Wp(P, 4), Bp(P, 4), nullptr, E, w.scale + 1, nullptr, s)));
+        return cudaSuccess;
+    }
     if (!training) {
         __nv_bfloat16 *a0 = (__nv_bfloat16 *)w.data, *a1 = a0 + (int64_t)kWidth * N;
         SAL_TRY((launch_conv<1, kWidth, float, __nv_bfloat16, FWD_HIDDEN>(V, d, bnd, w.scale, Wp(P, 0), Bp(P, 0), nullptr, a0, nullptr, nullptr, s)));
@@ -561,7 +785,7 @@ InferLayout infer_layout(sal_dims d, int L)
 size_t surrogate_infer_ws_bytes(sal_dims d, int L) { return infer_layout(d, L).total; }
 
 cudaError_t surrogate_infer(const float *V, sal_dims d, int L, int bnd, const float *params, float *E, float thr,
-                            int *counts, void *ws, cudaStream_t s)
+                            int *counts, void *ws, cudaStream_t s, int prec, const TcControl *tc)
 {
     const InferLayout w = infer_layout(d, L);
     if (w.bt <= 0 || FB_T % w.bt || FB_X % w.bx) return cudaErrorInvalidValue;
@@ -570,7 +794,7 @@ cudaError_t surrogate_infer(const float *V, sal_dims d, int L, int bnd, const fl
     float *eex = (float *)(base + w.eex), *sums = (float *)(base + w.sums);
     int64_t *list = (int64_t *)(base + w.list);
     int *ctr = (int *)(base + w.counters);          // [0] tiles queued, [1] blocks recomputed, [2] checked
-    SAL_TRY(surrogate_forward(V, d, bnd, params, E, false, base + w.fwd, s));
+    SAL_TRY(surrogate_forward(V, d, bnd, params, E, false, base + w.fwd, s, prec, tc));
     const int64_t ns = w.nb * FB_S;
     sample_coords_kernel<<<(unsigned)((ns + 255) / 256 < 4096 ? (ns + 255) / 256 : 4096), 256, 0, s>>>(d.T, d.X, d.Y, w.nbx,
                                                                                                       w.nby, w.nb, coords);

@@ -75,11 +75,15 @@ class Surrogate:
             self._ws = {key: torch.empty(n.value, dtype=torch.uint8, device=self.device)}
         return self._ws[key]
 
-    def forward(self, V: torch.Tensor, training: bool = False, E: torch.Tensor | None = None, stream=None):
+    def forward(self, V: torch.Tensor, training: bool = False, E: torch.Tensor | None = None, stream=None,
+                p=None):
+        """E from V.  Inference (training=False) with p.precision = bf16 runs the hidden layers
+        on the tensor cores."""
+        p = p if p is not None else self.p
         if E is None:
             E = torch.empty((3,) + tuple(V.shape), device=V.device, dtype=torch.float32)
         ws = self._workspace(V.shape, training)
-        check(N.lib().sal_surrogate_forward(_ptr(V), api.dims_of(V), ctypes.byref(self.p), _ptr(self.params),
+        check(N.lib().sal_surrogate_forward(_ptr(V), api.dims_of(V), ctypes.byref(p), _ptr(self.params),
                                             _ptr(E), int(training), _ptr(ws), ws.numel(), _stream(stream)))
         return E
 

@@ -46,6 +46,45 @@ def test_forward_matches_reference():
     assert np.abs(got_inf - ref).max() / np.abs(ref).max() < 3e-2
 
 
+@pytest.mark.parametrize("shape", [(12, 14, 40), (9, 7, 300)])
+def test_tensor_core_inference_matches_cuda_cores_and_reference(shape):
+    """Hidden layers as tcgen05 products (BF16 operands, FP32 accumulation) against the CUDA-core
+    inference (same BF16 activations) and the FP64 reference; lines of 128 outputs along y,
+    ragged at the end (40 and 300 = 2 x 128 + 44)."""
+    V = synth.make_volume(shape, seed=2)
+    model, params = _model(seed=4)
+    Vd = torch.from_numpy(V).to(DEV)
+    rms = np.sqrt(np.mean(V.astype(np.float64) ** 2))
+    ref = O.surrogate_forward(V[None].astype(np.float64) / rms, surrogate.WIDTHS, _bf16(params)) * rms
+    cc = model.forward(Vd, training=False).cpu().numpy()
+    api.sal_device_status()
+    tc = model.forward(Vd, training=False, p=api.params(precision="bf16")).cpu().numpy()
+    api.sal_device_status()
+    assert np.isfinite(tc).all()
+    assert np.abs(tc - cc).max() / np.abs(cc).max() < 1e-2
+    assert np.abs(tc - ref).max() / np.abs(ref).max() < 3e-2
+
+
+def test_tensor_core_inference_wait_runs_out_and_context_survives():
+    V = torch.from_numpy(synth.make_volume((6, 5, 130), seed=5)).to(DEV)
+    model, _ = _model(seed=6)
+    p = api.params(precision="bf16")
+    ref = model.forward(V, training=False, p=p).clone()
+    api.sal_device_status()
+    api.sal_test_stall_tensor_cores(True)
+    try:
+        model.forward(V, training=False, p=p)
+        with pytest.raises(N.SalError) as ei:
+            api.sal_device_status()
+        assert ei.value.status == N.SAL_ERR_TIMEOUT
+    finally:
+        api.sal_test_stall_tensor_cores(False)
+    api.sal_device_status()
+    again = model.forward(V, training=False, p=p)
+    api.sal_device_status()
+    assert torch.equal(again, ref)
+
+
 def test_backward_matches_reference():
     V = synth.make_volume((16, 17, 40), seed=2)
     model, params = _model(seed=4)
