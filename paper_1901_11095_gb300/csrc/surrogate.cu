@@ -542,15 +542,19 @@ __global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (threadIdx.x == 0 && !stall) {
-            const uint32_t hb = smem_u32(sH(bi)), wb = smem_u32(sW);
+            // one descriptor per operand; every tap and k-step is a compile-time byte offset
+            // added to its 14-bit start-address field (no carry: shared memory < 256 KB)
+            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sH(bi)), TCH * 16, 128);
+            const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
+            const uint32_t dtm = tmem + 32 * bi;
+#pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
-                const int dt = tap / 9, dx = (tap / 3) % 3, dy = tap % 3;
-                const uint32_t ab = hb + (dt * 3 + dx) * TC_LINE + dy * 16;
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ad = energy_detail::smem_desc(ab + ks * 2 * (TCH * 16), TCH * 16, 128);
-                    const uint64_t bd = energy_detail::smem_desc(wb + (tap * 2 + ks) * 1024, 128, 256);
-                    tc_mma_bf16(tmem + 32 * bi, ad, bd, idesc, (tap | ks) != 0);
+                    const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC_LINE + (tap % 3) * 16 +
+                                           ks * 2 * (TCH * 16)) >> 4;
+                    const uint32_t boff = ((tap * 2 + ks) * 1024) >> 4;
+                    tc_mma_bf16(dtm, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -602,16 +606,138 @@ __global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
+// The same layer with one halo buffer per CTA and two CTAs per SM: the halo keeps only the
+// three real channel groups per line (6240 bytes); the second k-step's upper group then reads
+// the next line's first group (or a zero pad after the last line), which meets the zero
+// weights of channels 24..31 and adds nothing.
+constexpr int TC1_LINE = 3 * TCH * 16;
+constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
+constexpr size_t TC1_SMEM = (size_t)TC_WB + TC1_HALO + 64;
+
+__device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
+                                          int bnd, int64_t k, int64_t ny, unsigned char *buf)
+{
+    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+    const int64_t y0 = yb * TCY;
+    for (int e = threadIdx.x; e < 9 * TCH * 3; e += TC_NT) {
+        const int line = e / (TCH * 3), r = e - line * (TCH * 3);
+        const int yy = r / 3, kc = r - yy * 3;
+        const int64_t gt = ext_index(tl + line / 3 - 1, T, bnd), gx = ext_index(xl + line % 3 - 1, X, bnd);
+        const int64_t gy = ext_index(y0 - 1 + yy, Y, bnd);
+        cp_async16(buf + line * TC1_LINE + kc * (TCH * 16) + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
+                                                              int64_t X, int64_t Y, int bnd,
+                                                              const float *__restrict__ w, const float *__restrict__ b,
+                                                              __nv_bfloat16 *__restrict__ out, int *status, int stall,
+                                                              uint64_t limit_ns)
+{
+    using energy_detail::smem_u32;
+    extern __shared__ __align__(128) unsigned char tc_sm[];
+    unsigned char *sW = tc_sm, *sHb = tc_sm + TC_WB;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tc_sm + TC_WB + TC1_HALO);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    __shared__ float sb[32];
+
+    for (int e = threadIdx.x; e < 27 * 2 * 32 * 16; e += TC_NT) {
+        const int kk = e & 15, n = (e >> 4) & 31, ts = e >> 9, tap = ts >> 1, ks = ts & 1;
+        const int c = ks * 16 + kk;
+        const float v = (n < kWidth && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(sW + ts * 1024 + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
+            __float2bfloat16_rn(v);
+    }
+    if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < kWidth ? b[threadIdx.x] : 0.f;
+    for (int e = threadIdx.x; e < TCH; e += TC_NT)   // the pad read by the last line's upper group
+        *reinterpret_cast<uint4 *>(sHb + 9 * TC1_LINE + e * 16) = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny;
+    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, 32);
+    uint32_t phase = 0u;
+    bool ok = true;
+    if ((int64_t)blockIdx.x < ntiles) tc1_stage(in, T, X, Y, bnd, blockIdx.x, ny, sHb);
+    for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0 && !stall) {
+            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sHb), TCH * 16, 128);
+            const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
+#pragma unroll
+            for (int tap = 0; tap < 27; ++tap) {
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC1_LINE + (tap % 3) * 16 +
+                                           ks * 2 * (TCH * 16)) >> 4;
+                    const uint32_t boff = ((tap * 2 + ks) * 1024) >> 4;
+                    tc_mma_bf16(tmem, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        const bool done = energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
+        if (__syncthreads_or(!done)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        // the halo is free: the next line's copies overlap this line's epilogue
+        const int64_t kn = k + gridDim.x;
+        if (kn < ntiles) tc1_stage(in, T, X, Y, bnd, kn, ny, sHb);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_epilogue(tmem, 0, k, X, Y, ny, sb, out);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
+        if (!stall) energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+constexpr bool kTcOneBuffer = true;   // two CTAs per SM with one halo each (else one CTA, two halos)
+
 cudaError_t launch_conv24_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const float *w, const float *b,
                              __nv_bfloat16 *out, const TcControl &c, cudaStream_t s)
 {
     const int64_t ny = (d.Y + TCY - 1) / TCY, ntiles = d.T * d.X * ny;
     if (ntiles <= 0) return cudaSuccess;
-    cudaError_t e = set_smem(conv24_tc_kernel, TC_SMEM);
-    if (e != cudaSuccess) return e;
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (kTcOneBuffer) {
+        cudaError_t e = set_smem(conv24_tc1_kernel, TC1_SMEM);
+        if (e != cudaSuccess) return e;
+        int64_t grid = 2 * (int64_t)nsm;                 // two CTAs per SM (shared memory), persistent
+        if (grid > ntiles) grid = ntiles;
+        conv24_tc1_kernel<<<(unsigned)grid, TC_NT, TC1_SMEM, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, c.status,
+                                                                  c.stall, c.limit_ns);
+        return cudaGetLastError();
+    }
+    cudaError_t e = set_smem(conv24_tc_kernel, TC_SMEM);
+    if (e != cudaSuccess) return e;
     const int64_t grid = ntiles < nsm ? ntiles : nsm;   // one CTA per SM (shared memory), persistent
     conv24_tc_kernel<<<(unsigned)grid, TC_NT, TC_SMEM, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, c.status, c.stall,
                                                             c.limit_ns);
