@@ -288,8 +288,8 @@ SAL_API sal_status sal_surrogate_param_count(int64_t *n);
 SAL_API sal_status sal_surrogate_workspace_size(sal_dims dims, int32_t training, size_t *bytes);
 /* E [3][T*X*Y] predicted from V (device pointers).  With training = 1 the activations stay in
  * `ws` for sal_surrogate_backward (FP32 activations, CUDA cores).  With training = 0 the
- * activations are BF16; p->precision = SAL_PREC_BF16 then runs the three hidden 24 -> 24
- * layers as tcgen05 products (BF16 operands, FP32 accumulation; bounded waits, a timeout
+ * activations are BF16; p->precision = SAL_PREC_BF16 then runs layers 2..5 (24 input
+ * channels) as tcgen05 products (BF16 operands, FP32 accumulation; bounded waits, a timeout
  * reported by sal_device_status), any other precision keeps every layer on the CUDA cores.
  * sal_surrogate_infer follows the same rule. */
 SAL_API sal_status sal_surrogate_forward(const float *V, sal_dims dims, const sal_params *p, const float *params,

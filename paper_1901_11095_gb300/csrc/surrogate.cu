@@ -606,13 +606,14 @@ __global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
-// The same layer with one halo buffer per CTA and two CTAs per SM: the halo keeps only the
-// three real channel groups per line (6240 bytes); the second k-step's upper group then reads
-// the next line's first group (or a zero pad after the last line), which meets the zero
-// weights of channels 24..31 and adds nothing.
+// Layers on the tensor cores with one halo buffer per CTA and two CTAs per SM.  The halo keeps
+// only the three real channel groups per line (6240 bytes); the second k-step's upper group
+// then reads the next line's first group (or a zero pad after the last line), which meets the
+// zero weights of channels 24..31 and adds nothing.  CO = 24: hidden layer (bias, GELU, BF16
+// interleaved out, N = 32); CO = 3: output layer (N = 16, outputs 3..15 zero; bias and the RMS
+// scale applied, FP32 E written planar [3][voxel]).
 constexpr int TC1_LINE = 3 * TCH * 16;
 constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
-constexpr size_t TC1_SMEM = (size_t)TC_WB + TC1_HALO + 64;
 
 __device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
                                           int bnd, int64_t k, int64_t ny, unsigned char *buf)
@@ -629,27 +630,31 @@ __device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
-                                                              int64_t X, int64_t Y, int bnd,
-                                                              const float *__restrict__ w, const float *__restrict__ b,
-                                                              __nv_bfloat16 *__restrict__ out, int *status, int stall,
-                                                              uint64_t limit_ns)
+template <int CO>
+__global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
+                                                            int64_t X, int64_t Y, int bnd,
+                                                            const float *__restrict__ w, const float *__restrict__ b,
+                                                            __nv_bfloat16 *__restrict__ out, float *__restrict__ E,
+                                                            const float *__restrict__ out_scale_p, int *status,
+                                                            int stall, uint64_t limit_ns)
 {
+    constexpr int NB = CO > 16 ? 32 : 16;       // N of the products
+    constexpr int BT = NB * 32;                 // bytes of one B tile (NB x 16 BF16)
     using energy_detail::smem_u32;
     extern __shared__ __align__(128) unsigned char tc_sm[];
-    unsigned char *sW = tc_sm, *sHb = tc_sm + TC_WB;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tc_sm + TC_WB + TC1_HALO);
+    unsigned char *sW = tc_sm, *sHb = tc_sm + 27 * 2 * BT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sHb + TC1_HALO);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     __shared__ float sb[32];
 
-    for (int e = threadIdx.x; e < 27 * 2 * 32 * 16; e += TC_NT) {
-        const int kk = e & 15, n = (e >> 4) & 31, ts = e >> 9, tap = ts >> 1, ks = ts & 1;
+    for (int e = threadIdx.x; e < 27 * 2 * NB * 16; e += TC_NT) {
+        const int kk = e & 15, n = (e >> 4) % NB, ts = e / (16 * NB), tap = ts >> 1, ks = ts & 1;
         const int c = ks * 16 + kk;
-        const float v = (n < kWidth && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
-        *reinterpret_cast<__nv_bfloat16 *>(sW + ts * 1024 + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
+        const float v = (n < CO && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(sW + ts * BT + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
             __float2bfloat16_rn(v);
     }
-    if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < kWidth ? b[threadIdx.x] : 0.f;
+    if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < CO ? b[threadIdx.x] : 0.f;
     for (int e = threadIdx.x; e < TCH; e += TC_NT)   // the pad read by the last line's upper group
         *reinterpret_cast<uint4 *>(sHb + 9 * TC1_LINE + e * 16) = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
@@ -665,9 +670,10 @@ __global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat1
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    const float out_scale = out_scale_p ? *out_scale_p : 1.f;
 
-    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny;
-    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, 32);
+    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny, Nv = T * X * Y;
+    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, NB);
     uint32_t phase = 0u;
     bool ok = true;
     if ((int64_t)blockIdx.x < ntiles) tc1_stage(in, T, X, Y, bnd, blockIdx.x, ny, sHb);
@@ -685,7 +691,7 @@ __global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat1
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC1_LINE + (tap % 3) * 16 +
                                            ks * 2 * (TCH * 16)) >> 4;
-                    const uint32_t boff = ((tap * 2 + ks) * 1024) >> 4;
+                    const uint32_t boff = ((tap * 2 + ks) * BT) >> 4;
                     tc_mma_bf16(tmem, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
                 }
             }
@@ -703,7 +709,22 @@ __global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat1
         const int64_t kn = k + gridDim.x;
         if (kn < ntiles) tc1_stage(in, T, X, Y, bnd, kn, ny, sHb);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tc_epilogue(tmem, 0, k, X, Y, ny, sb, out);
+        if (CO == kWidth) {
+            tc_epilogue(tmem, 0, k, X, Y, ny, sb, out);
+        } else {
+            const int warp = threadIdx.x >> 5, q = warp & 3;
+            if (warp < 4) {   // N = 16: one load per lane quadrant
+                float v[16];
+                energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16), v);
+                const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+                const int64_t y = yb * TCY + 32 * q + (threadIdx.x & 31);
+                if (y < Y) {
+                    const int64_t vox = (tl * X + xl) * Y + y;
+#pragma unroll
+                    for (int c = 0; c < CO; ++c) E[c * Nv + vox] = (v[c] + sb[c]) * out_scale;
+                }
+            }
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
@@ -717,6 +738,29 @@ __global__ void __launch_bounds__(TC_NT, 2) conv24_tc1_kernel(const __nv_bfloat1
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
+template <int CO>
+constexpr size_t tc1_smem() { return (size_t)27 * 2 * (CO > 16 ? 32 : 16) * 32 + TC1_HALO + 64; }
+
+// One layer on the tensor cores: CO = 24 (hidden) or 3 (output, writes E).
+template <int CO>
+cudaError_t launch_conv_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const float *w, const float *b,
+                           __nv_bfloat16 *out, float *E, const float *out_scale, const TcControl &c, cudaStream_t s)
+{
+    const int64_t ny = (d.Y + TCY - 1) / TCY, ntiles = d.T * d.X * ny;
+    if (ntiles <= 0) return cudaSuccess;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    constexpr size_t smem = tc1_smem<CO>();
+    cudaError_t e = set_smem(conv_tc1_kernel<CO>, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = 2 * (int64_t)nsm;                 // two CTAs per SM (shared memory), persistent
+    if (grid > ntiles) grid = ntiles;
+    conv_tc1_kernel<CO><<<(unsigned)grid, TC_NT, smem, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, E, out_scale, c.status,
+                                                           c.stall, c.limit_ns);
+    return cudaGetLastError();
+}
+
 constexpr bool kTcOneBuffer = true;   // two CTAs per SM with one halo each (else one CTA, two halos)
 
 cudaError_t launch_conv24_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const float *w, const float *b,
@@ -727,15 +771,7 @@ cudaError_t launch_conv24_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (kTcOneBuffer) {
-        cudaError_t e = set_smem(conv24_tc1_kernel, TC1_SMEM);
-        if (e != cudaSuccess) return e;
-        int64_t grid = 2 * (int64_t)nsm;                 // two CTAs per SM (shared memory), persistent
-        if (grid > ntiles) grid = ntiles;
-        conv24_tc1_kernel<<<(unsigned)grid, TC_NT, TC1_SMEM, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, c.status,
-                                                                  c.stall, c.limit_ns);
-        return cudaGetLastError();
-    }
+    if (kTcOneBuffer) return launch_conv_tc<kWidth>(in, d, bnd, w, b, out, nullptr, nullptr, c, s);
     cudaError_t e = set_smem(conv24_tc_kernel, TC_SMEM);
     if (e != cudaSuccess) return e;
     const int64_t grid = ntiles < nsm ? ntiles : nsm;   // one CTA per SM (shared memory), persistent
@@ -815,14 +851,15 @@ cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *
     SAL_TRY(cudaGetLastError());
     const float *P = params;
     if (!training && prec == SAL_PREC_BF16) {
-        // hidden 24 -> 24 layers on the tensor cores; activations interleaved [voxel][24]
+        // layers 2..5 on the tensor cores (layer 1 has a single input channel); activations
+        // interleaved [voxel][24]
         if (!tc || !tc->status) return cudaErrorInvalidValue;
         __nv_bfloat16 *a0 = (__nv_bfloat16 *)w.data, *a1 = a0 + (int64_t)kWidth * N;
         SAL_TRY((launch_conv<1, kWidth, float, __nv_bfloat16, FWD_HIDDEN, true>(V, d, bnd, w.scale, Wp(P, 0), Bp(P, 0), nullptr, a0, nullptr, nullptr, s)));
         SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 1), Bp(P, 1), a1, *tc, s));
         SAL_TRY(launch_conv24_tc(a1, d, bnd, Wp(P, 2), Bp(P, 2), a0, *tc, s));
         SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 3), Bp(P, 3), a1, *tc, s));
-        SAL_TRY((launch_conv<kWidth, 3, __nv_bfloat16, float, FWD_OUTPUT, true>(a1, d, bnd, nullptr, Wp(P, 4), Bp(P, 4), nullptr, E, w.scale + 1, nullptr, s)));
+        SAL_TRY(launch_conv_tc<3>(a1, d, bnd, Wp(P, 4), Bp(P, 4), nullptr, E, w.scale + 1, *tc, s));
         return cudaSuccess;
     }
     if (!training) {
