@@ -457,6 +457,35 @@ def run_surrogate(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+def run_surrogate_forward(args) -> None:
+    """The surrogate network alone (seeded initial weights, no training) on a 128 x 128 x 256
+    F3-kind volume: milliseconds per forward on the CUDA cores and with layers 2..5 on the
+    tensor cores.  A small, quick case for profiling the convolution kernels."""
+    import torch
+
+    from paper_1901_11095_gb300 import api, surrogate, synth
+
+    dev = torch.device("cuda:0")
+    V = torch.from_numpy(synth.make_volume((128, 128, 256), seed=0, kind="f3")).to(dev)
+    model = surrogate.Surrogate(dev, seed=0)
+    E = torch.empty((3,) + tuple(V.shape), device=dev, dtype=torch.float32)
+    out = {"mode": "surrogate forward", "volume": list(V.shape), "steps": args.steps, "warmup": args.warmup}
+    for name, prec in (("cuda_cores", "fp32"), ("tensor_cores", "bf16")):
+        p = api.params(precision=prec)
+        for _ in range(args.warmup):
+            model.forward(V, E=E, p=p)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            model.forward(V, E=E, p=p)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        api.sal_device_status()
+        out[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank: int, world: int) -> None:
     import torch
     import torch.distributed as dist
@@ -611,6 +640,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
     ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and time its inference")
+    ap.add_argument("--surrogate-forward", action="store_true",
+                    help="time the surrogate network alone (seeded weights) on a 128x128x256 volume")
     ap.add_argument("--train-volumes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     args = ap.parse_args()
@@ -631,6 +662,9 @@ def main():
         return
     if args.surrogate:
         run_surrogate(args)
+        return
+    if args.surrogate_forward:
+        run_surrogate_forward(args)
         return
     (run_batch if args.workload == "batch64" else run_ours)(args, rank, world)
     if world > 1:

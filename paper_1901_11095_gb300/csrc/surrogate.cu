@@ -12,6 +12,9 @@
 // field stays inside the volume; the loss mask keeps a margin of at least one voxel per
 // layer from every face, so the gradient never reaches the boundary extension and the
 // result is exact.
+#include <string.h>
+
+#include <cuda.h>   // CUtensorMap and the tiled-map encoder's types (the encoder is found at run time)
 #include <cuda_bf16.h>
 
 #include "energy_tc.cuh"   // tcgen05 helpers: descriptors, bounded mbarrier wait, tensor-memory load
@@ -607,12 +610,16 @@ __global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16
 }
 
 // Layers on the tensor cores with one halo buffer per CTA and two CTAs per SM.  The halo keeps
-// only the three real channel groups per line (6240 bytes); the second k-step's upper group
-// then reads the next line's first group (or a zero pad after the last line), which meets the
-// zero weights of channels 24..31 and adds nothing.  CO = 24: hidden layer (bias, GELU, BF16
-// interleaved out, N = 32); CO = 3: output layer (N = 16, outputs 3..15 zero; bias and the RMS
-// scale applied, FP32 E written planar [3][voxel]).
-constexpr int TC1_LINE = 3 * TCH * 16;
+// only the three real channel groups per line, each group's 130 rows on a 128-byte boundary
+// (2176 bytes, as the tensor-memory-access unit requires of its destinations); the second
+// k-step's upper group then reads the next line's first group (or a zero pad after the last
+// line), which meets the zero weights of channels 24..31 and adds nothing.  Likewise the B
+// tiles of the hidden layer keep only their 24 real rows (768 bytes each): the 4th 8-row group
+// a product reads is the next tile's first, and lands in outputs 24..31, which are never used.
+// CO = 24: hidden layer (bias, GELU, BF16 interleaved out, N = 32); CO = 3: output layer
+// (N = 16, outputs 3..15 zero; bias and the RMS scale applied, FP32 E written planar).
+constexpr int TC1_GRP = 17 * 128;                           // bytes of one channel group of a line
+constexpr int TC1_LINE = 3 * TC1_GRP;
 constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
 
 __device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
@@ -625,9 +632,39 @@ __device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, 
         const int yy = r / 3, kc = r - yy * 3;
         const int64_t gt = ext_index(tl + line / 3 - 1, T, bnd), gx = ext_index(xl + line % 3 - 1, X, bnd);
         const int64_t gy = ext_index(y0 - 1 + yy, Y, bnd);
-        cp_async16(buf + line * TC1_LINE + kc * (TCH * 16) + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
+        cp_async16(buf + line * TC1_LINE + kc * TC1_GRP + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Whether the whole halo of line tile k lies inside the volume (no boundary extension needed).
+__device__ __forceinline__ bool tc1_interior(int64_t T, int64_t X, int64_t Y, int64_t k, int64_t ny)
+{
+    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+    const int64_t y0 = yb * TCY;
+    return y0 >= 1 && y0 + TCY + 1 <= Y && xl >= 1 && xl + 1 < X && tl >= 1 && tl + 1 < T;
+}
+
+// The halo of an interior line tile by the tensor-memory-access unit: 27 boxes of 130 rows x 8
+// channels (one per line and channel group), each landing as [y][8 channels] in its place;
+// completion is counted in bytes on the barrier.  Issued by one thread.
+__device__ __forceinline__ void tc1_stage_tma(const CUtensorMap *tmap, int64_t X, int64_t ny, int64_t k,
+                                              unsigned char *buf, uint32_t bar)
+{
+    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
+    const int y0 = (int)(yb * TCY) - 1;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9 * 3 * TCH * 16) : "memory");
+    const uint64_t tm = reinterpret_cast<uint64_t>(tmap);
+    for (int line = 0; line < 9; ++line) {
+        const int t = (int)tl + line / 3 - 1, x = (int)xl + line % 3 - 1;
+        for (int kc = 0; kc < 3; ++kc) {
+            const uint32_t dst = energy_detail::smem_u32(buf + line * TC1_LINE + kc * TC1_GRP);
+            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                         "%4, %5}], [%6];" ::"r"(dst),
+                         "l"(tm), "r"(kc * 8), "r"(y0), "r"(x), "r"(t), "r"(bar)
+                         : "memory");
+        }
+    }
 }
 
 template <int CO>
@@ -636,29 +673,38 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
                                                             const float *__restrict__ w, const float *__restrict__ b,
                                                             __nv_bfloat16 *__restrict__ out, float *__restrict__ E,
                                                             const float *__restrict__ out_scale_p, int *status,
-                                                            int stall, uint64_t limit_ns)
+                                                            int stall, uint64_t limit_ns,
+                                                            const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     constexpr int NB = CO > 16 ? 32 : 16;       // N of the products
-    constexpr int BT = NB * 32;                 // bytes of one B tile (NB x 16 BF16)
+    constexpr int BT = CO > 16 ? 768 : 512;     // bytes between B tiles (24 or 16 stored rows x 16 BF16)
+    constexpr int WB = 27 * 2 * BT + (CO > 16 ? 256 : 0);   // + the 4th group the last tile reads
+    static_assert(WB % 128 == 0, "halo on a 128-byte boundary");
     using energy_detail::smem_u32;
     extern __shared__ __align__(128) unsigned char tc_sm[];
-    unsigned char *sW = tc_sm, *sHb = tc_sm + 27 * 2 * BT;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sHb + TC1_HALO);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    unsigned char *sW = tc_sm, *sHb = tc_sm + WB;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sHb + TC1_HALO);   // [0]: products, [1]: halo copies
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
     __shared__ float sb[32];
 
-    for (int e = threadIdx.x; e < 27 * 2 * NB * 16; e += TC_NT) {
-        const int kk = e & 15, n = (e >> 4) % NB, ts = e / (16 * NB), tap = ts >> 1, ks = ts & 1;
+    constexpr int NS = BT / 32;                 // stored rows per B tile
+    for (int e = threadIdx.x; e < 27 * 2 * NS * 16; e += TC_NT) {
+        const int kk = e & 15, n = (e >> 4) % NS, ts = e / (16 * NS), tap = ts >> 1, ks = ts & 1;
         const int c = ks * 16 + kk;
         const float v = (n < CO && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
         *reinterpret_cast<__nv_bfloat16 *>(sW + ts * BT + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
             __float2bfloat16_rn(v);
     }
+    for (int e = threadIdx.x; e < (WB - 27 * 2 * BT) / 16; e += TC_NT)   // finite rows after the last tile
+        *reinterpret_cast<uint4 *>(sW + 27 * 2 * BT + e * 16) = make_uint4(0, 0, 0, 0);
     if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < CO ? b[threadIdx.x] : 0.f;
     for (int e = threadIdx.x; e < TCH; e += TC_NT)   // the pad read by the last line's upper group
         *reinterpret_cast<uint4 *>(sHb + 9 * TC1_LINE + e * 16) = make_uint4(0, 0, 0, 0);
+    // the tensor-memory-access unit writes only to 128-byte aligned destinations
+    if (smem_u32(sHb) & 127u) use_tma = 0;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) {
@@ -674,23 +720,43 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
 
     const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny, Nv = T * X * Y;
     constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, NB);
-    uint32_t phase = 0u;
-    bool ok = true;
-    if ((int64_t)blockIdx.x < ntiles) tc1_stage(in, T, X, Y, bnd, blockIdx.x, ny, sHb);
+    uint32_t phase = 0u, tphase = 0u;
+    bool ok = true, tma_pending = false;
+    // stages tile k by the tensor-memory-access unit when its halo is interior, else by copies
+    auto stage = [&](int64_t k) -> bool {
+        if (use_tma && tc1_interior(T, X, Y, k, ny)) {
+            if (threadIdx.x == 0) tc1_stage_tma(&tmap, X, ny, k, sHb, smem_u32(bar + 1));
+            return true;
+        }
+        tc1_stage(in, T, X, Y, bnd, k, ny, sHb);
+        return false;
+    };
+    bool cur_tma = false;
+    if ((int64_t)blockIdx.x < ntiles) cur_tma = stage(blockIdx.x);
+    tma_pending = cur_tma;
     for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (cur_tma) {
+            const bool in_ok = energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
+            if (__syncthreads_or(!in_ok)) {
+                ok = false;
+                break;
+            }
+            tphase ^= 1u;
+            tma_pending = false;
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
         if (threadIdx.x == 0 && !stall) {
-            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sHb), TCH * 16, 128);
+            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sHb), TC1_GRP, 128);
             const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
 #pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC1_LINE + (tap % 3) * 16 +
-                                           ks * 2 * (TCH * 16)) >> 4;
+                                           ks * 2 * TC1_GRP) >> 4;
                     const uint32_t boff = ((tap * 2 + ks) * BT) >> 4;
                     tc_mma_bf16(tmem, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
                 }
@@ -707,7 +773,10 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
         phase ^= 1u;
         // the halo is free: the next line's copies overlap this line's epilogue
         const int64_t kn = k + gridDim.x;
-        if (kn < ntiles) tc1_stage(in, T, X, Y, bnd, kn, ny, sHb);
+        if (kn < ntiles) {
+            cur_tma = stage(kn);
+            tma_pending = cur_tma;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (CO == kWidth) {
             tc_epilogue(tmem, 0, k, X, Y, ny, sb, out);
@@ -732,6 +801,8 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
         if (threadIdx.x == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
         if (!stall) energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
     }
+    // copies still in flight (a timeout after a prefetch) must land before the CTA exits
+    if (tma_pending) energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -739,7 +810,37 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
 }
 
 template <int CO>
-constexpr size_t tc1_smem() { return (size_t)27 * 2 * (CO > 16 ? 32 : 16) * 32 + TC1_HALO + 64; }
+constexpr size_t tc1_smem() { return (size_t)27 * 2 * (CO > 16 ? 768 : 512) + (CO > 16 ? 256 : 0) + TC1_HALO + 64; }
+
+// The activation tensor [T][X][Y][24] BF16 as a 4-D tiled map with boxes of 8 channels x 130
+// rows; false when the encoder is unavailable or refuses (then every halo is copied by cp.async).
+bool encode_act_map(const __nv_bfloat16 *act, sal_dims d, CUtensorMap *map)
+{
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+        looked = true;
+    }
+    if (!fn || d.T > 0x7fffffff || d.X > 0x7fffffff || d.Y > 0x7fffffff) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)kWidth, (cuuint64_t)d.Y, (cuuint64_t)d.X, (cuuint64_t)d.T};
+    const cuuint64_t row = (cuuint64_t)kWidth * sizeof(__nv_bfloat16);
+    const cuuint64_t strides[3] = {row, row * (cuuint64_t)d.Y, row * (cuuint64_t)d.Y * (cuuint64_t)d.X};
+    const cuuint32_t box[4] = {8, (cuuint32_t)TCH, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    memset(map, 0, sizeof(*map));
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)act, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // One layer on the tensor cores: CO = 24 (hidden) or 3 (output, writes E).
 template <int CO>
@@ -756,8 +857,10 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const f
     if (e != cudaSuccess) return e;
     int64_t grid = 2 * (int64_t)nsm;                 // two CTAs per SM (shared memory), persistent
     if (grid > ntiles) grid = ntiles;
+    CUtensorMap map;
+    const int use_tma = encode_act_map(in, d, &map) ? 1 : 0;
     conv_tc1_kernel<CO><<<(unsigned)grid, TC_NT, smem, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, E, out_scale, c.status,
-                                                           c.stall, c.limit_ns);
+                                                           c.stall, c.limit_ns, map, use_tma);
     return cudaGetLastError();
 }
 
