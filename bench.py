@@ -458,15 +458,17 @@ def run_surrogate(args) -> None:
 
 
 def run_surrogate_forward(args) -> None:
-    """The surrogate network alone (seeded initial weights, no training) on a 128 x 128 x 256
-    F3-kind volume: milliseconds per forward on the CUDA cores and with layers 2..5 on the
-    tensor cores.  A small, quick case for profiling the convolution kernels."""
+    """The surrogate network alone (seeded initial weights, no training) on an F3-kind volume of
+    --surrogate-shape (default 128 x 128 x 256, a small, quick case for profiling the
+    convolution kernels): milliseconds per forward on the CUDA cores and with layers 2..5 on
+    the tensor cores."""
     import torch
 
     from paper_1901_11095_gb300 import api, surrogate, synth
 
     dev = torch.device("cuda:0")
-    V = torch.from_numpy(synth.make_volume((128, 128, 256), seed=0, kind="f3")).to(dev)
+    shape = tuple(int(v) for v in args.surrogate_shape.lower().split("x"))
+    V = torch.from_numpy(synth.make_volume(shape, seed=0, kind="f3")).to(dev)
     model = surrogate.Surrogate(dev, seed=0)
     E = torch.empty((3,) + tuple(V.shape), device=dev, dtype=torch.float32)
     out = {"mode": "surrogate forward", "volume": list(V.shape), "steps": args.steps, "warmup": args.warmup}
@@ -594,6 +596,8 @@ def run_ours(args, rank: int, world: int) -> None:
     tile = api.sal_autotune_query(args.L, p.precision, N)     # the tile shape the launches used
     fpv = algorithmic_flops_per_voxel(args.L, BX=int(tile["bx"]))
     flops = fpv * N
+    n_mu = (args.L + 1) // 2
+    direct_fpv = 2 * (args.L ** 2 + 4 * n_mu * args.L ** 2 * (1 + args.L) + 5 * n_mu * args.L ** 2)
     achieved = flops / (k1_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
@@ -610,7 +614,12 @@ def run_ours(args, rank: int, world: int) -> None:
                      "traffic_source": traffic[1] if traffic else None,
                      "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
                                     f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
-                     "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]]},
+                     "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]],
+                     # the same time against the operation count of the unfolded separable DFT
+                     # (L^2 + 4 n_mu L^2 (1 + L) + 5 n_mu L^2 MACs per voxel): how far the folding
+                     # and the sliding recurrences moved the path past that method's ALU bound
+                     "direct_method_flops_per_voxel": direct_fpv,
+                     "direct_method_equivalent_tflops": direct_fpv * N / (k1_ms / 1e3) / 1e12},
         "kernels_ms": {"spectral_energy": k1_ms, "directional_compare_and_stats": statistics.mean(k2),
                        "combine": statistics.mean(k4)},
         "hbm_stages": {"directional_compare_GBs": k2_gbs, "combine_GBs": k4_gbs, "peak_GBs": hbm,
@@ -641,7 +650,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
     ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and time its inference")
     ap.add_argument("--surrogate-forward", action="store_true",
-                    help="time the surrogate network alone (seeded weights) on a 128x128x256 volume")
+                    help="time the surrogate network alone (seeded weights) on --surrogate-shape")
+    ap.add_argument("--surrogate-shape", default="128x128x256", help="T x X x Y of --surrogate-forward")
     ap.add_argument("--train-volumes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     args = ap.parse_args()

@@ -373,12 +373,14 @@ __device__ __forceinline__ bool energy_tile_tc(const float *__restrict__ V, int6
                     issue_mma<G>(tmem + (uint32_t)((pr - p0) * G::N), a_addr + pr * G::PAIR_BYTES, b_addr);
                 commit_mma(bar);
             }
-            const bool done = mbar_wait(bar, phase, ctl.limit_ns);
+            // one thread watches the barrier (bounded); the others sleep in the CTA barrier
+            // instead of taking issue slots from the co-resident CTA with polling
+            const bool done = threadIdx.x == 0 ? mbar_wait(bar, phase, ctl.limit_ns) : true;
             if (__syncthreads_or(!done)) {
                 ok = false;
                 // products that were issued may still be in flight: give them one more bounded
                 // wait before the caller releases the tensor memory
-                if (!ctl.stall) mbar_wait(bar, phase, ctl.limit_ns);
+                if (!ctl.stall && threadIdx.x == 0) mbar_wait(bar, phase, ctl.limit_ns);
                 break;
             }
             phase ^= 1u;

@@ -414,45 +414,66 @@ cudaError_t launch_wgrad(const float *a, const float *a_scale, const float *g, s
     return cudaGetLastError();
 }
 
-// ---- hidden 24 -> 24 layers on the tensor cores (inference) --------------------------------
+// ---- layers 2..5 on the tensor cores (inference) ------------------------------------------
 // Implicit GEMM per tap: for an output line (t, x, y0 .. y0 + 127),
 //     D[y][o] += sum_c A_tap[y][c] W[o][c][tap],  A_tap[y][c] = act[t + dt][x + dx][y + dy][c],
-// 27 taps x 2 products of K = 16 (channels 0..15, 16..31 with 24..31 zero), M = 128, N = 32
-// (outputs 24..31 zero), BF16 operands, FP32 accumulation in tensor memory.  The halo of the
-// line (3 x 3 lines x 130 rows x 32 channels) sits in shared memory as [line][channel group
-// of 8][y][8 channels], i.e. K-major core matrices of 8 rows x 16 bytes with the 8-row groups
-// 128 bytes apart and the channel groups 130 x 16 bytes apart: the operand of every tap is
-// the same buffer at another start address, so no operand is rebuilt per tap.  Two halo
-// buffers and two accumulators let the next line's copies and the previous line's epilogue
-// (bias, GELU, BF16, store) run while a line's products execute.  Activations interleaved
-// [voxel][24] BF16.  Every wait is bounded; on expiry the status word gets SAL_ERR_TIMEOUT.
+// 27 taps x 2 products of K = 16 (channels 0..15 and 16..31, 24..31 meeting zero weights),
+// M = 128, BF16 operands, FP32 accumulation in tensor memory.  CO = 24: hidden layer (N = 32,
+// bias, GELU, BF16 interleaved out); CO = 3: output layer (N = 16, outputs 3..15 zero; bias and
+// the RMS scale applied, FP32 E written planar [3][voxel]).  Activations interleaved [voxel][24].
+//
+// The 3 x 3 halo lines of a tile sit in shared memory as [line][channel group of 8][y][8
+// channels]: K-major core matrices of 8 rows x 16 bytes, 8-row groups 128 bytes apart, channel
+// groups 2176 bytes apart (130 rows on a 128-byte boundary, as the tensor-memory-access unit
+// requires of its destinations).  The operand of every tap is the same buffer at a byte offset
+// added to the descriptor's start address, so no operand is rebuilt per tap.  Only the three
+// real channel groups are kept: the second k-step's upper group reads the next line's first
+// group (or a zero pad after the last line), which meets the zero weights of channels 24..31.
+// Likewise the hidden layer's B tiles keep their 24 real rows (768 bytes each): the 4th 8-row
+// group a product reads is the next tile's first and lands in outputs 24..31, never used.
+// One halo and one accumulator per CTA, two CTAs per SM, persistent over the line tiles; the
+// next tile's halo is loaded while this tile's epilogue runs: interior tiles by 27
+// tensor-memory-access boxes (130 rows x 8 channels) counted in bytes on an mbarrier, tiles at
+// a face of the volume by 16-byte cp.async copies with the boundary extension.  Every wait is
+// bounded; on expiry the status word gets SAL_ERR_TIMEOUT.
 constexpr int TCY = 128, TCH = TCY + 2;                     // outputs per line tile, halo rows
-constexpr int TC_LINE = 4 * TCH * 16;                       // bytes of one halo line
-constexpr int TC_HALO = 9 * TC_LINE;                        // bytes of one halo buffer
-constexpr int TC_WB = 27 * 2 * 1024;                        // B operands [tap][k-step][32 x 16 BF16]
 constexpr int TC_NT = 256;
-constexpr size_t TC_SMEM = (size_t)TC_WB + 2 * TC_HALO + 64;
+constexpr int TC1_GRP = 17 * 128;                           // bytes of one channel group of a line
+constexpr int TC1_LINE = 3 * TC1_GRP;
+constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
+
+// A line tile: its first output plane t, row x and first column y0 (32-bit: the launcher
+// checks that T, X, Y and the tile count fit).
+struct TileC {
+    int t, x, y0;
+};
+
+__device__ __forceinline__ TileC tile_coords(long long k, int X, int ny)
+{
+    const unsigned kk = (unsigned)k, r = kk / (unsigned)ny;
+    return TileC{(int)(r / (unsigned)X), (int)(r % (unsigned)X), (int)(kk - r * (unsigned)ny) * TCY};
+}
+
+// Boundary extension of one coordinate in 32 bits (one reflection or wrap; wider cases take
+// the general routine).
+__device__ __forceinline__ int ext32(int i, int n, int bnd)
+{
+    if (i >= 0 && i < n) return i;
+    if (bnd == SAL_BND_PERIODIC) {
+        if (i < 0 && i >= -n) return i + n;
+        if (i >= n && i < 2 * n) return i - n;
+    } else {
+        if (n == 1) return 0;
+        if (i < 0 && i > -n) return -i;
+        if (i >= n && i <= 2 * n - 2) return 2 * (n - 1) - i;
+    }
+    return (int)ext_index(i, n, bnd);
+}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-
-// Copies the halo of line tile k (t, x, y0) into buf (channel groups 0..2; group 3 stays zero).
-__device__ __forceinline__ void tc_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
-                                         int bnd, int64_t k, int64_t ny, unsigned char *buf)
-{
-    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-    const int64_t y0 = yb * TCY;
-    for (int e = threadIdx.x; e < 9 * TCH * 3; e += TC_NT) {
-        const int line = e / (TCH * 3), r = e - line * (TCH * 3);
-        const int yy = r / 3, kc = r - yy * 3;
-        const int64_t gt = ext_index(tl + line / 3 - 1, T, bnd), gx = ext_index(xl + line % 3 - 1, X, bnd);
-        const int64_t gy = ext_index(y0 - 1 + yy, Y, bnd);
-        cp_async16(buf + line * TC_LINE + kc * (TCH * 16) + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -462,216 +483,82 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t a, uint64_t 
                  "r"(idesc), "r"(acc));
 }
 
-// Bias, GELU, BF16 and store of one line tile's accumulator (tensor-memory columns col0..+31).
-__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int col0, int64_t k, int64_t X, int64_t Y, int64_t ny,
-                                            const float *sb, __nv_bfloat16 *__restrict__ out)
+// The halo of tile c by 16-byte copies with the boundary extension (group 3 is never written).
+// Line by line: the extension of t and x is taken once per line, consecutive threads copy
+// consecutive 16-byte pieces of consecutive rows, and rows need the extension only at a face.
+__device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int T, int X, int Y, int bnd, TileC c,
+                                          unsigned char *buf)
 {
-    const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
-    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-    float v[16];
-    energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(col0 + 16 * h), v);
-    const int64_t y = yb * TCY + 32 * q + (threadIdx.x & 31);
-    if (y >= Y) return;
-    __nv_bfloat16 *o = out + ((tl * X + xl) * Y + y) * kWidth + 16 * h;
-    const int nc = h == 0 ? 16 : kWidth - 16;
-    uint32_t pk[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float a = gelu(v[2 * j] + sb[16 * h + 2 * j]);
-        const float b = gelu(v[2 * j + 1] + sb[16 * h + 2 * j + 1]);
-        const __nv_bfloat162 p2 = __floats2bfloat162_rn(a, b);
-        pk[j] = *reinterpret_cast<const uint32_t *>(&p2);
-    }
-    *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    if (nc == 16) *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-}
-
-__global__ void __launch_bounds__(TC_NT, 1) conv24_tc_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
-                                                             int64_t X, int64_t Y, int bnd,
-                                                             const float *__restrict__ w, const float *__restrict__ b,
-                                                             __nv_bfloat16 *__restrict__ out, int *status, int stall,
-                                                             uint64_t limit_ns)
-{
-    using energy_detail::smem_u32;
-    extern __shared__ __align__(128) unsigned char tc_sm[];
-    unsigned char *sW = tc_sm;
-    auto sH = [&](int bi) { return tc_sm + TC_WB + bi * TC_HALO; };
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tc_sm + TC_WB + 2 * TC_HALO);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-    __shared__ float sb[32];
-
-    // B operands: element (o, c) of tap / k-step at core-matrix offset, BF16-rounded weights
-    for (int e = threadIdx.x; e < 27 * 2 * 32 * 16; e += TC_NT) {
-        const int kk = e & 15, n = (e >> 4) & 31, ts = e >> 9, tap = ts >> 1, ks = ts & 1;
-        const int c = ks * 16 + kk;
-        const float v = (n < kWidth && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
-        *reinterpret_cast<__nv_bfloat16 *>(sW + ts * 1024 + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
-            __float2bfloat16_rn(v);
-    }
-    if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < kWidth ? b[threadIdx.x] : 0.f;
-    // channel group 3 (channels 24..31) of both halo buffers is zero for good
-    for (int e = threadIdx.x; e < 2 * 9 * TCH; e += TC_NT) {
-        const int bi = e / (9 * TCH), r = e - bi * 9 * TCH, line = r / TCH, yy = r - line * TCH;
-        *reinterpret_cast<uint4 *>(sH(bi) + line * TC_LINE + 3 * (TCH * 16) + yy * 16) = make_uint4(0, 0, 0, 0);
-    }
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot)) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-
-    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny;
-    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, 32);
-    uint32_t phases = 0u;   // bit b: parity of the next completion of barrier b
-    bool ok = true;
-    int64_t prev = -1;
-    const int64_t k0 = blockIdx.x;
-    if (k0 < ntiles) tc_stage(in, T, X, Y, bnd, k0, ny, sH(0));
-    int i = 0;
-    for (int64_t k = k0; k < ntiles && ok; k += gridDim.x, ++i) {
-        const int bi = i & 1;
-        // this line's halo is in: make the copies visible to the tensor cores
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0 && !stall) {
-            // one descriptor per operand; every tap and k-step is a compile-time byte offset
-            // added to its 14-bit start-address field (no carry: shared memory < 256 KB)
-            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sH(bi)), TCH * 16, 128);
-            const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
-            const uint32_t dtm = tmem + 32 * bi;
-#pragma unroll
-            for (int tap = 0; tap < 27; ++tap) {
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC_LINE + (tap % 3) * 16 +
-                                           ks * 2 * (TCH * 16)) >> 4;
-                    const uint32_t boff = ((tap * 2 + ks) * 1024) >> 4;
-                    tc_mma_bf16(dtm, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bars[bi]))
-                         : "memory");
+    const bool yin = c.y0 >= 1 && c.y0 - 1 + TCH <= Y;
+#pragma unroll 1
+    for (int line = 0; line < 9; ++line) {
+        const int gt = ext32(c.t + line / 3 - 1, T, bnd), gx = ext32(c.x + line % 3 - 1, X, bnd);
+        const __nv_bfloat16 *src = in + ((int64_t)gt * X + gx) * Y * kWidth;
+        unsigned char *dst = buf + line * TC1_LINE;
+        for (int e = threadIdx.x; e < TCH * 3; e += TC_NT) {
+            const int yy = e / 3, kc = e - yy * 3;
+            const int gy = yin ? c.y0 - 1 + yy : ext32(c.y0 - 1 + yy, Y, bnd);
+            cp_async16(dst + kc * TC1_GRP + yy * 16, src + gy * kWidth + kc * 8);
         }
-        // the previous line: its products must be done before its halo buffer is refilled
-        // and its accumulator read
-        if (prev >= 0) {
-            const bool done = energy_detail::mbar_wait(smem_u32(&bars[bi ^ 1]), (phases >> (bi ^ 1)) & 1u, limit_ns);
-            if (__syncthreads_or(!done)) {
-                ok = false;
-                break;
-            }
-            phases ^= 1u << (bi ^ 1);
-        }
-        const int64_t kn = k + gridDim.x;
-        if (kn < ntiles) tc_stage(in, T, X, Y, bnd, kn, ny, sH(bi ^ 1));
-        if (prev >= 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            tc_epilogue(tmem, 32 * (bi ^ 1), prev, X, Y, ny, sb, out);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        prev = k;
-    }
-    if (ok && prev >= 0) {
-        const int bi = (i - 1) & 1;
-        const bool done = energy_detail::mbar_wait(smem_u32(&bars[bi]), (phases >> bi) & 1u, limit_ns);
-        if (__syncthreads_or(!done)) {
-            ok = false;
-        } else {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            tc_epilogue(tmem, 32 * bi, prev, X, Y, ny, sb, out);
-        }
-    }
-    if (!ok) {
-        if (threadIdx.x == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
-        // products that were issued may still be in flight: one more bounded wait on each
-        // barrier before the tensor memory is released
-        if (!stall) {
-            energy_detail::mbar_wait(smem_u32(&bars[0]), phases & 1u, limit_ns);
-            energy_detail::mbar_wait(smem_u32(&bars[1]), (phases >> 1) & 1u, limit_ns);
-        }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
-}
-
-// Layers on the tensor cores with one halo buffer per CTA and two CTAs per SM.  The halo keeps
-// only the three real channel groups per line, each group's 130 rows on a 128-byte boundary
-// (2176 bytes, as the tensor-memory-access unit requires of its destinations); the second
-// k-step's upper group then reads the next line's first group (or a zero pad after the last
-// line), which meets the zero weights of channels 24..31 and adds nothing.  Likewise the B
-// tiles of the hidden layer keep only their 24 real rows (768 bytes each): the 4th 8-row group
-// a product reads is the next tile's first, and lands in outputs 24..31, which are never used.
-// CO = 24: hidden layer (bias, GELU, BF16 interleaved out, N = 32); CO = 3: output layer
-// (N = 16, outputs 3..15 zero; bias and the RMS scale applied, FP32 E written planar).
-constexpr int TC1_GRP = 17 * 128;                           // bytes of one channel group of a line
-constexpr int TC1_LINE = 3 * TC1_GRP;
-constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
-
-__device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int64_t T, int64_t X, int64_t Y,
-                                          int bnd, int64_t k, int64_t ny, unsigned char *buf)
-{
-    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-    const int64_t y0 = yb * TCY;
-    for (int e = threadIdx.x; e < 9 * TCH * 3; e += TC_NT) {
-        const int line = e / (TCH * 3), r = e - line * (TCH * 3);
-        const int yy = r / 3, kc = r - yy * 3;
-        const int64_t gt = ext_index(tl + line / 3 - 1, T, bnd), gx = ext_index(xl + line % 3 - 1, X, bnd);
-        const int64_t gy = ext_index(y0 - 1 + yy, Y, bnd);
-        cp_async16(buf + line * TC1_LINE + kc * TC1_GRP + yy * 16, in + ((gt * X + gx) * Y + gy) * kWidth + kc * 8);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Whether the whole halo of line tile k lies inside the volume (no boundary extension needed).
-__device__ __forceinline__ bool tc1_interior(int64_t T, int64_t X, int64_t Y, int64_t k, int64_t ny)
+// Whether the whole halo of tile c lies inside the volume (no boundary extension needed).
+__device__ __forceinline__ bool tc1_interior(int T, int X, int Y, TileC c)
 {
-    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-    const int64_t y0 = yb * TCY;
-    return y0 >= 1 && y0 + TCY + 1 <= Y && xl >= 1 && xl + 1 < X && tl >= 1 && tl + 1 < T;
+    return c.y0 >= 1 && c.y0 + TCY + 1 <= Y && c.x >= 1 && c.x + 1 < X && c.t >= 1 && c.t + 1 < T;
 }
 
-// The halo of an interior line tile by the tensor-memory-access unit: 27 boxes of 130 rows x 8
+// The halo of an interior tile by the tensor-memory-access unit: 27 boxes of 130 rows x 8
 // channels (one per line and channel group), each landing as [y][8 channels] in its place;
 // completion is counted in bytes on the barrier.  Issued by one thread.
-__device__ __forceinline__ void tc1_stage_tma(const CUtensorMap *tmap, int64_t X, int64_t ny, int64_t k,
-                                              unsigned char *buf, uint32_t bar)
+__device__ __forceinline__ void tc1_stage_tma(const CUtensorMap *tmap, TileC c, unsigned char *buf, uint32_t bar)
 {
-    const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-    const int y0 = (int)(yb * TCY) - 1;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9 * 3 * TCH * 16) : "memory");
     const uint64_t tm = reinterpret_cast<uint64_t>(tmap);
     for (int line = 0; line < 9; ++line) {
-        const int t = (int)tl + line / 3 - 1, x = (int)xl + line % 3 - 1;
+        const int t = c.t + line / 3 - 1, x = c.x + line % 3 - 1;
         for (int kc = 0; kc < 3; ++kc) {
             const uint32_t dst = energy_detail::smem_u32(buf + line * TC1_LINE + kc * TC1_GRP);
             asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
                          "%4, %5}], [%6];" ::"r"(dst),
-                         "l"(tm), "r"(kc * 8), "r"(y0), "r"(x), "r"(t), "r"(bar)
+                         "l"(tm), "r"(kc * 8), "r"(c.y0 - 1), "r"(x), "r"(t), "r"(bar)
                          : "memory");
         }
     }
 }
 
+// Bias, GELU, BF16 and store of the hidden layer's accumulator: warp w reads lane quadrant
+// w % 4 (rows = y) and column half w / 4 (channels 0..15 or 16..23).
+__device__ __forceinline__ void tc_epilogue_hidden(uint32_t tmem, TileC c, int X, int Y, const float *sb,
+                                                   __nv_bfloat16 *__restrict__ out)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
+    float v[16];
+    energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h), v);
+    const int y = c.y0 + 32 * q + (threadIdx.x & 31);
+    if (y >= Y) return;
+    __nv_bfloat16 *o = out + (((int64_t)c.t * X + c.x) * Y + y) * kWidth + 16 * h;
+    uint32_t pk[8];
+    const int npairs = h == 0 ? 8 : (kWidth - 16) / 2;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j >= npairs) break;
+        const float a = gelu(v[2 * j] + sb[16 * h + 2 * j]);
+        const float bb = gelu(v[2 * j + 1] + sb[16 * h + 2 * j + 1]);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(a, bb);
+        pk[j] = *reinterpret_cast<const uint32_t *>(&p2);
+    }
+    *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    if (h == 0) *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
 template <int CO>
-__global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int64_t T,
-                                                            int64_t X, int64_t Y, int bnd,
-                                                            const float *__restrict__ w, const float *__restrict__ b,
-                                                            __nv_bfloat16 *__restrict__ out, float *__restrict__ E,
+__global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int T, int X,
+                                                            int Y, int bnd, const float *__restrict__ w,
+                                                            const float *__restrict__ b, __nv_bfloat16 *__restrict__ out,
+                                                            float *__restrict__ E,
                                                             const float *__restrict__ out_scale_p, int *status,
                                                             int stall, uint64_t limit_ns,
                                                             const __grid_constant__ CUtensorMap tmap, int use_tma)
@@ -690,8 +577,8 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
     constexpr int NS = BT / 32;                 // stored rows per B tile
     for (int e = threadIdx.x; e < 27 * 2 * NS * 16; e += TC_NT) {
         const int kk = e & 15, n = (e >> 4) % NS, ts = e / (16 * NS), tap = ts >> 1, ks = ts & 1;
-        const int c = ks * 16 + kk;
-        const float v = (n < CO && c < kWidth) ? w[((int64_t)n * kWidth + c) * 27 + tap] : 0.f;
+        const int cin = ks * 16 + kk;
+        const float v = (n < CO && cin < kWidth) ? w[((int64_t)n * kWidth + cin) * 27 + tap] : 0.f;
         *reinterpret_cast<__nv_bfloat16 *>(sW + ts * BT + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
             __float2bfloat16_rn(v);
     }
@@ -718,25 +605,32 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
     const uint32_t tmem = *tslot;
     const float out_scale = out_scale_p ? *out_scale_p : 1.f;
 
-    const int64_t ny = (Y + TCY - 1) / TCY, ntiles = T * X * ny, Nv = T * X * Y;
+    const int ny = (Y + TCY - 1) / TCY;
+    const long long ntiles = (long long)T * X * ny, Nv = (long long)T * X * Y;
     constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, NB);
     uint32_t phase = 0u, tphase = 0u;
     bool ok = true, tma_pending = false;
-    // stages tile k by the tensor-memory-access unit when its halo is interior, else by copies
-    auto stage = [&](int64_t k) -> bool {
-        if (use_tma && tc1_interior(T, X, Y, k, ny)) {
-            if (threadIdx.x == 0) tc1_stage_tma(&tmap, X, ny, k, sHb, smem_u32(bar + 1));
+    // stages tile c by the tensor-memory-access unit when its halo is interior, else by copies
+    auto stage = [&](TileC c) -> bool {
+        if (use_tma && tc1_interior(T, X, Y, c)) {
+            if (threadIdx.x == 0) tc1_stage_tma(&tmap, c, sHb, smem_u32(bar + 1));
             return true;
         }
-        tc1_stage(in, T, X, Y, bnd, k, ny, sHb);
+        tc1_stage(in, T, X, Y, bnd, c, sHb);
         return false;
     };
+    TileC cur{0, 0, 0};
     bool cur_tma = false;
-    if ((int64_t)blockIdx.x < ntiles) cur_tma = stage(blockIdx.x);
+    if ((long long)blockIdx.x < ntiles) {
+        cur = tile_coords(blockIdx.x, X, ny);
+        cur_tma = stage(cur);
+    }
     tma_pending = cur_tma;
-    for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    for (long long k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        // one thread watches each barrier (bounded) and the CTA follows it through a barrier:
+        // the other warps sleep in the barrier instead of taking issue slots with polling
         if (cur_tma) {
-            const bool in_ok = energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
+            const bool in_ok = threadIdx.x == 0 ? energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns) : true;
             if (__syncthreads_or(!in_ok)) {
                 ok = false;
                 break;
@@ -748,6 +642,7 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
         }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (threadIdx.x == 0 && !stall) {
             const uint64_t a0 = energy_detail::smem_desc(smem_u32(sHb), TC1_GRP, 128);
             const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
@@ -765,44 +660,45 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
                              smem_u32(bar))
                          : "memory");
         }
-        const bool done = energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
+        const bool done = threadIdx.x == 0 ? energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns) : true;
         if (__syncthreads_or(!done)) {
             ok = false;
             break;
         }
         phase ^= 1u;
-        // the halo is free: the next line's copies overlap this line's epilogue
-        const int64_t kn = k + gridDim.x;
+        // the halo is free: the next tile's copies overlap this tile's epilogue
+        const TileC done_c = cur;
+        const long long kn = k + gridDim.x;
         if (kn < ntiles) {
-            cur_tma = stage(kn);
+            cur = tile_coords(kn, X, ny);
+            cur_tma = stage(cur);
             tma_pending = cur_tma;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (CO == kWidth) {
-            tc_epilogue(tmem, 0, k, X, Y, ny, sb, out);
+            tc_epilogue_hidden(tmem, done_c, X, Y, sb, out);
         } else {
             const int warp = threadIdx.x >> 5, q = warp & 3;
             if (warp < 4) {   // N = 16: one load per lane quadrant
                 float v[16];
                 energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16), v);
-                const int64_t yb = k % ny, xl = (k / ny) % X, tl = k / (ny * X);
-                const int64_t y = yb * TCY + 32 * q + (threadIdx.x & 31);
+                const int y = done_c.y0 + 32 * q + (threadIdx.x & 31);
                 if (y < Y) {
-                    const int64_t vox = (tl * X + xl) * Y + y;
+                    const long long vox = ((long long)done_c.t * X + done_c.x) * Y + y;
 #pragma unroll
-                    for (int c = 0; c < CO; ++c) E[c * Nv + vox] = (v[c] + sb[c]) * out_scale;
+                    for (int ch = 0; ch < CO; ++ch) E[ch * Nv + vox] = (v[ch] + sb[ch]) * out_scale;
                 }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    if (!ok) {
-        if (threadIdx.x == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
+    if (!ok && threadIdx.x == 0) {
+        atomicExch(status, (int)SAL_ERR_TIMEOUT);
         if (!stall) energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
     }
     // copies still in flight (a timeout after a prefetch) must land before the CTA exits
-    if (tma_pending) energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
+    if (tma_pending && threadIdx.x == 0) energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -830,7 +726,7 @@ bool encode_act_map(const __nv_bfloat16 *act, sal_dims d, CUtensorMap *map)
             fn = (EncodeFn)p;
         looked = true;
     }
-    if (!fn || d.T > 0x7fffffff || d.X > 0x7fffffff || d.Y > 0x7fffffff) return false;
+    if (!fn) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)kWidth, (cuuint64_t)d.Y, (cuuint64_t)d.X, (cuuint64_t)d.T};
     const cuuint64_t row = (cuuint64_t)kWidth * sizeof(__nv_bfloat16);
     const cuuint64_t strides[3] = {row, row * (cuuint64_t)d.Y, row * (cuuint64_t)d.Y * (cuuint64_t)d.X};
@@ -849,6 +745,8 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const f
 {
     const int64_t ny = (d.Y + TCY - 1) / TCY, ntiles = d.T * d.X * ny;
     if (ntiles <= 0) return cudaSuccess;
+    // tile coordinates and indices travel in 32 bits
+    if (d.T > 0x7fffffff || d.X > 0x7fffffff || d.Y > 0x7fffffff || ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -859,27 +757,8 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const f
     if (grid > ntiles) grid = ntiles;
     CUtensorMap map;
     const int use_tma = encode_act_map(in, d, &map) ? 1 : 0;
-    conv_tc1_kernel<CO><<<(unsigned)grid, TC_NT, smem, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, E, out_scale, c.status,
-                                                           c.stall, c.limit_ns, map, use_tma);
-    return cudaGetLastError();
-}
-
-constexpr bool kTcOneBuffer = true;   // two CTAs per SM with one halo each (else one CTA, two halos)
-
-cudaError_t launch_conv24_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const float *w, const float *b,
-                             __nv_bfloat16 *out, const TcControl &c, cudaStream_t s)
-{
-    const int64_t ny = (d.Y + TCY - 1) / TCY, ntiles = d.T * d.X * ny;
-    if (ntiles <= 0) return cudaSuccess;
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (kTcOneBuffer) return launch_conv_tc<kWidth>(in, d, bnd, w, b, out, nullptr, nullptr, c, s);
-    cudaError_t e = set_smem(conv24_tc_kernel, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = ntiles < nsm ? ntiles : nsm;   // one CTA per SM (shared memory), persistent
-    conv24_tc_kernel<<<(unsigned)grid, TC_NT, TC_SMEM, s>>>(in, d.T, d.X, d.Y, bnd, w, b, out, c.status, c.stall,
-                                                            c.limit_ns);
+    conv_tc1_kernel<CO><<<(unsigned)grid, TC_NT, smem, s>>>(in, (int)d.T, (int)d.X, (int)d.Y, bnd, w, b, out, E,
+                                                           out_scale, c.status, c.stall, c.limit_ns, map, use_tma);
     return cudaGetLastError();
 }
 
@@ -959,9 +838,9 @@ cudaError_t surrogate_forward(const float *V, sal_dims d, int bnd, const float *
         if (!tc || !tc->status) return cudaErrorInvalidValue;
         __nv_bfloat16 *a0 = (__nv_bfloat16 *)w.data, *a1 = a0 + (int64_t)kWidth * N;
         SAL_TRY((launch_conv<1, kWidth, float, __nv_bfloat16, FWD_HIDDEN, true>(V, d, bnd, w.scale, Wp(P, 0), Bp(P, 0), nullptr, a0, nullptr, nullptr, s)));
-        SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 1), Bp(P, 1), a1, *tc, s));
-        SAL_TRY(launch_conv24_tc(a1, d, bnd, Wp(P, 2), Bp(P, 2), a0, *tc, s));
-        SAL_TRY(launch_conv24_tc(a0, d, bnd, Wp(P, 3), Bp(P, 3), a1, *tc, s));
+        SAL_TRY(launch_conv_tc<kWidth>(a0, d, bnd, Wp(P, 1), Bp(P, 1), a1, nullptr, nullptr, *tc, s));
+        SAL_TRY(launch_conv_tc<kWidth>(a1, d, bnd, Wp(P, 2), Bp(P, 2), a0, nullptr, nullptr, *tc, s));
+        SAL_TRY(launch_conv_tc<kWidth>(a0, d, bnd, Wp(P, 3), Bp(P, 3), a1, nullptr, nullptr, *tc, s));
         SAL_TRY(launch_conv_tc<3>(a1, d, bnd, Wp(P, 4), Bp(P, 4), nullptr, E, w.scale + 1, *tc, s));
         return cudaSuccess;
     }
