@@ -128,6 +128,32 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
     }
     const int64_t gt = t0 + t, gx = x0 + x;
     if (gt >= T || gx >= X) return;
+    if constexpr (MODE == FWD_HIDDEN && ILV && sizeof(TOUT) == 2 && CO % 8 == 0) {
+        // interleaved BF16 activations: the thread's two voxels are adjacent along y, so their
+        // 2 x CO channels are one contiguous run written as 16-byte vectors (the warp's 32
+        // voxels form one contiguous span)
+        if (!zout) {
+            const int64_t gy = y0 + 2 * yp;
+            if (gy >= Y) return;
+            const int nr = gy + 1 < Y ? 2 : 1;
+            uint4 *dst = reinterpret_cast<uint4 *>(out + ((gt * X + gx) * Y + gy) * CO);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (r >= nr) break;
+#pragma unroll
+                for (int g = 0; g < CO / 8; ++g) {
+                    uint32_t p[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(gelu(acc[8 * g + 2 * j][r]), gelu(acc[8 * g + 2 * j + 1][r]));
+                        memcpy(&p[j], &h, 4);
+                    }
+                    dst[r * (CO / 8) + g] = make_uint4(p[0], p[1], p[2], p[3]);
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int64_t gy = y0 + 2 * yp + r;
