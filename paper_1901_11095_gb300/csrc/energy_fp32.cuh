@@ -612,22 +612,47 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
     }
 }
 
+// Asynchronous 4-byte copy global -> shared (completion by cp.async.wait_*).
+__device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
 // Halo tile of V in shared memory; outside the volume the boundary extension supplies the
 // samples.  G provides BT, BX, BY, H, HX, PY, NV and NT.
 template <class G>
 __device__ __forceinline__ void stage_v(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
                                         int64_t t0, int64_t x0, int64_t y0, float *sV)
 {
-    constexpr int H = G::H, PY = G::PY;
+    constexpr int H = G::H, PY = G::PY, HX = G::HX;
     const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
-                        y0 + G::BY + H <= Y;
+                        y0 + G::BY + H <= Y && (int64_t)(G::BT + 2 * H) * X * Y < 0x7fffffffLL;
     if (inside) {
+        // asynchronous 4-byte copies (no register round trip); the element offsets in the
+        // volume fit in 32 bits and advance by NT elements of the [plane][row][column] halo
+        // at a time, each step NT / PY rows and NT % PY columns further
+        constexpr int DRS = G::NT / PY, DYS = G::NT - DRS * PY;
+        static_assert(DRS + 1 < HX, "one step crosses at most one plane");
         const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
+        const int Yi = (int)Y, XYi = (int)(X * Y);
+        int yy = threadIdx.x % PY, r = threadIdx.x / PY;
+        int xx = r % HX, a = r / HX;
         for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            const int r = i / PY, yy = i - r * PY;
-            const int a = r / G::HX, xx = r - a * G::HX;
-            sV[i] = __ldg(src + ((int64_t)a * X + xx) * Y + yy);
+            cp_async_f32(sV + i, src + (a * XYi + xx * Yi + yy));
+            yy += DYS;
+            int dr = DRS;
+            if (yy >= PY) {
+                yy -= PY;
+                ++dr;
+            }
+            xx += dr;
+            if (xx >= HX) {
+                xx -= HX;
+                ++a;
+            }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
         for (int i = threadIdx.x; i < G::NV; i += G::NT) {
             const int r = i / PY, yy = i - r * PY;
@@ -967,11 +992,6 @@ __device__ __forceinline__ void energy_tile_any(const float *__restrict__ V, int
 }
 
 // ---- mode 3: the next tile's V halo in flight while the current tile finishes -----------
-__device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
 
 // Issues the asynchronous copies of one tile's V halo into sV (same layout as stage_v) and
 // commits them as one group.
