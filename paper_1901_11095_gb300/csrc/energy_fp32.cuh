@@ -229,9 +229,11 @@ __device__ __forceinline__ float cabs2(f2x v)
 // direct DFT; the others by a sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w)
 // (|Q_r| = |F_r|): Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the
 // twiddles of a whole period are equal; Q_0 = F_0 needs no rotation.
-template <int L, int R, int NZ>
+template <int L, int R, int NZ, bool ADD = false>
 __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
 {
+    // ADD: the magnitudes are added to m (the -nu line of a pair onto the +nu line's)
+    auto put = [&](float &dst, float v) { dst = ADD ? dst + v : v; };
     constexpr int H = (L - 1) / 2;
     const f2x z0 = Z[H];
     const f2x m2 = pk(-2.f, -2.f);
@@ -246,7 +248,7 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
     }
     f2x P[L];          // P[H + w] for w = -H..H
     P[H] = s;
-    m[0][0] = sqrt_approx(cabs2(s));
+    put(m[0][0], sqrt_approx(cabs2(s)));
 #pragma unroll
     for (int w = 1; w <= H; ++w) {
         f2x A = mul2(U[1], tw.c2[w % L]);
@@ -259,7 +261,7 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
         const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
         const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
         const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
-        m[0][w] = sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm));
+        put(m[0][w], sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm)));
         P[H + w] = Fp;
         P[H - w] = Fm;
     }
@@ -273,9 +275,9 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
             P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, tw_index<L>(w, r - H));
             P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, tw_index<L>(-w, r - H));
         }
-        m[r + 1][0] = sqrt_approx(cabs2(P[H]));
+        put(m[r + 1][0], sqrt_approx(cabs2(P[H])));
 #pragma unroll
-        for (int w = 1; w <= H; ++w) m[r + 1][w] = sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w]));
+        for (int w = 1; w <= H; ++w) put(m[r + 1][w], sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w])));
     }
 }
 
@@ -393,7 +395,7 @@ __device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j
 {
     float w[G::H + 1][3];
     load_w<G>(sW, mu, nu, w);
-    float mp[G::R][G::H + 1], mm[G::R][G::H + 1];
+    float mp[G::R][G::H + 1];   // |F(+nu)| + |F(-nu)| per output and |omega|
     {
         f2x Z[G::NZ];
         load_line<G>(lp, j, Z);
@@ -402,14 +404,10 @@ __device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j
     {
         f2x Z[G::NZ];
         load_line<G>(lm, j, Z);
-        line_mags_strip<G::L, G::R>(Z, tw, mm);
+        line_mags_strip<G::L, G::R, G::NZ, true>(Z, tw, mp);
     }
 #pragma unroll
-    for (int r = 0; r < G::R; ++r) {
-#pragma unroll
-        for (int om = 0; om <= G::H; ++om) mp[r][om] += mm[r][om];
-        accum<G>(mp[r], w, 0, et[r], ex[r], ey[r]);
-    }
+    for (int r = 0; r < G::R; ++r) accum<G>(mp[r], w, 0, et[r], ex[r], ey[r]);
 }
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
@@ -671,12 +669,14 @@ template <class G>
 __device__ __forceinline__ void t_stage(const float *sV, float *sG1, const Tw<G::L> &tw)
 {
     constexpr int L = G::L, H = G::H, PY = G::PY;
+    // item i = (row r = (t, x'), column y') of the output planes; its samples along t are
+    // the halo elements i + k HX PY.  (r, y') advance by NT items at a time.
+    constexpr int DRS = G::NT / PY, DYS = G::NT - DRS * PY;
+    int r = threadIdx.x / PY, yy = threadIdx.x - r * PY;
     for (int i = threadIdx.x; i < G::BT * G::HX * PY; i += G::NT) {
-        const int r = i / PY, yy = i - r * PY;
-        const int t = r / G::HX, xx = r - t * G::HX;
         float a[L];
 #pragma unroll
-        for (int k = 0; k < L; ++k) a[k] = sV[((t + k) * G::HX + xx) * PY + yy];
+        for (int k = 0; k < L; ++k) a[k] = sV[i + k * G::HX * PY];
         const float a0 = a[H];
         float s = a0, U[H + 1], D[H + 1];
 #pragma unroll
@@ -686,7 +686,7 @@ __device__ __forceinline__ void t_stage(const float *sV, float *sG1, const Tw<G:
             U[k] = fmaf(-2.f, a0, p);
             D[k] = a[H + k] - a[H - k];
         }
-        float *o = sG1 + ((t * G::HX + xx) * L) * PY + yy;
+        float *o = sG1 + (r * L) * PY + yy;
         o[0] = s;
 #pragma unroll
         for (int mu = 1; mu <= H; ++mu) {
@@ -698,6 +698,12 @@ __device__ __forceinline__ void t_stage(const float *sV, float *sG1, const Tw<G:
             }
             o[(2 * mu - 1) * PY] = A;     // G1(mu) = A - iB
             o[(2 * mu) * PY] = -B;
+        }
+        yy += DYS;
+        r += DRS;
+        if (yy >= PY) {
+            yy -= PY;
+            ++r;
         }
     }
 }
@@ -812,12 +818,14 @@ template <class G>
 __device__ __forceinline__ void t_stage_mu(const float *sV, float *sG1m, int mu, const TwRow<G::L> &tr)
 {
     constexpr int L = G::L, H = G::H, PY = G::PY;
+    // item i = (row r = (t, x'), column y') of the output planes; its samples along t are
+    // the halo elements i + k HX PY.  (r, y') advance by NT items at a time.
+    constexpr int DRS = G::NT / PY, DYS = G::NT - DRS * PY;
+    int r = threadIdx.x / PY, yy = threadIdx.x - r * PY;
     for (int i = threadIdx.x; i < G::BT * G::HX * PY; i += G::NT) {
-        const int r = i / PY, yy = i - r * PY;
-        const int t = r / G::HX, xx = r - t * G::HX;
         float a[L];
 #pragma unroll
-        for (int k = 0; k < L; ++k) a[k] = sV[((t + k) * G::HX + xx) * PY + yy];
+        for (int k = 0; k < L; ++k) a[k] = sV[i + k * G::HX * PY];
         float *o = sG1m + (2 * r) * PY + yy;
         if (mu == 0) {
             float sum = a[H];
@@ -834,6 +842,12 @@ __device__ __forceinline__ void t_stage_mu(const float *sV, float *sG1m, int mu,
             }
             o[0] = A;       // G1(mu) = A - iB
             o[PY] = -B;
+        }
+        yy += DYS;
+        r += DRS;
+        if (yy >= PY) {
+            yy -= PY;
+            ++r;
         }
     }
 }
