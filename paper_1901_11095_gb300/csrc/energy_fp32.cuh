@@ -225,15 +225,14 @@ __device__ __forceinline__ float cabs2(f2x v)
 }
 
 // Magnitudes of the R consecutive windows of one complex line, window r centred at
-// Z[H + r]: m[r][0] = |F_r(0)|, m[r][w] = |F_r(w)| + |F_r(-w)|.  Window 0 by the folded
-// direct DFT; the others by a sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w)
-// (|Q_r| = |F_r|): Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the
-// twiddles of a whole period are equal; Q_0 = F_0 needs no rotation.
-template <int L, int R, int NZ, bool ADD = false>
-__device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
+// Z[H + r], handed to put(r, w, m) as each is formed, w = 0..H in order for every window:
+// m = |F_r(0)| for w = 0, |F_r(w)| + |F_r(-w)| otherwise.  Window 0 by the folded direct
+// DFT; the others by a sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w) (|Q_r| = |F_r|):
+// Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the twiddles of a whole
+// period are equal; Q_0 = F_0 needs no rotation.
+template <int L, int R, int NZ, class Put>
+__device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, Put &&put)
 {
-    // ADD: the magnitudes are added to m (the -nu line of a pair onto the +nu line's)
-    auto put = [&](float &dst, float v) { dst = ADD ? dst + v : v; };
     constexpr int H = (L - 1) / 2;
     const f2x z0 = Z[H];
     const f2x m2 = pk(-2.f, -2.f);
@@ -248,7 +247,7 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
     }
     f2x P[L];          // P[H + w] for w = -H..H
     P[H] = s;
-    put(m[0][0], sqrt_approx(cabs2(s)));
+    put(0, 0, sqrt_approx(cabs2(s)));
 #pragma unroll
     for (int w = 1; w <= H; ++w) {
         f2x A = mul2(U[1], tw.c2[w % L]);
@@ -261,7 +260,7 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
         const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
         const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
         const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
-        put(m[0][w], sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm)));
+        put(0, w, sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm)));
         P[H + w] = Fp;
         P[H - w] = Fm;
     }
@@ -275,16 +274,16 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
             P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, tw_index<L>(w, r - H));
             P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, tw_index<L>(-w, r - H));
         }
-        put(m[r + 1][0], sqrt_approx(cabs2(P[H])));
+        put(r + 1, 0, sqrt_approx(cabs2(P[H])));
 #pragma unroll
-        for (int w = 1; w <= H; ++w) put(m[r + 1][w], sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w])));
+        for (int w = 1; w <= H; ++w) put(r + 1, w, sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w])));
     }
 }
 
-// The same for the real mu = 0, nu = 0 line: m[r][w] = |F_r(w)| for w = 1..H only (the -w
-// point is the conjugate mirror, counted by the half-spectrum factor); m[r][0] unused.
-template <int L, int R, int NZ>
-__device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[R][(L + 1) / 2])
+// The same for the real mu = 0, nu = 0 line: put(r, w, |F_r(w)|) for w = 1..H only (the -w
+// point is the conjugate mirror, counted by the half-spectrum factor; w = 0 is the DC term).
+template <int L, int R, int NZ, class Put>
+__device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const Tw<L> &tw, Put &&put)
 {
     constexpr int H = (L - 1) / 2;
     const float z0 = lo(Z[H]);
@@ -304,10 +303,9 @@ __device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const T
             B = fmaf(D[k], lo(tw.s2[(w * k) % L]), B);
         }
         const f2x F = pk(A, -B);                 // F(w) = A - iB
-        m[0][w] = sqrt_approx(fmaf(A, A, B * B));
+        put(0, w, sqrt_approx(fmaf(A, A, B * B)));
         P[w] = F;
     }
-    m[0][0] = 0.f;
 #pragma unroll
     for (int r = 0; r + 1 < R; ++r) {
         const f2x d = pk(lo(Z[r + 2 * H + 1]) - lo(Z[r]), 0.f);
@@ -315,9 +313,8 @@ __device__ __forceinline__ void line_mags_strip_real(const f2x (&Z)[NZ], const T
 #pragma unroll
         for (int w = 1; w <= H; ++w) {
             P[w] = rot_acc<L>(P[w], d, dsw, tw, tw_index<L>(w, r - H));
-            m[r + 1][w] = sqrt_approx(cabs2(P[w]));
+            put(r + 1, w, sqrt_approx(cabs2(P[w])));
         }
-        m[r + 1][0] = 0.f;
     }
 }
 
@@ -360,17 +357,12 @@ __device__ __forceinline__ void fill_w(float *sW, const SpecTables &tb)
     }
 }
 
-template <class G>
-__device__ __forceinline__ void accum(const float (&m)[G::H + 1], const float (&w)[G::H + 1][3], int wfirst, float &et,
-                                      float &ex, float &ey)
+// One magnitude (or folded pair of magnitudes) into an output's three energies.
+__device__ __forceinline__ void wsum(const float (&w)[3], float m, float &et, float &ex, float &ey)
 {
-#pragma unroll
-    for (int om = 0; om <= G::H; ++om) {
-        if (om < wfirst) continue;
-        et = fmaf(w[om][0], m[om], et);
-        ex = fmaf(w[om][1], m[om], ex);
-        ey = fmaf(w[om][2], m[om], ey);
-    }
+    et = fmaf(w[0], m, et);
+    ex = fmaf(w[1], m, ex);
+    ey = fmaf(w[2], m, ey);
 }
 
 // One complex line (weights of group (mu, nu)) for the thread's R outputs.
@@ -382,10 +374,7 @@ __device__ __forceinline__ void y_single(const float2 *line, int j, int mu, int 
     load_line<G>(line, j, Z);
     float w[G::H + 1][3];
     load_w<G>(sW, mu, nu, w);
-    float m[G::R][G::H + 1];
-    line_mags_strip<G::L, G::R>(Z, tw, m);
-#pragma unroll
-    for (int r = 0; r < G::R; ++r) accum<G>(m[r], w, 0, et[r], ex[r], ey[r]);
+    line_mags_strip<G::L, G::R>(Z, tw, [&](int r, int om, float m) { wsum(w[om], m, et[r], ex[r], ey[r]); });
 }
 
 // The +nu and -nu lines of one mu > 0, which share their weights.
@@ -399,15 +388,14 @@ __device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j
     {
         f2x Z[G::NZ];
         load_line<G>(lp, j, Z);
-        line_mags_strip<G::L, G::R>(Z, tw, mp);
+        line_mags_strip<G::L, G::R>(Z, tw, [&](int r, int om, float m) { mp[r][om] = m; });
     }
     {
         f2x Z[G::NZ];
         load_line<G>(lm, j, Z);
-        line_mags_strip<G::L, G::R, G::NZ, true>(Z, tw, mp);
+        line_mags_strip<G::L, G::R>(Z, tw,
+                                    [&](int r, int om, float m) { wsum(w[om], mp[r][om] + m, et[r], ex[r], ey[r]); });
     }
-#pragma unroll
-    for (int r = 0; r < G::R; ++r) accum<G>(mp[r], w, 0, et[r], ex[r], ey[r]);
 }
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
@@ -419,10 +407,7 @@ __device__ __forceinline__ void y_real(const float2 *line, int j, const float *s
     load_line<G>(line, j, Z);
     float w[G::H + 1][3];
     load_w<G>(sW, 0, 0, w);
-    float m[G::R][G::H + 1];
-    line_mags_strip_real<G::L, G::R>(Z, tw, m);
-#pragma unroll
-    for (int r = 0; r < G::R; ++r) accum<G>(m[r], w, 1, et[r], ex[r], ey[r]);
+    line_mags_strip_real<G::L, G::R>(Z, tw, [&](int r, int om, float m) { wsum(w[om], m, et[r], ex[r], ey[r]); });
 }
 
 // x stage for one mu: G1[mu](x-h..x+h, y') -> G2[mu, nu](x, y') for the BT x BX x PY items.
