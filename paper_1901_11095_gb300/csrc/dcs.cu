@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(DNT) dcs_line_kernel(const __grid_constant__ D
 // the next step are copied asynchronously while the current step is computed, each halo
 // value is read once per chunk (plus the two boundary planes of the chunk), and the boundary
 // extension and index set-up are paid once per item instead of once per copy.
-constexpr int SC = 64;                          // output planes per chunk
+constexpr int SC = 128;                         // output planes per chunk
 constexpr int RING = 18;                        // plane slots: 10 being read + 8 in flight
 constexpr int PROW = 72;                        // slot row pitch (floats); halo column c at c + 3
 constexpr int PSLOT = (DX + 2) * PROW;          // one plane slot (floats)
@@ -283,7 +283,6 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
     __shared__ double red[DNT / 32][3];
     const float g1 = k.g[1], g2 = k.g[2], g3 = k.g[3];
     const int tid = threadIdx.x;
-    const int yq = tid % (DY / QY), x = (tid / (DY / QY)) % DX, tq = tid / ((DY / QY) * DX);
     for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
         int lo = 0, hi = bt.n - 1;
         while (lo < hi) {
@@ -291,36 +290,46 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
             if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
         }
         const DVol &v = bt.v[lo];
-        const int64_t local = it - v.item0;
-        const int m = (int)(local / v.tiles);
-        const int64_t rec = local - m * v.tiles;
-        const int ty = (int)(rec % v.tiles_y);
-        const int tx = (int)((rec / v.tiles_y) % v.tiles_x);
-        const int64_t ck = rec / ((int64_t)v.tiles_y * v.tiles_x);
+        // item -> (map, chunk, x block, y block) in 32 bits (the launcher checks 3 x records)
+        const unsigned local = (unsigned)(it - v.item0), ntile = (unsigned)v.tiles;
+        const int m = (int)(local / ntile);
+        const unsigned rec = local - (unsigned)m * ntile, q1 = rec / (unsigned)v.tiles_y, q2 = q1 / (unsigned)v.tiles_x;
+        const int ty = (int)(rec - q1 * (unsigned)v.tiles_y);
+        const int tx = (int)(q1 - q2 * (unsigned)v.tiles_x);
+        const int64_t ck = q2;
         const int64_t T = v.T, X = v.X, Y = v.Y, XY = X * Y;
         const int64_t t0 = ck * SC, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
         const float *Em = v.E + m * T * XY;
         float *Sm = v.Sm + m * T * XY;
 
-        // this thread's copies within one plane: source offset in the plane, slot offset
-        int64_t goff[KEL];
+        // this thread's copies within one plane: source pointer of its element in plane 0 of
+        // the map and its byte offset in a slot (a shared-memory address is 32 bits)
+        const float *srcq[KEL];
         int soff[KEL];
 #pragma unroll
         for (int q = 0; q < KEL; ++q) {
             const int e = tid + q * DNT;
             const int b = e / (DY + 2), c = e - b * (DY + 2);
-            goff[q] = e < PEL ? ext_index(x0 - 1 + b, X, bt.bnd) * Y + ext_index(y0 - 1 + c, Y, bt.bnd) : 0;
-            soff[q] = e < PEL ? b * PROW + 3 + c : -1;
+            srcq[q] = Em + (e < PEL ? ext_index(x0 - 1 + b, X, bt.bnd) * Y + ext_index(y0 - 1 + c, Y, bt.bnd) : 0);
+            soff[q] = e < PEL ? (b * PROW + 3 + c) * (int)sizeof(float) : -1;
         }
-        // copies halo planes r0 .. r1 - 1 of the chunk (plane r is t0 - 1 + r) into their slots
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(sE);
+        // copies halo planes r0 .. r1 - 1 of the chunk (plane r is t0 - 1 + r) into their slots;
+        // planes inside the volume skip the boundary extension, and only the last of a thread's
+        // KEL copies can fall outside the plane's PEL elements
         auto stage = [&](int r0, int r1) {
             int slot = r0 % RING;
             for (int r = r0; r < r1; ++r) {
-                const float *src = Em + ext_index(t0 - 1 + r, T, bt.bnd) * XY;
-                float *dst = sE + slot * PSLOT;
+                int64_t gt = t0 - 1 + r;
+                if ((uint64_t)gt >= (uint64_t)T) gt = ext_index(gt, T, bt.bnd);
+                const int64_t poff = gt * XY;
+                const unsigned dst = sbase + (unsigned)(slot * PSLOT * (int)sizeof(float));
 #pragma unroll
                 for (int q = 0; q < KEL; ++q)
-                    if (soff[q] >= 0) cp_async4(dst + soff[q], src + goff[q]);
+                    if ((q + 1) * DNT <= PEL || soff[q] >= 0)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + (unsigned)soff[q]),
+                                     "l"(srcq[q] + poff)
+                                     : "memory");
                 slot = slot + 1 == RING ? 0 : slot + 1;
             }
             cp_async_commit();
@@ -328,6 +337,13 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
 
         const int64_t left = T - t0;
         const int nsteps = (int)(((left < SC ? left : SC) + DT - 1) / DT);
+        // thread -> (t quarter, x row, y quad) of the block; a block at the last columns of the
+        // volume packs its nyq < 16 live quads into the first threads, so that whole warps sit
+        // out the arithmetic instead of computing columns past Y
+        const int64_t left_y = Y - y0;
+        const int nyq = left_y >= DY ? DY / QY : (int)((left_y + QY - 1) / QY);
+        const int yq = tid % nyq, x = (tid / nyq) % DX, tq = tid / (nyq * DX);
+        const bool live = tq < DT / QT;
         const int64_t gx = x0 + x, gy = y0 + QY * yq;
         float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
 
@@ -341,90 +357,95 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
             }
             __syncthreads();
 
-            // halo planes rb .. rb + 5 of this thread's 4 output planes, rows x .. x + 2,
-            // columns 4 yq .. 4 yq + 5 (stored at + 3)
-            const int rb = DT * st + QT * tq;
-            int sl[QT + 2];
+            if (live) {
+                // halo planes rb .. rb + 5 of this thread's 4 output planes, rows x .. x + 2,
+                // columns 4 yq .. 4 yq + 5 (stored at + 3)
+                const int rb = DT * st + QT * tq;
+                int sl[QT + 2];
+                {
+                    int sp = rb % RING;
 #pragma unroll
-            for (int p = 0; p < QT + 2; ++p) {
-                const int sp = (rb + p) % RING;
-                sl[p] = sp * PSLOT + x * PROW + QY * yq + 3;
-            }
-            float cen[QT][QY], out[QT][QY];
-#pragma unroll
-            for (int to = 0; to < QT; ++to) {
-                const float4 c4 = *reinterpret_cast<const float4 *>(sE + sl[to + 1] + PROW + 1);
-                cen[to][0] = c4.x; cen[to][1] = c4.y; cen[to][2] = c4.z; cen[to][3] = c4.w;
-#pragma unroll
-                for (int yo = 0; yo < QY; ++yo) out[to][yo] = 0.f;
-            }
-#pragma unroll
-            for (int p = 0; p < QT + 2; ++p)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float *row = sE + sl[p] + b * PROW;
-                    float w[QY + 2];
-                    w[0] = row[0];
-                    const float4 mid = *reinterpret_cast<const float4 *>(row + 1);
-                    w[1] = mid.x; w[2] = mid.y; w[3] = mid.z; w[4] = mid.w;
-                    w[5] = row[5];
-#pragma unroll
-                    for (int to = 0; to < QT; ++to) {
-                        const int dt = p - (to + 1);
-                        if (dt < -1 || dt > 1) continue;
-#pragma unroll
-                        for (int yo = 0; yo < QY; ++yo)
-#pragma unroll
-                            for (int cc = -1; cc <= 1; ++cc) {
-                                const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
-                                if (d2 == 0) continue;
-                                const float g = d2 == 1 ? g1 : (d2 == 2 ? g2 : g3);
-                                out[to][yo] += fabsf(fmaf(-g, w[yo + 1 + cc], cen[to][yo]));
-                            }
+                    for (int p = 0; p < QT + 2; ++p) {
+                        sl[p] = sp * PSLOT + x * PROW + QY * yq + 3;
+                        sp = sp + 1 == RING ? 0 : sp + 1;
                     }
                 }
-
-            if (gx < X) {
-                const bool full = gy + QY <= Y && t0 + rb + QT <= T;   // the whole 4 x 4 block is inside
-                float *o = Sm + ((t0 + rb) * X + gx) * Y + gy;
-                const int64_t plane = X * Y;
-                if (full) {
+                float cen[QT][QY], out[QT][QY];
 #pragma unroll
-                    for (int to = 0; to < QT; ++to) {
+                for (int to = 0; to < QT; ++to) {
+                    const float4 c4 = *reinterpret_cast<const float4 *>(sE + sl[to + 1] + PROW + 1);
+                    cen[to][0] = c4.x; cen[to][1] = c4.y; cen[to][2] = c4.z; cen[to][3] = c4.w;
 #pragma unroll
-                        for (int yo = 0; yo < QY; ++yo) {
-                            out[to][yo] *= k.invQ;
-                            mn = fminf(mn, out[to][yo]);
-                            mx = fmaxf(mx, out[to][yo]);
-                            sm += out[to][yo];
-                        }
-                        // widest aligned stores for this row start
-                        float *q = o + to * plane;
-                        const unsigned a = (unsigned)(reinterpret_cast<uintptr_t>(q) & 15);
-                        if (a == 0) {
-                            *reinterpret_cast<float4 *>(q) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
-                        } else if (a == 8) {
-                            *reinterpret_cast<float2 *>(q) = make_float2(out[to][0], out[to][1]);
-                            *reinterpret_cast<float2 *>(q + 2) = make_float2(out[to][2], out[to][3]);
-                        } else {   // 4 or 12: q + 1 is 8-byte aligned
-                            q[0] = out[to][0];
-                            *reinterpret_cast<float2 *>(q + 1) = make_float2(out[to][1], out[to][2]);
-                            q[3] = out[to][3];
+                    for (int yo = 0; yo < QY; ++yo) out[to][yo] = 0.f;
+                }
+#pragma unroll
+                for (int p = 0; p < QT + 2; ++p)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const float *row = sE + sl[p] + b * PROW;
+                        float w[QY + 2];
+                        w[0] = row[0];
+                        const float4 mid = *reinterpret_cast<const float4 *>(row + 1);
+                        w[1] = mid.x; w[2] = mid.y; w[3] = mid.z; w[4] = mid.w;
+                        w[5] = row[5];
+#pragma unroll
+                        for (int to = 0; to < QT; ++to) {
+                            const int dt = p - (to + 1);
+                            if (dt < -1 || dt > 1) continue;
+#pragma unroll
+                            for (int yo = 0; yo < QY; ++yo)
+#pragma unroll
+                                for (int cc = -1; cc <= 1; ++cc) {
+                                    const int d2 = dt * dt + (b - 1) * (b - 1) + cc * cc;
+                                    if (d2 == 0) continue;
+                                    const float g = d2 == 1 ? g1 : (d2 == 2 ? g2 : g3);
+                                    out[to][yo] += fabsf(fmaf(-g, w[yo + 1 + cc], cen[to][yo]));
+                                }
                         }
                     }
-                } else {
+
+                if (gx < X) {
+                    const bool full = gy + QY <= Y && t0 + rb + QT <= T;   // the whole 4 x 4 block is inside
+                    float *o = Sm + ((t0 + rb) * X + gx) * Y + gy;
+                    const int64_t plane = X * Y;
+                    if (full) {
 #pragma unroll
-                    for (int to = 0; to < QT; ++to) {
-                        const int64_t gt = t0 + rb + to;
-                        if (gt >= T) break;
+                        for (int to = 0; to < QT; ++to) {
 #pragma unroll
-                        for (int yo = 0; yo < QY; ++yo) {
-                            out[to][yo] *= k.invQ;
-                            if (gy + yo < Y) {
+                            for (int yo = 0; yo < QY; ++yo) {
+                                out[to][yo] *= k.invQ;
                                 mn = fminf(mn, out[to][yo]);
                                 mx = fmaxf(mx, out[to][yo]);
                                 sm += out[to][yo];
-                                o[to * plane + yo] = out[to][yo];
+                            }
+                            // widest aligned stores for this row start
+                            float *q = o + to * plane;
+                            const unsigned a = (unsigned)(reinterpret_cast<uintptr_t>(q) & 15);
+                            if (a == 0) {
+                                *reinterpret_cast<float4 *>(q) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
+                            } else if (a == 8) {
+                                *reinterpret_cast<float2 *>(q) = make_float2(out[to][0], out[to][1]);
+                                *reinterpret_cast<float2 *>(q + 2) = make_float2(out[to][2], out[to][3]);
+                            } else {   // 4 or 12: q + 1 is 8-byte aligned
+                                q[0] = out[to][0];
+                                *reinterpret_cast<float2 *>(q + 1) = make_float2(out[to][1], out[to][2]);
+                                q[3] = out[to][3];
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int to = 0; to < QT; ++to) {
+                            const int64_t gt = t0 + rb + to;
+                            if (gt >= T) break;
+#pragma unroll
+                            for (int yo = 0; yo < QY; ++yo) {
+                                out[to][yo] *= k.invQ;
+                                if (gy + yo < Y) {
+                                    mn = fminf(mn, out[to][yo]);
+                                    mx = fmaxf(mx, out[to][yo]);
+                                    sm += out[to][yo];
+                                    o[to * plane + yo] = out[to][yo];
+                                }
                             }
                         }
                     }
@@ -577,6 +598,7 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         v.X = d.X;
         v.Y = d.Y;
         v.tiles = dcs_num_records(d, p->stencil);
+        if (3 * v.tiles > 0x7fffffffLL) return cudaErrorInvalidValue;   // items of a volume in 32 bits
         v.tiles_x = (int)nx;
         v.tiles_y = (int)ny;
         v.item0 = total;
