@@ -230,42 +230,48 @@ __device__ __forceinline__ float cabs2(f2x v)
 // DFT; the others by a sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w) (|Q_r| = |F_r|):
 // Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the twiddles of a whole
 // period are equal; Q_0 = F_0 needs no rotation.
-template <int L, int R, int NZ, class Put>
-__device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, Put &&put)
-{
-    constexpr int H = (L - 1) / 2;
-    const f2x z0 = Z[H];
-    const f2x m2 = pk(-2.f, -2.f);
-    f2x U[H + 1], D[H + 1];
-    f2x s = z0;
+template <int L, int NZ>
+struct LineWalk {
+    static constexpr int H = (L - 1) / 2;
+    f2x P[L];   // Q_r(w) at P[H + w], w = -H..H
+
+    // window 0: m[0] = |F_0(0)|, m[w] = |F_0(w)| + |F_0(-w)|
+    __device__ __forceinline__ void start(const f2x (&Z)[NZ], const Tw<L> &tw, float (&m)[H + 1])
+    {
+        const f2x z0 = Z[H];
+        const f2x m2 = pk(-2.f, -2.f);
+        f2x U[H + 1], D[H + 1];
+        f2x s = z0;
 #pragma unroll
-    for (int k = 1; k <= H; ++k) {
-        const f2x p = add2(Z[H + k], Z[H - k]);
-        s = add2(s, p);
-        U[k] = fma2(z0, m2, p);
-        D[k] = sub2(Z[H + k], Z[H - k]);
-    }
-    f2x P[L];          // P[H + w] for w = -H..H
-    P[H] = s;
-    put(0, 0, sqrt_approx(cabs2(s)));
-#pragma unroll
-    for (int w = 1; w <= H; ++w) {
-        f2x A = mul2(U[1], tw.c2[w % L]);
-        f2x B = mul2(D[1], tw.s2[w % L]);
-#pragma unroll
-        for (int k = 2; k <= H; ++k) {
-            A = fma2(U[k], tw.c2[(w * k) % L], A);
-            B = fma2(D[k], tw.s2[(w * k) % L], B);
+        for (int k = 1; k <= H; ++k) {
+            const f2x p = add2(Z[H + k], Z[H - k]);
+            s = add2(s, p);
+            U[k] = fma2(z0, m2, p);
+            D[k] = sub2(Z[H + k], Z[H - k]);
         }
-        const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
-        const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
-        const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
-        put(0, w, sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm)));
-        P[H + w] = Fp;
-        P[H - w] = Fm;
-    }
+        P[H] = s;
+        m[0] = sqrt_approx(cabs2(s));
 #pragma unroll
-    for (int r = 0; r + 1 < R; ++r) {
+        for (int w = 1; w <= H; ++w) {
+            f2x A = mul2(U[1], tw.c2[w % L]);
+            f2x B = mul2(D[1], tw.s2[w % L]);
+#pragma unroll
+            for (int k = 2; k <= H; ++k) {
+                A = fma2(U[k], tw.c2[(w * k) % L], A);
+                B = fma2(D[k], tw.s2[(w * k) % L], B);
+            }
+            const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+            const f2x Fp = pk(ax + by, ay - bx);   // F(+w) = A - iB
+            const f2x Fm = pk(ax - by, ay + bx);   // F(-w) = A + iB
+            m[w] = sqrt_approx(cabs2(Fp)) + sqrt_approx(cabs2(Fm));
+            P[H + w] = Fp;
+            P[H - w] = Fm;
+        }
+    }
+
+    // window r + 1 from window r (r a compile-time constant once unrolled)
+    __device__ __forceinline__ void step(const f2x (&Z)[NZ], const Tw<L> &tw, int r, float (&m)[H + 1])
+    {
         const f2x d = sub2(Z[r + 2 * H + 1], Z[r]);
         const f2x dsw = swapneg(d);
         P[H] = add2(P[H], d);
@@ -274,9 +280,53 @@ __device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> 
             P[H + w] = rot_acc<L>(P[H + w], d, dsw, tw, tw_index<L>(w, r - H));
             P[H - w] = rot_acc<L>(P[H - w], d, dsw, tw, tw_index<L>(-w, r - H));
         }
-        put(r + 1, 0, sqrt_approx(cabs2(P[H])));
+        m[0] = sqrt_approx(cabs2(P[H]));
 #pragma unroll
-        for (int w = 1; w <= H; ++w) put(r + 1, w, sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w])));
+        for (int w = 1; w <= H; ++w) m[w] = sqrt_approx(cabs2(P[H + w])) + sqrt_approx(cabs2(P[H - w]));
+    }
+};
+
+// Magnitudes of the R consecutive windows of one complex line, window r centred at
+// Z[H + r], handed to put(r, w, m), w = 0..H in order for every window: m = |F_r(0)| for
+// w = 0, |F_r(w)| + |F_r(-w)| otherwise.  Window 0 by the folded direct DFT; the others by a
+// sliding recurrence on Q_r(w) = e^{-i th w r} F_r(w) (|Q_r| = |F_r|):
+// Q_{r+1} = Q_r + (Z[r+2h+1] - Z[r]) e^{-i th w (r-h)}, because the twiddles of a whole
+// period are equal; Q_0 = F_0 needs no rotation.
+template <int L, int R, int NZ, class Put>
+__device__ __forceinline__ void line_mags_strip(const f2x (&Z)[NZ], const Tw<L> &tw, Put &&put)
+{
+    constexpr int H = (L - 1) / 2;
+    LineWalk<L, NZ> lw;
+    float m[H + 1];
+    lw.start(Z, tw, m);
+#pragma unroll
+    for (int w = 0; w <= H; ++w) put(0, w, m[w]);
+#pragma unroll
+    for (int r = 0; r + 1 < R; ++r) {
+        lw.step(Z, tw, r, m);
+#pragma unroll
+        for (int w = 0; w <= H; ++w) put(r + 1, w, m[w]);
+    }
+}
+
+// Two lines walked window by window together (independent work for the scheduler to
+// interleave): put(r, w, ma, mb) with each line's magnitudes as in line_mags_strip.
+template <int L, int R, int NZ, class Put>
+__device__ __forceinline__ void line_mags_strip2(const f2x (&Za)[NZ], const f2x (&Zb)[NZ], const Tw<L> &tw, Put &&put)
+{
+    constexpr int H = (L - 1) / 2;
+    LineWalk<L, NZ> la, lb;
+    float ma[H + 1], mb[H + 1];
+    la.start(Za, tw, ma);
+    lb.start(Zb, tw, mb);
+#pragma unroll
+    for (int w = 0; w <= H; ++w) put(0, w, ma[w], mb[w]);
+#pragma unroll
+    for (int r = 0; r + 1 < R; ++r) {
+        la.step(Za, tw, r, ma);
+        lb.step(Zb, tw, r, mb);
+#pragma unroll
+        for (int w = 0; w <= H; ++w) put(r + 1, w, ma[w], mb[w]);
     }
 }
 
@@ -384,18 +434,12 @@ __device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j
 {
     float w[G::H + 1][3];
     load_w<G>(sW, mu, nu, w);
-    float mp[G::R][G::H + 1];   // |F(+nu)| + |F(-nu)| per output and |omega|
-    {
-        f2x Z[G::NZ];
-        load_line<G>(lp, j, Z);
-        line_mags_strip<G::L, G::R>(Z, tw, [&](int r, int om, float m) { mp[r][om] = m; });
-    }
-    {
-        f2x Z[G::NZ];
-        load_line<G>(lm, j, Z);
-        line_mags_strip<G::L, G::R>(Z, tw,
-                                    [&](int r, int om, float m) { wsum(w[om], mp[r][om] + m, et[r], ex[r], ey[r]); });
-    }
+    f2x Zp[G::NZ], Zm[G::NZ];
+    load_line<G>(lp, j, Zp);
+    load_line<G>(lm, j, Zm);
+    line_mags_strip2<G::L, G::R>(Zp, Zm, tw, [&](int r, int om, float mp, float mm) {
+        wsum(w[om], mp + mm, et[r], ex[r], ey[r]);   // |F(+nu)| + |F(-nu)| share the weights
+    });
 }
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
