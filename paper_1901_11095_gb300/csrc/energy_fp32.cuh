@@ -646,50 +646,63 @@ __device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 
-// Halo tile of V in shared memory; outside the volume the boundary extension supplies the
-// samples.  G provides BT, BX, BY, H, HX, PY, NV and NT.
+// Issues the asynchronous 4-byte copies of one tile's V halo into sV ([plane][row][column],
+// NV floats); outside the volume the boundary extension supplies the samples.  Element
+// i = (a, x', y') advances by NT elements at a time, NT / PY rows and NT % PY columns further,
+// so no element needs a division.  Interior tiles address the volume by 32-bit offsets from
+// the halo's first sample; tiles at a face extend each coordinate (a range check, the
+// extension only outside).  G provides BT, BX, BY, H, HX, PY, NV and NT.
+template <class G>
+__device__ __forceinline__ void issue_v_copies(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                               int64_t t0, int64_t x0, int64_t y0, float *sV)
+{
+    constexpr int H = G::H, PY = G::PY, HX = G::HX;
+    constexpr int DRS = G::NT / PY, DYS = G::NT - DRS * PY;
+    static_assert(DRS + 1 < HX, "one step crosses at most one plane");
+    int yy = threadIdx.x % PY, r = threadIdx.x / PY;
+    int xx = r % HX, a = r / HX;
+    auto advance = [&]() {
+        yy += DYS;
+        int dr = DRS;
+        if (yy >= PY) {
+            yy -= PY;
+            ++dr;
+        }
+        xx += dr;
+        if (xx >= HX) {
+            xx -= HX;
+            ++a;
+        }
+    };
+    const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
+                        y0 + G::BY + H <= Y && (int64_t)(G::BT + 2 * H) * X * Y < 0x7fffffffLL;
+    if (inside) {
+        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
+        const int Yi = (int)Y, XYi = (int)(X * Y);
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            cp_async_f32(sV + i, src + (a * XYi + xx * Yi + yy));
+            advance();
+        }
+    } else {
+        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
+            int64_t gt = t0 - H + a, gx = x0 - H + xx, gy = y0 - H + yy;
+            if ((uint64_t)gt >= (uint64_t)T) gt = ext_index(gt, T, bnd);
+            if ((uint64_t)gx >= (uint64_t)X) gx = ext_index(gx, X, bnd);
+            if ((uint64_t)gy >= (uint64_t)Y) gy = ext_index(gy, Y, bnd);
+            cp_async_f32(sV + i, V + (gt * X + gx) * Y + gy);
+            advance();
+        }
+    }
+}
+
+// Halo tile of V in shared memory, complete and visible to the thread on return (the caller
+// synchronises the CTA).
 template <class G>
 __device__ __forceinline__ void stage_v(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
                                         int64_t t0, int64_t x0, int64_t y0, float *sV)
 {
-    constexpr int H = G::H, PY = G::PY, HX = G::HX;
-    const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
-                        y0 + G::BY + H <= Y && (int64_t)(G::BT + 2 * H) * X * Y < 0x7fffffffLL;
-    if (inside) {
-        // asynchronous 4-byte copies (no register round trip); the element offsets in the
-        // volume fit in 32 bits and advance by NT elements of the [plane][row][column] halo
-        // at a time, each step NT / PY rows and NT % PY columns further
-        constexpr int DRS = G::NT / PY, DYS = G::NT - DRS * PY;
-        static_assert(DRS + 1 < HX, "one step crosses at most one plane");
-        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
-        const int Yi = (int)Y, XYi = (int)(X * Y);
-        int yy = threadIdx.x % PY, r = threadIdx.x / PY;
-        int xx = r % HX, a = r / HX;
-        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            cp_async_f32(sV + i, src + (a * XYi + xx * Yi + yy));
-            yy += DYS;
-            int dr = DRS;
-            if (yy >= PY) {
-                yy -= PY;
-                ++dr;
-            }
-            xx += dr;
-            if (xx >= HX) {
-                xx -= HX;
-                ++a;
-            }
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    } else {
-        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            const int r = i / PY, yy = i - r * PY;
-            const int a = r / G::HX, xx = r - a * G::HX;
-            const int64_t gt = ext_index(t0 - H + a, T, bnd);
-            const int64_t gx = ext_index(x0 - H + xx, X, bnd);
-            const int64_t gy = ext_index(y0 - H + yy, Y, bnd);
-            sV[i] = __ldg(V + (gt * X + gx) * Y + gy);
-        }
-    }
+    issue_v_copies<G>(V, T, X, Y, bnd, t0, x0, y0, sV);
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Stage t: every (t, x', y') column of the halo tile -> G1 components
@@ -1042,26 +1055,7 @@ template <class G>
 __device__ __forceinline__ void stage_v_async(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
                                               int64_t t0, int64_t x0, int64_t y0, float *sV)
 {
-    constexpr int H = G::H, PY = G::PY;
-    const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
-                        y0 + G::BY + H <= Y;
-    if (inside) {
-        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
-        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            const int r = i / PY, yy = i - r * PY;
-            const int a = r / G::HX, xx = r - a * G::HX;
-            cp_async_f32(sV + i, src + ((int64_t)a * X + xx) * Y + yy);
-        }
-    } else {
-        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            const int r = i / PY, yy = i - r * PY;
-            const int a = r / G::HX, xx = r - a * G::HX;
-            const int64_t gt = ext_index(t0 - H + a, T, bnd);
-            const int64_t gx = ext_index(x0 - H + xx, X, bnd);
-            const int64_t gy = ext_index(y0 - H + yy, Y, bnd);
-            cp_async_f32(sV + i, V + (gt * X + gx) * Y + gy);
-        }
-    }
+    issue_v_copies<G>(V, T, X, Y, bnd, t0, x0, y0, sV);
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
