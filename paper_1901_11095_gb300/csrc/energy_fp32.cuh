@@ -784,6 +784,26 @@ __device__ __forceinline__ void store_outputs(float *__restrict__ E, int64_t T, 
 }
 
 // One output tile of one volume.  Every thread of the CTA calls it with the same tile.
+// Stage y of one mu for this thread's strip j of output row `row`: every line of the G2 slice
+// that x_stage_slide left in sG2.
+template <class G>
+__device__ __forceinline__ void y_stage_mu(const float2 *sG2, int row, int j, int mu, const float *sW,
+                                           const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R],
+                                           float (&ey)[G::R])
+{
+    constexpr int L = G::L, H = G::H;
+    const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
+    if (mu == 0) {
+        y_real<G>(l0, j, sW, tw, et, ex, ey);
+#pragma unroll 1
+        for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
+    } else {
+        y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
+#pragma unroll 1
+        for (int nu = 1; nu <= H; ++nu) y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
+    }
+}
+
 template <class G>
 __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
                                             int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
@@ -809,6 +829,7 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
     __syncthreads();
 
     const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;
+    const bool ylive = y0 + G::R * j < Y;   // strips wholly past the last column sit out stage y
     float et[G::R], ex[G::R], ey[G::R];
 #pragma unroll
     for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
@@ -817,17 +838,7 @@ __device__ __forceinline__ void energy_tile(const float *__restrict__ V, int64_t
     for (int mu = 0; mu <= H; ++mu) {
         x_stage_slide<G>(sG1, sG2, mu, tw);
         __syncthreads();
-        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
-        if (mu == 0) {
-            y_real<G>(l0, j, sW, tw, et, ex, ey);
-#pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
-        } else {
-            y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
-#pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu)
-                y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
-        }
+        if (ylive) y_stage_mu<G>(sG2, row, j, mu, sW, tw, et, ex, ey);
         __syncthreads();
     }
 
@@ -1081,6 +1092,7 @@ __device__ __forceinline__ void energy_tile_pf(const TileRef &c, const TileRef *
     __syncthreads();
 
     const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;
+    const bool ylive = c.y0 + G::R * j < c.Y;   // strips wholly past the last column sit out stage y
     float et[G::R], ex[G::R], ey[G::R];
 #pragma unroll
     for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
@@ -1090,17 +1102,7 @@ __device__ __forceinline__ void energy_tile_pf(const TileRef &c, const TileRef *
         x_stage_slide<G>(sG1, sG2, mu, tw);
         __syncthreads();
         if (mu == H && nx) stage_v_async<G>(nx->V, nx->T, nx->X, nx->Y, bnd, nx->t0, nx->x0, nx->y0, sO);
-        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
-        if (mu == 0) {
-            y_real<G>(l0, j, sW, tw, et, ex, ey);
-#pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
-        } else {
-            y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
-#pragma unroll 1
-            for (int nu = 1; nu <= H; ++nu)
-                y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
-        }
+        if (ylive) y_stage_mu<G>(sG2, row, j, mu, sW, tw, et, ex, ey);
         __syncthreads();
     }
     store_outputs<G>(c.E, c.T, c.X, c.Y, c.t0, c.x0, c.y0, row, j, tb.escale, et, ex, ey);
