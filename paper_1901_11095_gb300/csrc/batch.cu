@@ -54,39 +54,62 @@ __global__ void __launch_bounds__(256) reduce_volumes_kernel(const __grid_consta
     }
 }
 
+constexpr int CCH = 1024;   // voxels per chunk of the combination: 256 threads x 4
+
 struct CVol {
     const float *Sm;   // [3][N]
     float *S;
     int64_t N;
+    int64_t chunk0;    // first chunk of this volume
 };
 struct CBatch {
     int n;
     double a, b, c, eps;
+    int64_t chunks;
     CVol v[kMaxBatch];
 };
 
-// Eq. 6 on the min-max normalised maps of every volume of the batch; one grid-stride pass
-// per volume, all in one launch.
+// Eq. 6 on the min-max normalised maps of every volume of the batch, in one launch: each
+// block first forms every volume's offsets and factors (FP64, once per block, into shared
+// memory), then walks the chunks of 1024 consecutive voxels of all volumes (a chunk's volume
+// by binary search), each thread loading its four voxels' three maps before any store.
 __global__ void __launch_bounds__(256) combine_batch_kernel(const __grid_constant__ CBatch cb,
                                                             const double *__restrict__ stats)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ float coef[kMaxBatch][6];   // lo[0..2], al[0..2] of each volume
     const double wts[3] = {cb.a, cb.b, cb.c};
-    for (int vi = 0; vi < cb.n; ++vi) {
-        const CVol &v = cb.v[vi];
-        float lo[3], al[3];
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const double l = stats[9 * vi + 3 * m], h = stats[9 * vi + 3 * m + 1];
-            const double mag = fmax(fabs(l), fabs(h));
-            const double scale = (h - l) <= cb.eps * mag ? 0.0 : 1.0 / (h - l);
-            lo[m] = (float)l;
-            al[m] = (float)(wts[m] * scale);
+    for (int e = threadIdx.x; e < 3 * cb.n; e += blockDim.x) {
+        const int vi = e / 3, m = e - 3 * vi;
+        const double l = stats[9 * vi + 3 * m], h = stats[9 * vi + 3 * m + 1];
+        const double mag = fmax(fabs(l), fabs(h));
+        const double scale = (h - l) <= cb.eps * mag ? 0.0 : 1.0 / (h - l);
+        coef[vi][m] = (float)l;
+        coef[vi][3 + m] = (float)(wts[m] * scale);
+    }
+    __syncthreads();
+    for (int64_t c = blockIdx.x; c < cb.chunks; c += gridDim.x) {
+        int lo = 0, hi = cb.n - 1;   // last volume whose first chunk is <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cb.v[mid].chunk0 <= c) lo = mid; else hi = mid - 1;
         }
+        const CVol &v = cb.v[lo];
+        const float *cf = coef[lo];
+        const int64_t base = (c - v.chunk0) * CCH + threadIdx.x;
         const float *s0 = v.Sm, *s1 = v.Sm + v.N, *s2 = v.Sm + 2 * v.N;
-        for (int64_t i = i0; i < v.N; i += stride)
-            v.S[i] = fmaf(al[2], s2[i] - lo[2], fmaf(al[1], s1[i] - lo[1], al[0] * (s0[i] - lo[0])));
+        float x0[CCH / 256], x1[CCH / 256], x2[CCH / 256];
+#pragma unroll
+        for (int k = 0; k < CCH / 256; ++k) {
+            const int64_t i = base + k * 256;
+            x0[k] = i < v.N ? __ldg(s0 + i) : 0.f;
+            x1[k] = i < v.N ? __ldg(s1 + i) : 0.f;
+            x2[k] = i < v.N ? __ldg(s2 + i) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < CCH / 256; ++k) {
+            const int64_t i = base + k * 256;
+            if (i < v.N) v.S[i] = fmaf(cf[5], x2[k] - cf[2], fmaf(cf[4], x1[k] - cf[1], cf[3] * (x0[k] - cf[0])));
+        }
     }
 }
 
@@ -110,15 +133,17 @@ cudaError_t launch_batch_stats_combine(const BatchVolDesc *vols, int n, const sa
         cb.v[i].Sm = vols[i].Sm;
         cb.v[i].S = vols[i].S;
         cb.v[i].N = vols[i].N;
-        total += vols[i].N;
+        cb.v[i].chunk0 = total;
+        total += (vols[i].N + CCH - 1) / CCH;
     }
+    cb.chunks = total;
     reduce_volumes_kernel<<<n, 256, 0, s>>>(rb, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (total / n + 255) / 256;
+    int64_t blocks = total;                         // chunks
     const int64_t cap = (int64_t)nsm * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
