@@ -282,7 +282,8 @@ def run_batch(args, rank: int, world: int) -> None:
         return
     out = {"metric": "saliency voxels/s", "value": world * nvox / (ms / 1e3), "unit": "voxels/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision], "data": "synthetic",
            "config": workload_config(args), "autotune_choice": choice,
            "e2e": {"value": world * nvox / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": 4 * nvox,
                    "d2h_bytes_per_step": 4 * nvox, "ms_per_step": e2e_ms},
@@ -603,23 +604,44 @@ def run_ours(args, rank: int, world: int) -> None:
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
     k4_gbs = 16 * N / (statistics.mean(k4) / 1e3) / 1e9
     traffic = ENERGY_TRAFFIC.get((args.workload, args.L, args.precision))
+    if args.precision == "fp32":
+        roofline = {"bound": "alu", "kernel": "spectral energy (fused local DFT, projections, mean)",
+                    "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                    "traffic": traffic[0] if traffic else None,
+                    "traffic_source": traffic[1] if traffic else None,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
+                                   f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
+                    "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]],
+                    # the same time against the operation count of the unfolded separable DFT
+                    # (L^2 + 4 n_mu L^2 (1 + L) + 5 n_mu L^2 MACs per voxel): how far the folding
+                    # and the sliding recurrences moved the path past that method's ALU bound
+                    "direct_method_flops_per_voxel": direct_fpv,
+                    "direct_method_equivalent_tflops": direct_fpv * N / (k1_ms / 1e3) / 1e12}
+    else:
+        # stage y as tensor-core products: the contraction it stands for is the length-L DFT of
+        # every window of the n_mu L lines (4 n_mu L^3 real MACs per voxel), against the dense
+        # peak of the operand type (BF16 measured; TF32 = BF16 x the nominal 1.1 / 2.25)
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        tc_peak = bf16 if args.precision == "bf16" else bf16 * 1.1 / 2.25
+        tc_fpv = 2 * 4 * n_mu * args.L ** 3
+        tc_achieved = tc_fpv * N / (k1_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "spectral energy with stage y on tcgen05 "
+                                                  f"({args.precision.upper()} operands, FP32 accumulation)",
+                    "achieved": tc_achieved, "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_achieved / tc_peak,
+                    "traffic": None, "traffic_source": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" +
+                                   ("" if args.precision == "bf16" else " x 1.1 / 2.25 (nominal TF32 / BF16)"),
+                    "flops_per_voxel": tc_fpv,
+                    "note": "the CUDA-core part (stages t and x, |F| of every frequency, the weights) "
+                            "bounds this kernel, not the products",
+                    "fp32_algorithm_tflops": achieved}
     out = {
         "metric": "saliency voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision], "data": "synthetic",
         "config": workload_config(args),
-        "roofline": {"bound": "alu", "kernel": "spectral energy (fused local DFT, projections, mean)",
-                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                     "traffic": traffic[0] if traffic else None,
-                     "traffic_source": traffic[1] if traffic else None,
-                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
-                                    f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
-                     "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]],
-                     # the same time against the operation count of the unfolded separable DFT
-                     # (L^2 + 4 n_mu L^2 (1 + L) + 5 n_mu L^2 MACs per voxel): how far the folding
-                     # and the sliding recurrences moved the path past that method's ALU bound
-                     "direct_method_flops_per_voxel": direct_fpv,
-                     "direct_method_equivalent_tflops": direct_fpv * N / (k1_ms / 1e3) / 1e12},
+        "roofline": roofline,
         "kernels_ms": {"spectral_energy": k1_ms, "directional_compare_and_stats": statistics.mean(k2),
                        "combine": statistics.mean(k4)},
         "hbm_stages": {"directional_compare_GBs": k2_gbs, "combine_GBs": k4_gbs, "peak_GBs": hbm,
