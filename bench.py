@@ -136,6 +136,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, dist_mod, device) -> float:
+    """The slowest rank's time: the job's step ends when its last rank ends (an all-reduce MAX
+    of one FP64 value; `device` is the backend's device, a GPU for NCCL, the CPU for gloo)."""
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed (each rank its own, weak scaling)
+    per second of the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -251,9 +267,7 @@ def run_batch(args, rank: int, world: int) -> None:
         torch.cuda.synchronize(dev)
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     # end to end: host volumes in, host saliency maps out, through the public batched call
     Vh = [torch.from_numpy(v).pin_memory() for v in vols]
     Sh = [torch.empty(v.shape, dtype=torch.float32).pin_memory() for v in vols]
@@ -278,14 +292,16 @@ def run_batch(args, rank: int, world: int) -> None:
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     g.close()
+    if world > 1:
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     if rank != 0:
         return
-    out = {"metric": "saliency voxels/s", "value": world * nvox / (ms / 1e3), "unit": "voxels/s", "n_gpus": world,
+    out = {"metric": "saliency voxels/s", "value": job_rate(world, nvox, ms), "unit": "voxels/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.precision], "data": "synthetic",
            "config": workload_config(args), "autotune_choice": choice,
-           "e2e": {"value": world * nvox / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": 4 * nvox,
+           "e2e": {"value": job_rate(world, nvox, e2e_ms), "unit": "voxels/s", "h2d_bytes_per_step": 4 * nvox,
                    "d2h_bytes_per_step": 4 * nvox, "ms_per_step": e2e_ms},
            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
@@ -548,10 +564,8 @@ def run_ours(args, rank: int, world: int) -> None:
     total_ms = evs[0][0].elapsed_time(evs[-1][3])
     ms = total_ms / args.steps
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N / (ms / 1e3)
+        ms = max_over_ranks(ms, dist, dev)
+    value = job_rate(world, N, ms)
 
     # end to end through the public C-ABI call on HOST buffers: sal_saliency_host copies the
     # pinned V in, runs the path and copies S back into pinned host memory; successive calls
@@ -584,9 +598,7 @@ def run_ours(args, rank: int, world: int) -> None:
     api.sal_host_release(ws_host)
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     if rank != 0:
         return
@@ -647,7 +659,7 @@ def run_ours(args, rank: int, world: int) -> None:
         "hbm_stages": {"directional_compare_GBs": k2_gbs, "combine_GBs": k4_gbs, "peak_GBs": hbm,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
                        "bytes_per_voxel": {"directional_compare": 24, "combine": 16}},
-        "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": 4 * N,
+        "e2e": {"value": job_rate(world, N, e2e_ms), "unit": "voxels/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": e2e_ms},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
