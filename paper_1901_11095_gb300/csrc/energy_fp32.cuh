@@ -56,6 +56,9 @@ struct EGeo {
     static constexpr int NALIAS = (NV * 4 > NG2 * 8) ? NV : NG2 * 2;
     static constexpr int NW = ((H + 1) * (H + 1) * (H + 1) * 3 + 3) / 4 * 4;   // projection weights
     static constexpr int NZ = R + 2 * H;                // window of one thread's R outputs
+    // mu > 0 pairs (+nu, -nu) interleaved in G2 and walked as transposed pairs (fewer
+    // instructions; above L = 11 the extra live state costs more than it saves)
+    static constexpr bool PAIR4 = L_ <= 11;
     // batched modes: G2 lines [s][row][y'] (s = 0: +|nu|, 1: -|nu|), row stride = PY2 float2
     static constexpr int NG2B = 2 * ROWS * PY2;         // float2
     static constexpr int NG1M = BT * HX * 2 * PY;       // floats: [(t, x')][re, im][y'] of one mu
@@ -330,6 +333,86 @@ __device__ __forceinline__ void line_mags_strip2(const f2x (&Za)[NZ], const f2x 
     }
 }
 
+// The +nu and -nu lines of a pair walked together in transposed pairs: X = (Re line +nu,
+// Re line -nu), Y = (Im line +nu, Im line -nu) of every sample and every recurrence state, so
+// that one packed multiply and one packed FMA give the squared magnitudes of both lines.
+// m[w] = |F+(w)| + |F+(-w)| + |F-(w)| + |F-(-w)| (m[0]: the two DC terms), summed in the order
+// (|F+(w)| + |F+(-w)|) + (|F-(w)| + |F-(-w)|).
+template <int L, int NZ>
+struct PairWalk {
+    static constexpr int H = (L - 1) / 2;
+    f2x X[L], Y[L];   // Q_r(w) of both lines at [H + w], w = -H..H
+
+    __device__ __forceinline__ static void mags(f2x xp, f2x yp, f2x xm, f2x ym, float &m)
+    {
+        const f2x qp = fma2(yp, yp, mul2(xp, xp)), qm = fma2(ym, ym, mul2(xm, xm));
+        m = (sqrt_approx(lo(qp)) + sqrt_approx(lo(qm))) + (sqrt_approx(hi(qp)) + sqrt_approx(hi(qm)));
+    }
+    __device__ __forceinline__ static float mag0(f2x x, f2x y)
+    {
+        const f2x q = fma2(y, y, mul2(x, x));
+        return sqrt_approx(lo(q)) + sqrt_approx(hi(q));
+    }
+
+    __device__ __forceinline__ void start(const f2x (&ZX)[NZ], const f2x (&ZY)[NZ], const Tw<L> &tw,
+                                          float (&m)[H + 1])
+    {
+        const f2x m2 = pk(-2.f, -2.f);
+        f2x UX[H + 1], UY[H + 1], DX[H + 1], DY[H + 1];
+        f2x sx = ZX[H], sy = ZY[H];
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            const f2x px = add2(ZX[H + k], ZX[H - k]), py = add2(ZY[H + k], ZY[H - k]);
+            sx = add2(sx, px);
+            sy = add2(sy, py);
+            UX[k] = fma2(ZX[H], m2, px);
+            UY[k] = fma2(ZY[H], m2, py);
+            DX[k] = sub2(ZX[H + k], ZX[H - k]);
+            DY[k] = sub2(ZY[H + k], ZY[H - k]);
+        }
+        X[H] = sx;
+        Y[H] = sy;
+        m[0] = mag0(sx, sy);
+#pragma unroll
+        for (int w = 1; w <= H; ++w) {
+            f2x ax = mul2(UX[1], tw.c2[w % L]), ay = mul2(UY[1], tw.c2[w % L]);
+            f2x bx = mul2(DX[1], tw.s2[w % L]), by = mul2(DY[1], tw.s2[w % L]);
+#pragma unroll
+            for (int k = 2; k <= H; ++k) {
+                ax = fma2(UX[k], tw.c2[(w * k) % L], ax);
+                ay = fma2(UY[k], tw.c2[(w * k) % L], ay);
+                bx = fma2(DX[k], tw.s2[(w * k) % L], bx);
+                by = fma2(DY[k], tw.s2[(w * k) % L], by);
+            }
+            X[H + w] = add2(ax, by);   // F(+w) = A - iB
+            Y[H + w] = sub2(ay, bx);
+            X[H - w] = sub2(ax, by);   // F(-w) = A + iB
+            Y[H - w] = add2(ay, bx);
+            mags(X[H + w], Y[H + w], X[H - w], Y[H - w], m[w]);
+        }
+    }
+
+    // window r + 1 from window r (r a compile-time constant once unrolled): each state gains
+    // d e^{-i th k} = (dX c + dY s, dY c - dX s)
+    __device__ __forceinline__ void step(const f2x (&ZX)[NZ], const f2x (&ZY)[NZ], const Tw<L> &tw, int r,
+                                         float (&m)[H + 1])
+    {
+        const f2x dx = sub2(ZX[r + 2 * H + 1], ZX[r]), dy = sub2(ZY[r + 2 * H + 1], ZY[r]);
+        X[H] = add2(X[H], dx);
+        Y[H] = add2(Y[H], dy);
+#pragma unroll
+        for (int w = -H; w <= H; ++w) {
+            if (w == 0) continue;
+            const int k = tw_index<L>(w, r - H), kn = (L - k) % L;   // s2[kn] = -s2[k]
+            X[H + w] = fma2(dy, tw.s2[k], fma2(dx, tw.c2[k], X[H + w]));
+            Y[H + w] = fma2(dx, tw.s2[kn], fma2(dy, tw.c2[k], Y[H + w]));
+        }
+        m[0] = mag0(X[H], Y[H]);
+#pragma unroll
+        for (int w = 1; w <= H; ++w) mags(X[H + w], Y[H + w], X[H - w], Y[H - w], m[w]);
+    }
+};
+
 // The same for the real mu = 0, nu = 0 line: put(r, w, |F_r(w)|) for w = 1..H only (the -w
 // point is the conjugate mirror, counted by the half-spectrum factor; w = 0 is the DC term).
 template <int L, int R, int NZ, class Put>
@@ -440,6 +523,35 @@ __device__ __forceinline__ void y_pair(const float2 *lp, const float2 *lm, int j
     line_mags_strip2<G::L, G::R>(Zp, Zm, tw, [&](int r, int om, float mp, float mm) {
         wsum(w[om], mp + mm, et[r], ex[r], ey[r]);   // |F(+nu)| + |F(-nu)| share the weights
     });
+}
+
+// The +nu and -nu lines of one mu > 0 as stage x interleaves them (a float4 per column:
+// Re +nu, Re -nu, Im +nu, Im -nu), which share their weights.
+template <class G>
+__device__ __forceinline__ void y_pair4(const float4 *line, int j, int mu, int nu, const float *sW,
+                                        const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+{
+    float w[G::H + 1][3];
+    load_w<G>(sW, mu, nu, w);
+    f2x ZX[G::NZ], ZY[G::NZ];
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(line + G::R * j);
+#pragma unroll
+    for (int n = 0; n < G::NZ; ++n) {
+        const ulonglong2 v = p[n];
+        ZX[n] = v.x;
+        ZY[n] = v.y;
+    }
+    PairWalk<G::L, G::NZ> pw;
+    float m[G::H + 1];
+    pw.start(ZX, ZY, tw, m);
+#pragma unroll
+    for (int om = 0; om <= G::H; ++om) wsum(w[om], m[om], et[0], ex[0], ey[0]);
+#pragma unroll
+    for (int r = 0; r + 1 < G::R; ++r) {
+        pw.step(ZX, ZY, tw, r, m);
+#pragma unroll
+        for (int om = 0; om <= G::H; ++om) wsum(w[om], m[om], et[r + 1], ex[r + 1], ey[r + 1]);
+    }
 }
 
 // The real mu = 0, nu = 0 line, omega > 0 only.
@@ -584,7 +696,60 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
                     orow[nu * G::PY2] = make_float2(pr[nu], pi[nu]);
                 }
             }
+        } else if constexpr (G::PAIR4) {
+            // mu > 0: row = [line nu = 0: PY2 float2][pair |nu| = 1..H: PY2 float4 each], a pair
+            // column holding (Re G2(+nu), Re G2(-nu), Im G2(+nu), Im G2(-nu)) so that stage y
+            // reads both lines of a pair with one 128-bit load, already transposed
+            const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
+            const f2x m2 = pk(-2.f, -2.f);
+            f2x z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = pk(g[n * XS + cre], g[n * XS + cim]);
+            const f2x z0 = z[H];
+            f2x sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const f2x p = add2(z[H + k], z[H - k]);
+                sum = add2(sum, p);
+                U[k] = fma2(z0, m2, p);
+                D[k] = sub2(z[H + k], z[H - k]);
+            }
+            f2x *o2 = reinterpret_cast<f2x *>(sG2 + (t * BX) * RS) + yy;              // line nu = 0, row x = 0
+            float4 *o4 = reinterpret_cast<float4 *>(sG2 + (t * BX) * RS + G::PY2) + yy;   // pair 1, row x = 0
+            o2[0] = sum;
+            f2x Pp[H + 1], Pm[H + 1];   // P(+nu), P(-nu)
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                f2x A = mul2(U[1], tw.c2[nu % L]);
+                f2x B = mul2(D[1], tw.s2[nu % L]);
+#pragma unroll
+                for (int k = 2; k <= H; ++k) {
+                    A = fma2(U[k], tw.c2[(nu * k) % L], A);
+                    B = fma2(D[k], tw.s2[(nu * k) % L], B);
+                }
+                const float ax = lo(A), ay = hi(A), bx = lo(B), by = hi(B);
+                const f2x Fp = pk(ax + by, ay - bx);   // F_0(+nu) = A - iB
+                const f2x Fm = pk(ax - by, ay + bx);   // F_0(-nu) = A + iB
+                o4[(nu - 1) * G::PY2] = make_float4(lo(Fp), lo(Fm), hi(Fp), hi(Fm));
+                Pp[nu] = Fp;
+                Pm[nu] = Fm;
+            }
+#pragma unroll
+            for (int r = 1; r < BX; ++r) {
+                const f2x d = sub2(z[r + 2 * H], z[r - 1]);
+                const f2x dsw = swapneg(d);
+                sum = add2(sum, d);
+                o2[r * RS] = sum;
+#pragma unroll
+                for (int nu = 1; nu <= H; ++nu) {
+                    const int k = tw_index<L>(nu, r - 1 - H);
+                    Pp[nu] = rot_acc<L>(Pp[nu], d, dsw, tw, k);
+                    Pm[nu] = rot_acc<L>(Pm[nu], d, dsw, tw, (L - k) % L);
+                    o4[r * (RS / 2) + (nu - 1) * G::PY2] = make_float4(lo(Pp[nu]), lo(Pm[nu]), hi(Pp[nu]), hi(Pm[nu]));
+                }
+            }
         } else {
+            // mu > 0, lines nu = -H..H at slot H + nu
             const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
             const f2x m2 = pk(-2.f, -2.f);
             f2x z[NZX];
@@ -792,12 +957,19 @@ __device__ __forceinline__ void y_stage_mu(const float2 *sG2, int row, int j, in
                                            float (&ey)[G::R])
 {
     constexpr int L = G::L, H = G::H;
-    const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
     if (mu == 0) {
+        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
         y_real<G>(l0, j, sW, tw, et, ex, ey);
 #pragma unroll 1
         for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
+    } else if constexpr (G::PAIR4) {
+        const float2 *l0 = sG2 + row * L * G::PY2;         // line nu = 0, then the pairs |nu| = 1..H
+        y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
+        const float4 *l4 = reinterpret_cast<const float4 *>(l0 + G::PY2);
+#pragma unroll 1
+        for (int nu = 1; nu <= H; ++nu) y_pair4<G>(l4 + (nu - 1) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
     } else {
+        const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
         y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
 #pragma unroll 1
         for (int nu = 1; nu <= H; ++nu) y_pair<G>(l0 + nu * G::PY2, l0 - nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
