@@ -59,6 +59,9 @@ struct EGeo {
     // mu > 0 pairs (+nu, -nu) interleaved in G2 and walked as transposed pairs (fewer
     // instructions; above L = 11 the extra live state costs more than it saves)
     static constexpr bool PAIR4 = L_ <= 11;
+    // mu = 0: the single lines nu = 1, 2 (3, 4, ...) stored and walked as pairs too (measured:
+    // L = 9 -2 %, L = 11 unchanged, L = 5 and 7 slower, their extra live state not paid back)
+    static constexpr bool PAIR0 = L_ == 9 || L_ == 11;
     // batched modes: G2 lines [s][row][y'] (s = 0: +|nu|, 1: -|nu|), row stride = PY2 float2
     static constexpr int NG2B = 2 * ROWS * PY2;         // float2
     static constexpr int NG1M = BT * HX * 2 * PY;       // floats: [(t, x')][re, im][y'] of one mu
@@ -333,29 +336,30 @@ __device__ __forceinline__ void line_mags_strip2(const f2x (&Za)[NZ], const f2x 
     }
 }
 
-// The +nu and -nu lines of a pair walked together in transposed pairs: X = (Re line +nu,
-// Re line -nu), Y = (Im line +nu, Im line -nu) of every sample and every recurrence state, so
-// that one packed multiply and one packed FMA give the squared magnitudes of both lines.
-// m[w] = |F+(w)| + |F+(-w)| + |F-(w)| + |F-(-w)| (m[0]: the two DC terms), summed in the order
-// (|F+(w)| + |F+(-w)|) + (|F-(w)| + |F-(-w)|).
+// Two lines a, b walked together in transposed pairs: X = (Re a, Re b), Y = (Im a, Im b) of
+// every sample and every recurrence state, so that one packed multiply and one packed FMA give
+// the squared magnitudes of both lines.  Per line: ma[w] = |Fa(w)| + |Fa(-w)|, ma[0] = |Fa(0)|
+// (and mb for line b).
 template <int L, int NZ>
 struct PairWalk {
     static constexpr int H = (L - 1) / 2;
     f2x X[L], Y[L];   // Q_r(w) of both lines at [H + w], w = -H..H
 
-    __device__ __forceinline__ static void mags(f2x xp, f2x yp, f2x xm, f2x ym, float &m)
+    __device__ __forceinline__ static void mags(f2x xp, f2x yp, f2x xm, f2x ym, float &ma, float &mb)
     {
         const f2x qp = fma2(yp, yp, mul2(xp, xp)), qm = fma2(ym, ym, mul2(xm, xm));
-        m = (sqrt_approx(lo(qp)) + sqrt_approx(lo(qm))) + (sqrt_approx(hi(qp)) + sqrt_approx(hi(qm)));
+        ma = sqrt_approx(lo(qp)) + sqrt_approx(lo(qm));
+        mb = sqrt_approx(hi(qp)) + sqrt_approx(hi(qm));
     }
-    __device__ __forceinline__ static float mag0(f2x x, f2x y)
+    __device__ __forceinline__ static void mag0(f2x x, f2x y, float &ma, float &mb)
     {
         const f2x q = fma2(y, y, mul2(x, x));
-        return sqrt_approx(lo(q)) + sqrt_approx(hi(q));
+        ma = sqrt_approx(lo(q));
+        mb = sqrt_approx(hi(q));
     }
 
     __device__ __forceinline__ void start(const f2x (&ZX)[NZ], const f2x (&ZY)[NZ], const Tw<L> &tw,
-                                          float (&m)[H + 1])
+                                          float (&ma)[H + 1], float (&mb)[H + 1])
     {
         const f2x m2 = pk(-2.f, -2.f);
         f2x UX[H + 1], UY[H + 1], DX[H + 1], DY[H + 1];
@@ -372,7 +376,7 @@ struct PairWalk {
         }
         X[H] = sx;
         Y[H] = sy;
-        m[0] = mag0(sx, sy);
+        mag0(sx, sy, ma[0], mb[0]);
 #pragma unroll
         for (int w = 1; w <= H; ++w) {
             f2x ax = mul2(UX[1], tw.c2[w % L]), ay = mul2(UY[1], tw.c2[w % L]);
@@ -388,14 +392,14 @@ struct PairWalk {
             Y[H + w] = sub2(ay, bx);
             X[H - w] = sub2(ax, by);   // F(-w) = A + iB
             Y[H - w] = add2(ay, bx);
-            mags(X[H + w], Y[H + w], X[H - w], Y[H - w], m[w]);
+            mags(X[H + w], Y[H + w], X[H - w], Y[H - w], ma[w], mb[w]);
         }
     }
 
     // window r + 1 from window r (r a compile-time constant once unrolled): each state gains
     // d e^{-i th k} = (dX c + dY s, dY c - dX s)
     __device__ __forceinline__ void step(const f2x (&ZX)[NZ], const f2x (&ZY)[NZ], const Tw<L> &tw, int r,
-                                         float (&m)[H + 1])
+                                         float (&ma)[H + 1], float (&mb)[H + 1])
     {
         const f2x dx = sub2(ZX[r + 2 * H + 1], ZX[r]), dy = sub2(ZY[r + 2 * H + 1], ZY[r]);
         X[H] = add2(X[H], dx);
@@ -407,9 +411,9 @@ struct PairWalk {
             X[H + w] = fma2(dy, tw.s2[k], fma2(dx, tw.c2[k], X[H + w]));
             Y[H + w] = fma2(dx, tw.s2[kn], fma2(dy, tw.c2[k], Y[H + w]));
         }
-        m[0] = mag0(X[H], Y[H]);
+        mag0(X[H], Y[H], ma[0], mb[0]);
 #pragma unroll
-        for (int w = 1; w <= H; ++w) mags(X[H + w], Y[H + w], X[H - w], Y[H - w], m[w]);
+        for (int w = 1; w <= H; ++w) mags(X[H + w], Y[H + w], X[H - w], Y[H - w], ma[w], mb[w]);
     }
 };
 
@@ -542,15 +546,50 @@ __device__ __forceinline__ void y_pair4(const float4 *line, int j, int mu, int n
         ZY[n] = v.y;
     }
     PairWalk<G::L, G::NZ> pw;
-    float m[G::H + 1];
-    pw.start(ZX, ZY, tw, m);
+    float ma[G::H + 1], mb[G::H + 1];   // |F(+nu)| and |F(-nu)| terms, summed in that order
+    pw.start(ZX, ZY, tw, ma, mb);
 #pragma unroll
-    for (int om = 0; om <= G::H; ++om) wsum(w[om], m[om], et[0], ex[0], ey[0]);
+    for (int om = 0; om <= G::H; ++om) wsum(w[om], ma[om] + mb[om], et[0], ex[0], ey[0]);
 #pragma unroll
     for (int r = 0; r + 1 < G::R; ++r) {
-        pw.step(ZX, ZY, tw, r, m);
+        pw.step(ZX, ZY, tw, r, ma, mb);
 #pragma unroll
-        for (int om = 0; om <= G::H; ++om) wsum(w[om], m[om], et[r + 1], ex[r + 1], ey[r + 1]);
+        for (int om = 0; om <= G::H; ++om) wsum(w[om], ma[om] + mb[om], et[r + 1], ex[r + 1], ey[r + 1]);
+    }
+}
+
+// Two single lines (mu, nua) and (mu, nub) stored interleaved like a pair (Re a, Re b, Im a,
+// Im b per column), each with its own weights (line a's terms first in every output).
+template <class G>
+__device__ __forceinline__ void y_single_pair4(const float4 *line, int j, int mu, int nua, int nub, const float *sW,
+                                               const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R],
+                                               float (&ey)[G::R])
+{
+    float wa[G::H + 1][3], wb[G::H + 1][3];
+    load_w<G>(sW, mu, nua, wa);
+    load_w<G>(sW, mu, nub, wb);
+    f2x ZX[G::NZ], ZY[G::NZ];
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(line + G::R * j);
+#pragma unroll
+    for (int n = 0; n < G::NZ; ++n) {
+        const ulonglong2 v = p[n];
+        ZX[n] = v.x;
+        ZY[n] = v.y;
+    }
+    PairWalk<G::L, G::NZ> pw;
+    float ma[G::H + 1], mb[G::H + 1];
+    pw.start(ZX, ZY, tw, ma, mb);
+#pragma unroll
+    for (int om = 0; om <= G::H; ++om) wsum(wa[om], ma[om], et[0], ex[0], ey[0]);
+#pragma unroll
+    for (int om = 0; om <= G::H; ++om) wsum(wb[om], mb[om], et[0], ex[0], ey[0]);
+#pragma unroll
+    for (int r = 0; r + 1 < G::R; ++r) {
+        pw.step(ZX, ZY, tw, r, ma, mb);
+#pragma unroll
+        for (int om = 0; om <= G::H; ++om) wsum(wa[om], ma[om], et[r + 1], ex[r + 1], ey[r + 1]);
+#pragma unroll
+        for (int om = 0; om <= G::H; ++om) wsum(wb[om], mb[om], et[r + 1], ex[r + 1], ey[r + 1]);
     }
 }
 
@@ -655,7 +694,54 @@ __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int
         const int t = i / PY, yy = i - t * PY;
         const float *g = sG1 + (t * G::HX * L) * PY + yy;
         float2 *o = sG2 + ((t * BX) * L + H) * G::PY2 + yy;   // line nu = 0 of output row (t, x = 0)
-        if (mu == 0) {
+        if (mu == 0 && G::PAIR0) {
+            // real input, lines nu = 0..H; row = [nu = 0: PY2 float2][pairs (1, 2), (3, 4), ...:
+            // PY2 float4 each, (Re a, Re b, Im a, Im b)][nu = H alone when H is odd: PY2 float2]
+            float z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
+            const float z0 = z[H];
+            float sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const float p = z[H + k] + z[H - k];
+                sum += p;
+                U[k] = fmaf(-2.f, z0, p);
+                D[k] = z[H + k] - z[H - k];
+            }
+            float2 *r0 = sG2 + (t * BX) * RS + yy;
+            float4 *q0 = reinterpret_cast<float4 *>(sG2 + (t * BX) * RS + G::PY2) + yy;
+            float pr[H + 1], pi[H + 1];
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                float A = 0.f, B = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
+                    B = fmaf(D[k], lo(tw.s2[(nu * k) % L]), B);
+                }
+                pr[nu] = A;   // F_0(nu) = A - iB = Q_0(nu)
+                pi[nu] = -B;
+            }
+#pragma unroll
+            for (int r = 0; r < BX; ++r) {
+                if (r > 0) {
+                    const float d = z[r + 2 * H] - z[r - 1];
+                    sum += d;
+#pragma unroll
+                    for (int nu = 1; nu <= H; ++nu) {
+                        const int k = tw_index<L>(nu, r - 1 - H);
+                        pr[nu] = fmaf(d, lo(tw.c2[k]), pr[nu]);    // + d e^{-i th k}
+                        pi[nu] = fmaf(-d, lo(tw.s2[k]), pi[nu]);
+                    }
+                }
+                r0[r * RS] = make_float2(sum, 0.f);
+#pragma unroll
+                for (int q = 0; q < H / 2; ++q)
+                    q0[r * (RS / 2) + q * G::PY2] = make_float4(pr[2 * q + 1], pr[2 * q + 2], pi[2 * q + 1], pi[2 * q + 2]);
+                if (H & 1) r0[r * RS + H * G::PY2] = make_float2(pr[H], pi[H]);
+            }
+        } else if (mu == 0) {
             float z[NZX];
 #pragma unroll
             for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
@@ -957,7 +1043,14 @@ __device__ __forceinline__ void y_stage_mu(const float2 *sG2, int row, int j, in
                                            float (&ey)[G::R])
 {
     constexpr int L = G::L, H = G::H;
-    if (mu == 0) {
+    if (mu == 0 && G::PAIR0) {
+        const float2 *l0 = sG2 + row * L * G::PY2;         // nu = 0, the pairs (1, 2), ..., nu = H if odd
+        y_real<G>(l0, j, sW, tw, et, ex, ey);
+        const float4 *l4 = reinterpret_cast<const float4 *>(l0 + G::PY2);
+#pragma unroll 1
+        for (int q = 0; q < H / 2; ++q) y_single_pair4<G>(l4 + q * G::PY2, j, 0, 2 * q + 1, 2 * q + 2, sW, tw, et, ex, ey);
+        if (H & 1) y_single<G>(l0 + H * G::PY2, j, 0, H, sW, tw, et, ex, ey);
+    } else if (mu == 0) {
         const float2 *l0 = sG2 + (row * L + H) * G::PY2;   // line nu = 0 of this row
         y_real<G>(l0, j, sW, tw, et, ex, ey);
 #pragma unroll 1
