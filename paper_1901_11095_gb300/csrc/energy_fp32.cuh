@@ -683,7 +683,11 @@ __device__ __forceinline__ void x_stage(const float *sG1, float2 *sG2, int mu, c
 // Q_r(nu) = Q_{r-1}(nu) + (z[r+2h] - z[r-1]) e^{-i th nu (r-1-h)} with Q_0 = F_0, so that
 // Q_r(nu) = e^{-i th nu r} F_r(nu).  That unit factor depends on (nu, x) only, the same for
 // every y' of a G2 line, so the y transform carries it unchanged into F and |F| does not
-// see it.  mu = 0 (real input) writes lines nu = 0..h.
+// see it.  mu = 0 (real input) writes lines nu = 0..h.  Layout of a G2 row (L x PY2 float2):
+// modes 0 and 3 with PAIR4 (L <= 11) put the line nu = 0 first and then, for mu > 0, each
+// pair (+nu, -nu) as PY2 float4 columns (Re +nu, Re -nu, Im +nu, Im -nu); with PAIR0 (L = 9,
+// 11) the mu = 0 lines nu = 1, 2 (3, 4, ...) are paired the same way and an odd last line
+// follows alone; otherwise line nu sits at slot h + nu.
 template <class G>
 __device__ __forceinline__ void x_stage_slide(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
 {
