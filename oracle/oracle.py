@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "sal_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 REFLECT, PERIODIC = 0, 1
-STENCIL_26, STENCIL_LINE = 0, 1
+STENCIL_26, STENCIL_LINE, STENCIL_DIAG_TX = 0, 1, 2
 
 _lib = None
 
@@ -65,6 +65,9 @@ def _load():
         lib.oracle_maps_at.restype = I_
         lib.oracle_dcs.argtypes = [f64p, L_, L_, L_, I_, I_, I_, D_, I_, f64p]
         lib.oracle_dcs.restype = I_
+        ip_ = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_dcs_user.argtypes = [f64p, L_, L_, L_, I_, ip_, ip_, f64p, I_, I_, f64p]
+        lib.oracle_dcs_user.restype = I_
         lib.oracle_stats.argtypes = [f64p, L_, f64p]
         lib.oracle_stats.restype = None
         lib.oracle_combine.argtypes = [f64p, f64p, L_, D_, D_, D_, D_, f64p]
@@ -180,6 +183,29 @@ def dcs(E, bnd=REFLECT, stencil=STENCIL_26, L=7, sigma=1.0, threads=None) -> np.
     rc = _load().oracle_dcs(ep, *shape, bnd, stencil, L, float(sigma), threads or default_threads(), op)
     if rc:
         raise ValueError(f"oracle_dcs failed ({rc})")
+    return out
+
+
+def dcs_user(E, offsets, weights, bnd=REFLECT, threads=None) -> np.ndarray:
+    """Eq. 5 with caller-given neighbourhoods: offsets[m] is a list of (dt, dx, dy), weights[m]
+    the matching weights; S_m = mean over k of |E_m - w_k E_m(v + o_k)|."""
+    E, ep = _f64(E)
+    shape = E.shape[1:]
+    qmax = max(len(o) for o in offsets)
+    off = np.zeros((3, qmax, 3), dtype=np.intc)
+    w = np.zeros((3, qmax))
+    Q = np.zeros(3, dtype=np.intc)
+    for m in range(3):
+        Q[m] = len(offsets[m])
+        off[m, :Q[m]] = np.asarray(offsets[m], dtype=np.intc).reshape(-1, 3)
+        w[m, :Q[m]] = weights[m]
+    w, wp = _f64(w)
+    ip = ctypes.POINTER(ctypes.c_int)
+    out, op = _f64(np.zeros(E.shape))
+    rc = _load().oracle_dcs_user(ep, *shape, bnd, Q.ctypes.data_as(ip), off.ctypes.data_as(ip), wp, qmax,
+                                 threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_dcs_user failed ({rc})")
     return out
 
 

@@ -21,7 +21,11 @@
  *  R6  Eq. 5 is taken literally, w on the neighbour inside |.|, with Gaussian weights
  *      g(o) = exp(-|o|^2 / (2 sigma^2)); E outside the volume uses the same extension;
  *  R7  neighbourhoods: the 26 voxels around the centre (Q = 26), or the paper's d x 1
- *      line of side d = L along axis m for map m (offsets +-1..+-h, Q = L - 1);
+ *      line of side d = L along axis m for map m (offsets +-1..+-h, Q = L - 1), or the
+ *      d x 1 line along the t-x diagonal of Fig. 3 for every map (offsets (k, k, 0),
+ *      k = +-1..+-h, Q = L - 1), or a caller-given list of offsets with explicit weights
+ *      per map (the text after Eq. 5 lets orientation, size and weights be tuned; Q is the
+ *      number of offsets);
  *  R8  before Eq. 6 each S_m is min-max normalised with global min and max; a map whose
  *      range hi - lo <= eps * max(|hi|, |lo|) is treated as constant and becomes 0.
  */
@@ -34,6 +38,7 @@
 #define ORC_PERIODIC 1
 #define ORC_STENCIL_26 0
 #define ORC_STENCIL_LINE 1
+#define ORC_STENCIL_DIAG_TX 2
 
 static const double ORC_PI = 3.14159265358979323846264338327950288;
 
@@ -324,6 +329,15 @@ static int neighbourhood(int stencil, int m, int L, int off[][3])
                     if (a == 0 && b == 0 && c == 0) continue;
                     off[Q][0] = a; off[Q][1] = b; off[Q][2] = c; ++Q;
                 }
+    } else if (stencil == ORC_STENCIL_DIAG_TX) {
+        int h = (L - 1) / 2;
+        for (int k = -h; k <= h; ++k) {
+            if (k == 0) continue;
+            off[Q][0] = k;
+            off[Q][1] = k;
+            off[Q][2] = 0;
+            ++Q;
+        }
     } else {
         int h = (L - 1) / 2;
         for (int k = -h; k <= h; ++k) {
@@ -369,6 +383,41 @@ int oracle_dcs(const double *E, long T, long X, long Y, int bnd, int stencil, in
                         s += fabs(c - g[k] * Em[(tn * X + xn) * Y + yn]);
                     }
                     Sm[m * N + (t * X + x) * Y + y] = s / (double)Q;
+                }
+    }
+    return 0;
+}
+
+/*
+ * Eq. 5 with a caller-given neighbourhood per map (reading R7, user stencils):
+ *   S_m[v] = Q_m^-1 sum_{k < Q_m} | E_m[v] - w_m[k] E_m[v + o_m[k]] |
+ * off is [3][qmax][3] (dt, dx, dy), w is [3][qmax], Q[m] the number of offsets of map m.
+ * E outside the volume comes from the boundary extension, as for the built-in stencils.
+ */
+int oracle_dcs_user(const double *E, long T, long X, long Y, int bnd, const int *Q, const int *off,
+                    const double *w, int qmax, int nthreads, double *Sm)
+{
+    if (T < 1 || X < 1 || Y < 1 || qmax < 1) return -1;
+    for (int m = 0; m < 3; ++m)
+        if (Q[m] < 1 || Q[m] > qmax) return -1;
+    long N = T * X * Y;
+    for (int m = 0; m < 3; ++m) {
+        const double *Em = E + m * N;
+        const int *o = off + (long)m * qmax * 3;
+        const double *wm = w + (long)m * qmax;
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1)
+        for (long t = 0; t < T; ++t)
+            for (long x = 0; x < X; ++x)
+                for (long y = 0; y < Y; ++y) {
+                    double c = Em[(t * X + x) * Y + y];
+                    double s = 0.0;
+                    for (int k = 0; k < Q[m]; ++k) {
+                        long tn = orc_ext_index(t + o[3 * k], T, bnd);
+                        long xn = orc_ext_index(x + o[3 * k + 1], X, bnd);
+                        long yn = orc_ext_index(y + o[3 * k + 2], Y, bnd);
+                        s += fabs(c - wm[k] * Em[(tn * X + xn) * Y + yn]);
+                    }
+                    Sm[m * N + (t * X + x) * Y + y] = s / (double)Q[m];
                 }
     }
     return 0;
