@@ -37,8 +37,8 @@ WORKLOADS = {
     "slab": ((462, 951, 160), "f3", 1),     # a profiling case: the F3 shape cut to 160 inlines
     "batch64": (None, "basic", 0),           # 64 volumes, every axis U[32, 192], seeds 0..63
 }
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 sub-partitions x 32)
+MUFU_PER_SM_CLK = 16             # square roots per SM and clock on the XU (MUFU) pipe
 
 # DRAM bytes (read + write) of one spectral-energy launch, from one ncu capture of the same
 # kernel build (dram__bytes_read.sum + dram__bytes_write.sum on the 462 x 951 x 160 slab,
@@ -71,6 +71,46 @@ def algorithmic_flops_per_voxel(L: int, R: int = 4, BX: int = 8) -> float:
     pair_adds = H * H * (H + 1)
     y = (n_cl * cline + rline) / R + 6 * groups + pair_adds
     return real_pass + (x_real + H * x_cplx) + y + 3
+
+
+def mufu_per_voxel(L: int) -> int:
+    """Square roots (MUFU sqrt.approx) per voxel of the energy kernel: one per |F| of the half
+    spectrum it forms, (L^3 - 1) / 2 (algorithmic_flops_per_voxel counts each as one flop)."""
+    return (L ** 3 - 1) // 2
+
+
+def measure_fma_rate(dev, stream, seconds: float = 1.0) -> dict:
+    """Measured FP32 FMA rate of this GPU: the library's FMA-chain probe (scalar FFMA and
+    packed f32x2 forms), 2048 threads per SM, timed with CUDA events on `stream` over about
+    `seconds` with the SM clock sampled meanwhile.  TFLOP/s, FMA = 2 flops."""
+    import torch
+
+    from paper_1901_11095_gb300 import api
+
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.empty(nsm * 2048, device=dev, dtype=torch.float32)
+    iters = 1 << 15
+    res = {"sms": nsm, "threads": out.numel(), "iters": iters}
+    for packed in (False, True):
+        api.sal_probe_fma_rate(out, iters, packed, stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = api.sal_probe_fma_rate(out, iters, packed, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        reps = max(1, int(seconds / 2 / max(e0.elapsed_time(e1) / 1e3, 1e-6)))
+        with ClockSampler(dev.index) as clk:
+            e0.record(stream)
+            for _ in range(reps):
+                api.sal_probe_fma_rate(out, iters, packed, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        res["packed" if packed else "scalar"] = {"tflops": flops / (ms / 1e3) / 1e12, "ms": ms, "reps": reps,
+                                                 "clocks": clk.summary()}
+    res["tflops"] = max(res["scalar"]["tflops"], res["packed"]["tflops"])
+    return res
 
 
 def load_peaks() -> dict:
@@ -543,6 +583,8 @@ def run_ours(args, rank: int, world: int) -> None:
         if ev is not None:
             ev[3].record(stream)
 
+    # the measured FP32 FMA rate (denominator beside the derived peak), before the timed region
+    fma_probe = measure_fma_rate(dev, stream) if args.precision == "fp32" and not args.no_fma_probe else None
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -604,31 +646,52 @@ def run_ours(args, rank: int, world: int) -> None:
         return
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
     k1_ms = statistics.mean(k1)
     tile = api.sal_autotune_query(args.L, p.precision, N)     # the tile shape the launches used
     fpv = algorithmic_flops_per_voxel(args.L, BX=int(tile["bx"]))
-    flops = fpv * N
+    n_sqrt = mufu_per_voxel(args.L)
+    fma_fpv = fpv - n_sqrt                                    # flops on the FMA pipe (sqrt excluded)
     n_mu = (args.L + 1) // 2
     direct_fpv = 2 * (args.L ** 2 + 4 * n_mu * args.L ** 2 * (1 + args.L) + 5 * n_mu * args.L ** 2)
-    achieved = flops / (k1_ms / 1e3) / 1e12
+    achieved = fma_fpv * N / (k1_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
     k4_gbs = 16 * N / (statistics.mean(k4) / 1e3) / 1e9
     traffic = ENERGY_TRAFFIC.get((args.workload, args.L, args.precision))
     if args.precision == "fp32":
+        clk_sum = clk.summary()
+        mhz = clk_sum["sm_mhz"] or sm_max
+        xu_peak = nsm * MUFU_PER_SM_CLK * mhz * 1e6                  # square roots per second
         roofline = {"bound": "alu", "kernel": "spectral energy (fused local DFT, projections, mean)",
                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                     "traffic": traffic[0] if traffic else None,
                     "traffic_source": traffic[1] if traffic else None,
-                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
-                                   f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
-                    "flops_per_voxel": fpv, "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]],
+                    "peak_source": f"derived: {nsm} SMs (device properties) x {FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"2 flop/FMA x {sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)",
+                    "flops_per_voxel": fma_fpv,
+                    "flops_note": "FP32 flops of the kernel's own algorithm on the FMA pipe (FMA = 2); the "
+                                  f"{n_sqrt} square roots per voxel run on the XU pipe and are counted apart",
+                    "tile": [tile["bt"], tile["bx"], tile["by"], tile["mode"]],
+                    "xu": {"sqrt_per_voxel": n_sqrt, "achieved_per_s": n_sqrt * N / (k1_ms / 1e3),
+                           "peak_per_s": xu_peak, "frac": n_sqrt * N / (k1_ms / 1e3) / xu_peak,
+                           "peak_source": f"{nsm} SMs x {MUFU_PER_SM_CLK} per clock x {mhz:.0f} MHz "
+                                          "(median SM clock sampled in the timed region)"},
                     # the same time against the operation count of the unfolded separable DFT
-                    # (L^2 + 4 n_mu L^2 (1 + L) + 5 n_mu L^2 MACs per voxel): how far the folding
-                    # and the sliding recurrences moved the path past that method's ALU bound
+                    # (L^2 + 4 n_mu L^2 (1 + L) + 5 n_mu L^2 MACs per voxel): above 1, because the
+                    # folding and the sliding recurrences do that method's work with fewer flops
                     "direct_method_flops_per_voxel": direct_fpv,
-                    "direct_method_equivalent_tflops": direct_fpv * N / (k1_ms / 1e3) / 1e12}
+                    "direct_method_equivalent_tflops": direct_fpv * N / (k1_ms / 1e3) / 1e12,
+                    "frac_direct_count": direct_fpv * N / (k1_ms / 1e3) / 1e12 / alu_peak}
+        if fma_probe is not None:
+            roofline["measured_fma_peak"] = fma_probe["tflops"]
+            roofline["frac_of_measured_fma_peak"] = achieved / fma_probe["tflops"]
+            roofline["measured_fma_probe"] = {
+                "scalar_tflops": fma_probe["scalar"]["tflops"], "packed_tflops": fma_probe["packed"]["tflops"],
+                "sm_mhz": fma_probe["packed"]["clocks"]["sm_mhz"],
+                "how": f"sal_probe_fma_rate: {fma_probe['threads']} threads x {8} independent FMA chains x "
+                       f"{fma_probe['iters']} steps, CUDA events, about 0.5 s per form"}
     else:
         # stage y as tensor-core products: the contraction it stands for is the length-L DFT of
         # every window of the n_mu L lines (4 n_mu L^3 real MACs per voxel), against the dense
@@ -681,6 +744,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fma-probe", action="store_true", help="skip the FP32 FMA-rate probe")
+    ap.add_argument("--fma-probe", action="store_true", help="only run the FP32 FMA-rate probe (one JSON line)")
     ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
     ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and time its inference")
     ap.add_argument("--surrogate-forward", action="store_true",
@@ -701,6 +766,12 @@ def main():
     sys.path.insert(0, ROOT)
     import __graft_entry__
     __graft_entry__.build()
+    if args.fma_probe:
+        import torch
+        dev = torch.device("cuda:0")
+        print(json.dumps({"mode": "fp32 fma rate", **measure_fma_rate(dev, torch.cuda.current_stream(dev), 2.0)}),
+              flush=True)
+        return
     if args.sweep:
         run_sweep(args)
         return

@@ -62,8 +62,13 @@ typedef enum { SAL_PREC_FP32 = 0, SAL_PREC_TF32 = 1, SAL_PREC_BF16 = 2 } sal_pre
 typedef enum { SAL_BND_REFLECT = 0, SAL_BND_PERIODIC = 1 } sal_boundary;
 /* SAL_STENCIL_26: the 26 voxels around the centre (Q = 26).
  * SAL_STENCIL_LINE: the paper's d x 1 window of side d = L along axis m for map m
- * (offsets +-1..+-h, Q = L - 1), Sec. 2 text after Eq. 5. */
-typedef enum { SAL_STENCIL_26 = 0, SAL_STENCIL_LINE = 1 } sal_stencil;
+ * (offsets +-1..+-h, Q = L - 1), Sec. 2 text after Eq. 5.
+ * SAL_STENCIL_DIAG_TX: the d x 1 window of side d = L along the t-x diagonal (Fig. 3), the
+ * same for every map: offsets (k, k, 0), k = +-1..+-h, Q = L - 1, weights
+ * g = exp(-2 k^2 / (2 sigma^2)).
+ * Any other neighbourhood (orientation, size and weights tuned as the text after Eq. 5
+ * allows) goes through sal_directional_compare_user. */
+typedef enum { SAL_STENCIL_26 = 0, SAL_STENCIL_LINE = 1, SAL_STENCIL_DIAG_TX = 2 } sal_stencil;
 
 typedef struct { int64_t T, X, Y; } sal_dims;
 
@@ -133,6 +138,33 @@ SAL_API sal_status sal_directional_compare(const float *E, sal_dims dims, const 
                                    void *stream);
 
 /*
+ * Caller-given neighbourhoods for Eq. 5 (the text after Eq. 5: the comparison window can be
+ * tuned in orientation, size and weights; Fig. 3 shows lines along t, x and the t-x diagonal).
+ * For map m: count[m] offsets offset[m][k] = (dt, dx, dy) with weights weight[m][k], and
+ *   S_m[v] = count[m]^-1 sum_k | E_m[v] - weight[m][k] E_m[v + offset[m][k]] |.
+ * Limits: 1 <= count[m] <= SAL_STENCIL_MAX_OFFSETS; every component in
+ * [-SAL_STENCIL_MAX_RADIUS, SAL_STENCIL_MAX_RADIUS]; no offset (0, 0, 0); finite weights.
+ * Host memory, read during the call only.
+ */
+#define SAL_STENCIL_MAX_OFFSETS 64
+#define SAL_STENCIL_MAX_RADIUS 7
+typedef struct {
+    int32_t count[3];
+    int32_t offset[3][SAL_STENCIL_MAX_OFFSETS][3];
+    float weight[3][SAL_STENCIL_MAX_OFFSETS];
+} sal_user_stencil;
+
+/*
+ * sal_directional_compare with the neighbourhood of `st` instead of p->stencil (p gives the
+ * boundary extension; its other fields are checked but unused).  Outputs and workspace as
+ * for sal_directional_compare (sal_dcs_workspace_size bytes).  SAL_ERR_INVALID_ARG for a
+ * stencil outside the limits above.
+ */
+SAL_API sal_status sal_directional_compare_user(const float *E, sal_dims dims, const sal_params *p,
+                                                const sal_user_stencil *st, float *Sm, double *stats, void *ws,
+                                                size_t ws_bytes, void *stream);
+
+/*
  * Weighted combination, Eq. 6, of the min-max normalised maps:
  * S = a N_t + b N_x + c N_y with N_m = (S_m - min_m) / (max_m - min_m).  `stats` is the
  * device array sal_directional_compare wrote.
@@ -176,6 +208,41 @@ SAL_API sal_status sal_saliency_host(const float *V_host, sal_dims dims, const s
 /* Waits for and destroys the streams and events kept for workspace ws (none: no-op). */
 SAL_API sal_status sal_host_release(void *ws);
 
+/* ---- Slabs along t ------------------------------------------------------------------------
+ * One volume of T planes split into slabs that run on different GPUs (one process per GPU)
+ * or on one GPU in turn.  The method's only global step is the normalisation before Eq. 6,
+ * which needs the (min, max) of each S_m over the whole volume: every other value depends on
+ * a bounded neighbourhood.  E at a voxel needs V within h = (L-1)/2 planes, and S_m needs E
+ * within r_t planes (r_t = 1 for the 26-neighbourhood, h for the line and t-x diagonal
+ * stencils).  So a slab that owns the planes [own_lo, own_hi) is given the planes
+ * [ext_lo, ext_hi) of V, ext_lo = max(0, own_lo - H), ext_hi = min(T, own_hi + H), with
+ * H = h + r_t from sal_slab_halo, and:
+ *   1. sal_slab_maps: steps 1-4 on those planes; S_m of its own planes into Sm_own
+ *      ([3][own_hi - own_lo][X][Y]) and their (min, max, sum) into stats_local (9 doubles);
+ *   2. the 9 doubles of every slab are gathered (between ranks: one all-gather of 9 doubles
+ *      per rank, the only exchange) and merged by sal_stats_merge;
+ *   3. sal_combine(Sm_own, merged stats, {own_hi - own_lo, X, Y}) gives the slab's S.
+ * S_m and S equal those of sal_saliency on the whole volume bit for bit when both use the
+ * same spectral-energy tile shape (the autotuner's choice per L, precision and size class:
+ * each value is then computed from the same samples in the same order), else within
+ * rounding; the sums differ only in rounding.
+ * PERIODIC wraps t from the last plane to the first, which a slab does not hold: with it a
+ * slab must be the whole volume (SAL_ERR_UNSUPPORTED otherwise).
+ */
+SAL_API sal_status sal_slab_halo(const sal_params *p, int64_t *planes);
+/* Workspace of sal_slab_maps for a slab given ext_planes = ext_hi - ext_lo planes of V. */
+SAL_API sal_status sal_slab_workspace_size(int64_t ext_planes, int64_t X, int64_t Y, const sal_params *p,
+                                           size_t *bytes);
+/* dims: the WHOLE volume (T, X, Y).  V_ext: device, the planes [ext_lo, ext_hi) of V
+ * (ext_lo, ext_hi exactly as above, else SAL_ERR_INVALID_ARG).  Sm_own, stats_local: device
+ * outputs (sizes above); ws: device, sal_slab_workspace_size bytes.  Asynchronous. */
+SAL_API sal_status sal_slab_maps(const float *V_ext, sal_dims dims, int64_t ext_lo, int64_t ext_hi, int64_t own_lo,
+                                 int64_t own_hi, const sal_params *p, float *Sm_own, double *stats_local, void *ws,
+                                 size_t ws_bytes, void *stream);
+/* Merges n statistics records (device, [n][9], (min, max, sum) per map) into out (device,
+ * 9 doubles): min of the minima, max of the maxima, FP64 sum of the sums in record order. */
+SAL_API sal_status sal_stats_merge(const double *stats, int32_t n, double *out, void *stream);
+
 /*
  * Directional compare for callers that cannot allocate device memory.
  *
@@ -192,7 +259,8 @@ SAL_API sal_status sal_host_release(void *ws);
  *    launches nothing.  The array takes 9 * (SAL_DCS_STATIC_MAX_TILES + 160) doubles,
  *    about 9.4 MB, on every GPU that loads the library, until the process exits;
  *  - the first call on a device looks up the array's device address (a one-time set-up
- *    for that device); make that first call before any stream capture;
+ *    for that device, repeated only if the device's context changes, e.g. after
+ *    cudaDeviceReset); make that first call before any stream capture;
  *  - every call shares the one array and overwrites every record it reads, so nothing has
  *    to be cleared between calls; two calls whose kernels overlap on the GPU (different
  *    streams, or different host threads on one device) race on it and must be ordered by
@@ -328,6 +396,20 @@ SAL_API sal_status sal_device_status(void *stream);
  * bounded waits runs out (after about 20 ms) and sal_device_status reports
  * SAL_ERR_TIMEOUT.  Off by default; never needed in normal use. */
 SAL_API sal_status sal_test_stall_tensor_cores(int32_t on);
+
+/*
+ * Measurement helper, not part of the method: the FP32 FMA rate of this GPU, the denominator
+ * of the spectral-energy kernel's ALU roofline.  Launches n_threads / 256 blocks of 256
+ * threads; each thread runs SAL_PROBE_CHAINS independent chains of `iters` FMAs
+ * (x <- x * a + b) and writes one float to out[thread] (device, n_threads floats, so nothing
+ * is optimised away).  packed = 0 issues scalar FFMA, packed = 1 the fma.rn.f32x2 form
+ * (two chains per instruction).  FP32 flops of one launch = 2 * SAL_PROBE_CHAINS * iters *
+ * n_threads; time it with events on `stream`.  n_threads must be a positive multiple of 256
+ * and iters a positive multiple of 16, else SAL_ERR_INVALID_ARG; SAL_ERR_CUDA if the launch
+ * fails.  Asynchronous on `stream`; allocates nothing.
+ */
+#define SAL_PROBE_CHAINS 8
+SAL_API sal_status sal_probe_fma_rate(float *out, int64_t n_threads, int32_t iters, int32_t packed, void *stream);
 
 /* Static text for a status code. */
 SAL_API const char *sal_status_string(sal_status s);

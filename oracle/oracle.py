@@ -306,3 +306,76 @@ def surrogate_loss_grad(x, widths, params, target, mask=None, bnd=REFLECT):
     loss = _load().oracle_surrogate_loss_grad(xp, *x.shape[1:], len(widths) - 1, _widths(widths), pp, bnd, tp,
                                               mp, gp)
     return loss, grads
+
+
+# ---- coarse-stride cubes (cube centres on a lattice of step s, E interpolated back) ------
+
+def _lattice_protos():
+    lib = _load()
+    if not getattr(lib, "_lattice_ready", False):
+        f64p = ctypes.POINTER(ctypes.c_double)
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L_, I_, D_ = ctypes.c_long, ctypes.c_int, ctypes.c_double
+        lib.oracle_lattice_size.argtypes = [L_, I_]
+        lib.oracle_lattice_size.restype = L_
+        lib.oracle_energy_lattice.argtypes = [f32p, L_, L_, L_, I_, I_, I_, I_, f64p]
+        lib.oracle_energy_lattice.restype = I_
+        lib.oracle_interp_lattice.argtypes = [f64p, I_, L_, L_, L_, I_, f64p]
+        lib.oracle_interp_lattice.restype = None
+        lib.oracle_energy_strided.argtypes = [f32p, L_, L_, L_, I_, I_, I_, I_, f64p]
+        lib.oracle_energy_strided.restype = I_
+        lib.oracle_saliency_strided.argtypes = [f32p, L_, L_, L_, I_, I_, I_, I_, D_, D_, D_, D_, D_, I_,
+                                                f64p, f64p, f64p, f64p]
+        lib.oracle_saliency_strided.restype = I_
+        lib._lattice_ready = True
+    return lib
+
+
+def lattice_size(n: int, s: int) -> int:
+    """Number of cube centres along an axis of n samples at stride s."""
+    return int(_lattice_protos().oracle_lattice_size(int(n), int(s)))
+
+
+def lattice_shape(shape, s):
+    return tuple(lattice_size(n, s) for n in shape)
+
+
+def energy_lattice(V, L, s, bnd=REFLECT, threads=None) -> np.ndarray:
+    """E_m of the cubes centred on the lattice points: [3][Tc][Xc][Yc]."""
+    V, vp = _f32(V)
+    out, op = _f64(np.zeros((3,) + lattice_shape(V.shape, s)))
+    rc = _lattice_protos().oracle_energy_lattice(vp, *V.shape, L, bnd, int(s), threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_energy_lattice failed ({rc})")
+    return out
+
+
+def interp_lattice(Ec, shape, s) -> np.ndarray:
+    """Trilinear interpolation of lattice values [C][Tc][Xc][Yc] to every voxel of `shape`."""
+    Ec, ep = _f64(Ec)
+    out, op = _f64(np.zeros((Ec.shape[0],) + tuple(shape)))
+    _lattice_protos().oracle_interp_lattice(ep, Ec.shape[0], *shape, int(s), op)
+    return out
+
+
+def energy_strided(V, L, s, bnd=REFLECT, threads=None) -> np.ndarray:
+    V, vp = _f32(V)
+    out, op = _f64(np.zeros((3,) + V.shape))
+    rc = _lattice_protos().oracle_energy_strided(vp, *V.shape, L, bnd, int(s), threads or default_threads(), op)
+    if rc:
+        raise ValueError(f"oracle_energy_strided failed ({rc})")
+    return out
+
+
+def saliency_strided(V, L=7, s=2, bnd=REFLECT, stencil=STENCIL_26, sigma=1.0, a=1 / 3, b=1 / 3, c=1 / 3,
+                     eps=1e-6, threads=None, full=False):
+    V, vp = _f32(V)
+    S, sp = _f64(np.zeros(V.shape))
+    E, ep = _f64(np.zeros((3,) + V.shape))
+    Sm, mp = _f64(np.zeros((3,) + V.shape))
+    st, tp = _f64(np.zeros(9))
+    rc = _lattice_protos().oracle_saliency_strided(vp, *V.shape, L, bnd, stencil, int(s), float(sigma), a, b, c, eps,
+                                                   threads or default_threads(), sp, ep, mp, tp)
+    if rc:
+        raise ValueError(f"oracle_saliency_strided failed ({rc})")
+    return (S, E, Sm, st.reshape(3, 3)) if full else S

@@ -318,6 +318,93 @@ int oracle_energy_at(const float *V, long T, long X, long Y, int L, int bnd,
     return 0;
 }
 
+/*
+ * Coarse-stride cubes (Sec. 2, first step: the local cube slides "with more than 50 %
+ * overlap"; reading R4 with a stride s > 1).  Along an axis of n samples the cube centres
+ * form the lattice c_i = min(i s, n - 1), i = 0 .. n_c - 1, n_c = ceil((n - 1) / s) + 1: step
+ * s, and the last sample always a centre, so every voxel lies between two centres.
+ */
+long oracle_lattice_size(long n, int s) { return n <= 1 ? 1 : (n - 2) / s + 2; }
+
+static long lattice_coord(long i, long n, int s)
+{
+    long c = i * (long)s;
+    return c < n - 1 ? c : n - 1;
+}
+
+/* Ec [3][Tc][Xc][Yc]: E_m of the cube centred on every lattice point (separable DFT). */
+int oracle_energy_lattice(const float *V, long T, long X, long Y, int L, int bnd, int s, int nthreads, double *Ec)
+{
+    if (L < 1 || (L % 2) == 0 || s < 1) return -1;
+    long Tc = oracle_lattice_size(T, s), Xc = oracle_lattice_size(X, s), Yc = oracle_lattice_size(Y, s);
+    long Nc = Tc * Xc * Yc;
+    int64_t *coords = (int64_t *)malloc(sizeof(int64_t) * 3 * Nc);
+    for (long i = 0; i < Tc; ++i)
+        for (long j = 0; j < Xc; ++j)
+            for (long k = 0; k < Yc; ++k) {
+                long v = (i * Xc + j) * Yc + k;
+                coords[3 * v] = lattice_coord(i, T, s);
+                coords[3 * v + 1] = lattice_coord(j, X, s);
+                coords[3 * v + 2] = lattice_coord(k, Y, s);
+            }
+    int rc = oracle_energy_at(V, T, X, Y, L, bnd, coords, Nc, nthreads, Ec);
+    free(coords);
+    return rc;
+}
+
+/* The two lattice centres around coordinate v and v's fraction of the way between them. */
+static void lattice_segment(long v, long n, int s, long *i0, double *f)
+{
+    long nc = oracle_lattice_size(n, s);
+    if (nc == 1) {
+        *i0 = 0;
+        *f = 0.0;
+        return;
+    }
+    long i = v / s;
+    if (i > nc - 2) i = nc - 2;
+    long lo = lattice_coord(i, n, s), hi = lattice_coord(i + 1, n, s);
+    *i0 = i;
+    *f = (double)(v - lo) / (double)(hi - lo);
+}
+
+/* Trilinear interpolation of lattice values Ec [C][Tc][Xc][Yc] back to every voxel: out [C][T][X][Y]. */
+void oracle_interp_lattice(const double *Ec, int C, long T, long X, long Y, int s, double *out)
+{
+    long Tc = oracle_lattice_size(T, s), Xc = oracle_lattice_size(X, s), Yc = oracle_lattice_size(Y, s);
+    long N = T * X * Y, Nc = Tc * Xc * Yc;
+    for (int m = 0; m < C; ++m)
+        for (long t = 0; t < T; ++t)
+            for (long x = 0; x < X; ++x)
+                for (long y = 0; y < Y; ++y) {
+                    long i, j, k;
+                    double ft, fx, fy;
+                    lattice_segment(t, T, s, &i, &ft);
+                    lattice_segment(x, X, s, &j, &fx);
+                    lattice_segment(y, Y, s, &k, &fy);
+                    double acc = 0.0;
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b)
+                            for (int c = 0; c < 2; ++c) {
+                                double wgt = (a ? ft : 1.0 - ft) * (b ? fx : 1.0 - fx) * (c ? fy : 1.0 - fy);
+                                if (wgt == 0.0) continue;   /* also keeps the index inside a 1-point lattice */
+                                acc += wgt * Ec[m * Nc + ((i + a) * Xc + (j + b)) * Yc + (k + c)];
+                            }
+                    out[m * N + (t * X + x) * Y + y] = acc;
+                }
+}
+
+/* E of every voxel with cubes on the lattice of stride s, interpolated back (s = 1: oracle_energy). */
+int oracle_energy_strided(const float *V, long T, long X, long Y, int L, int bnd, int s, int nthreads, double *E)
+{
+    long Nc = oracle_lattice_size(T, s) * oracle_lattice_size(X, s) * oracle_lattice_size(Y, s);
+    double *Ec = (double *)malloc(sizeof(double) * 3 * Nc);
+    int rc = oracle_energy_lattice(V, T, X, Y, L, bnd, s, nthreads, Ec);
+    if (!rc) oracle_interp_lattice(Ec, 3, T, X, Y, s, E);
+    free(Ec);
+    return rc;
+}
+
 /* Offsets of the neighbourhood of map m (reading R7); returns Q. */
 static int neighbourhood(int stencil, int m, int L, int off[][3])
 {
@@ -469,6 +556,28 @@ int oracle_saliency(const float *V, long T, long X, long Y, int L, int bnd, int 
     double *Sm = Sm_out ? Sm_out : (double *)malloc(sizeof(double) * 3 * N);
     double st[9];
     int rc = oracle_energy(V, T, X, Y, L, bnd, 0, nthreads, E);
+    if (!rc) rc = oracle_dcs(E, T, X, Y, bnd, stencil, L, sigma, nthreads, Sm);
+    if (!rc) {
+        oracle_stats(Sm, N, st);
+        oracle_combine(Sm, st, N, a, b, c, eps, S);
+        if (stats_out) memcpy(stats_out, st, sizeof(st));
+    }
+    if (!E_out) free(E);
+    if (!Sm_out) free(Sm);
+    return rc;
+}
+
+/* The whole method with cubes on the lattice of stride s (E interpolated back to every
+ * voxel before Eq. 5); s = 1 is oracle_saliency. */
+int oracle_saliency_strided(const float *V, long T, long X, long Y, int L, int bnd, int stencil, int s,
+                            double sigma, double a, double b, double c, double eps, int nthreads,
+                            double *S, double *E_out, double *Sm_out, double *stats_out)
+{
+    long N = T * X * Y;
+    double *E = E_out ? E_out : (double *)malloc(sizeof(double) * 3 * N);
+    double *Sm = Sm_out ? Sm_out : (double *)malloc(sizeof(double) * 3 * N);
+    double st[9];
+    int rc = oracle_energy_strided(V, T, X, Y, L, bnd, s, nthreads, E);
     if (!rc) rc = oracle_dcs(E, T, X, Y, bnd, stencil, L, sigma, nthreads, Sm);
     if (!rc) {
         oracle_stats(Sm, N, st);

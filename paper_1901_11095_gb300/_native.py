@@ -16,11 +16,13 @@ SAL_OK, SAL_ERR_INVALID_ARG, SAL_ERR_UNSUPPORTED, SAL_ERR_WORKSPACE, SAL_ERR_CUD
     SAL_ERR_INTERNAL = range(7)
 SAL_PREC_FP32, SAL_PREC_TF32, SAL_PREC_BF16 = 0, 1, 2
 SAL_BND_REFLECT, SAL_BND_PERIODIC = 0, 1
-SAL_STENCIL_26, SAL_STENCIL_LINE = 0, 1
+SAL_STENCIL_26, SAL_STENCIL_LINE, SAL_STENCIL_DIAG_TX = 0, 1, 2
+SAL_STENCIL_MAX_OFFSETS, SAL_STENCIL_MAX_RADIUS = 64, 7
 SAL_STATS_LEN = 9
 SAL_DCS_STATIC_MAX_TILES = 131072
 SAL_BATCH_MAX = 128
 SAL_SURR_LAYERS, SAL_SURR_WIDTH = 5, 24
+SAL_PROBE_CHAINS = 8
 
 
 class SalDims(ctypes.Structure):
@@ -31,6 +33,12 @@ class SalParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("boundary", ctypes.c_int32),
                 ("stencil", ctypes.c_int32), ("sigma", ctypes.c_float), ("reserved", ctypes.c_int32),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class SalUserStencil(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32 * 3),
+                ("offset", ((ctypes.c_int32 * 3) * SAL_STENCIL_MAX_OFFSETS) * 3),
+                ("weight", (ctypes.c_float * SAL_STENCIL_MAX_OFFSETS) * 3)]
 
 
 class SalVolume(ctypes.Structure):
@@ -71,6 +79,12 @@ def lib():
             "sal_spectral_energy": [vp, SalDims, pp, vp, vp],
             "sal_directional_compare": [vp, SalDims, pp, vp, vp, vp, sz, vp],
             "sal_directional_compare_static": [vp, SalDims, pp, vp, vp, vp],
+            "sal_directional_compare_user": [vp, SalDims, pp, ctypes.POINTER(SalUserStencil), vp, vp, vp, sz, vp],
+            "sal_slab_halo": [pp, i64p],
+            "sal_slab_workspace_size": [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, pp, ctypes.POINTER(sz)],
+            "sal_slab_maps": [vp, SalDims, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, pp, vp, vp,
+                              vp, sz, vp],
+            "sal_stats_merge": [vp, ctypes.c_int32, vp, vp],
             "sal_combine": [vp, vp, SalDims, pp, vp, vp],
             "sal_saliency": [vp, SalDims, pp, vp, vp, vp, sz, vp],
             "sal_host_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
@@ -99,6 +113,7 @@ def lib():
             "sal_surrogate_infer_workspace_size": [SalDims, pp, ctypes.POINTER(sz)],
             "sal_surrogate_infer": [vp, SalDims, pp, vp, vp, ctypes.c_float, vp, vp, sz, vp],
             "sal_test_stall_tensor_cores": [ctypes.c_int32],
+            "sal_probe_fma_rate": [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -121,11 +136,12 @@ def check(status: int) -> None:
 def exported_symbols() -> list[str]:
     return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
             "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_directional_compare_static",
-            "sal_combine", "sal_saliency", "sal_host_workspace_size", "sal_saliency_host", "sal_host_release",
+            "sal_directional_compare_user", "sal_slab_halo", "sal_slab_workspace_size", "sal_slab_maps",
+            "sal_stats_merge", "sal_combine", "sal_saliency", "sal_host_workspace_size", "sal_saliency_host", "sal_host_release",
             "sal_batch_workspace_size", "sal_saliency_batched",
             "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",
             "sal_autotune_batched", "sal_autotune_query", "sal_autotune_save", "sal_autotune_load",
             "sal_autotune_clear", "sal_device_status", "sal_test_stall_tensor_cores", "sal_surrogate_param_count",
             "sal_surrogate_workspace_size", "sal_surrogate_forward", "sal_surrogate_backward",
             "sal_surrogate_adam_step", "sal_surrogate_infer_workspace_size", "sal_surrogate_infer",
-            "sal_status_string", "sal_last_error"]
+            "sal_probe_fma_rate", "sal_status_string", "sal_last_error"]

@@ -11,11 +11,11 @@ import ctypes
 import torch
 
 from . import _native as N
-from ._native import SalDims, SalParams, SalTileChoice, SalVolume, check
+from ._native import SalDims, SalParams, SalTileChoice, SalUserStencil, SalVolume, check
 
 _PREC = {"fp32": N.SAL_PREC_FP32, "tf32": N.SAL_PREC_TF32, "bf16": N.SAL_PREC_BF16}
 _BND = {"reflect": N.SAL_BND_REFLECT, "periodic": N.SAL_BND_PERIODIC}
-_STENCIL = {"26": N.SAL_STENCIL_26, "line": N.SAL_STENCIL_LINE}
+_STENCIL = {"26": N.SAL_STENCIL_26, "line": N.SAL_STENCIL_LINE, "diag_tx": N.SAL_STENCIL_DIAG_TX}
 
 
 def sal_params_default() -> SalParams:
@@ -131,6 +131,79 @@ def sal_directional_compare_static(E: torch.Tensor, p: SalParams, Sm: torch.Tens
     check(N.lib().sal_directional_compare_static(_dev(E, name="E"), dims, ctypes.byref(p), _dev(Sm, name="Sm"),
                                                  _dev(stats, torch.float64, "stats"), _stream(stream)))
     return Sm, stats
+
+
+def user_stencil(offsets, weights) -> SalUserStencil:
+    """A sal_user_stencil from per-map lists: offsets[m] = [(dt, dx, dy), ...], weights[m] = [w, ...]."""
+    st = SalUserStencil()
+    for m in range(3):
+        if len(offsets[m]) != len(weights[m]):
+            raise ValueError(f"map {m}: {len(offsets[m])} offsets but {len(weights[m])} weights")
+        if len(offsets[m]) > N.SAL_STENCIL_MAX_OFFSETS:
+            raise ValueError(f"map {m}: at most {N.SAL_STENCIL_MAX_OFFSETS} offsets")
+        st.count[m] = len(offsets[m])
+        for k, (o, w) in enumerate(zip(offsets[m], weights[m])):
+            st.offset[m][k][0], st.offset[m][k][1], st.offset[m][k][2] = (int(v) for v in o)
+            st.weight[m][k] = float(w)
+    return st
+
+
+def sal_directional_compare_user(E: torch.Tensor, p: SalParams, st: SalUserStencil, Sm: torch.Tensor | None = None,
+                                 stats: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Eq. 5 with the caller's neighbourhood per map (see user_stencil): (S_m, stats)."""
+    dims = SalDims(*[int(s) for s in E.shape[1:]])
+    if Sm is None:
+        Sm = torch.empty_like(E)
+    if stats is None:
+        stats = torch.empty(N.SAL_STATS_LEN, device=E.device, dtype=torch.float64)
+    if ws is None:
+        ws = torch.empty(sal_dcs_workspace_size(dims, p), device=E.device, dtype=torch.uint8)
+    check(N.lib().sal_directional_compare_user(_dev(E, name="E"), dims, ctypes.byref(p), ctypes.byref(st),
+                                               _dev(Sm, name="Sm"), _dev(stats, torch.float64, "stats"),
+                                               _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
+    return Sm, stats
+
+
+def sal_slab_halo(p: SalParams) -> int:
+    """Planes of V a slab needs beyond its own on each side."""
+    n = ctypes.c_int64()
+    check(N.lib().sal_slab_halo(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_slab_workspace_size(ext_planes: int, X: int, Y: int, p: SalParams) -> int:
+    n = ctypes.c_size_t()
+    check(N.lib().sal_slab_workspace_size(int(ext_planes), int(X), int(Y), ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def sal_slab_maps(V_ext: torch.Tensor, dims: SalDims, ext_lo: int, ext_hi: int, own_lo: int, own_hi: int,
+                  p: SalParams, Sm_own: torch.Tensor | None = None, stats_local: torch.Tensor | None = None,
+                  ws: torch.Tensor | None = None, stream=None):
+    """Steps 1-4 of one slab: (S_m of its own planes [3, own, X, Y], their local (min, max, sum) [9])."""
+    X, Y = int(dims.X), int(dims.Y)
+    if Sm_own is None:
+        Sm_own = torch.empty((3, int(own_hi) - int(own_lo), X, Y), device=V_ext.device, dtype=torch.float32)
+    if stats_local is None:
+        stats_local = torch.empty(N.SAL_STATS_LEN, device=V_ext.device, dtype=torch.float64)
+    if ws is None:
+        ws = torch.empty(sal_slab_workspace_size(int(ext_hi) - int(ext_lo), X, Y, p), device=V_ext.device,
+                         dtype=torch.uint8)
+    check(N.lib().sal_slab_maps(_dev(V_ext, name="V_ext"), dims, int(ext_lo), int(ext_hi), int(own_lo), int(own_hi),
+                                ctypes.byref(p), _dev(Sm_own, name="Sm_own"),
+                                _dev(stats_local, torch.float64, "stats_local"), _dev(ws, torch.uint8, "ws"),
+                                ws.numel(), _stream(stream)))
+    return Sm_own, stats_local
+
+
+def sal_stats_merge(stats: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Merges statistics records [n, 9] (device) into one [9]: min, max and FP64 sum per map."""
+    if out is None:
+        out = torch.empty(N.SAL_STATS_LEN, device=stats.device, dtype=torch.float64)
+    n = stats.numel() // N.SAL_STATS_LEN
+    check(N.lib().sal_stats_merge(_dev(stats, torch.float64, "stats"), n, _dev(out, torch.float64, "out"),
+                                  _stream(stream)))
+    return out
 
 
 def sal_combine(Sm: torch.Tensor, stats: torch.Tensor, p: SalParams, S: torch.Tensor | None = None,
@@ -328,3 +401,11 @@ def sal_device_status(stream=None) -> None:
 
 def sal_test_stall_tensor_cores(on: bool) -> None:
     check(N.lib().sal_test_stall_tensor_cores(1 if on else 0))
+
+
+def sal_probe_fma_rate(out: torch.Tensor, iters: int, packed: bool = False, stream=None) -> float:
+    """Launches the FP32 FMA-rate probe (one float per thread into ``out``); returns the FP32
+    flops the launch performs (time it with events on ``stream``)."""
+    n = out.numel()
+    check(N.lib().sal_probe_fma_rate(_dev(out, name="out"), n, int(iters), 1 if packed else 0, _stream(stream)))
+    return 2.0 * N.SAL_PROBE_CHAINS * iters * n

@@ -10,6 +10,8 @@
 // sum (warp shuffles, then FP64 across warps) into one partial record; two small passes
 // finish the FP64 reduction.
 #include <float.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -125,28 +127,54 @@ __device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m,
         }
 }
 
-// Line stencil: one map m of one output tile of one volume; writes the tile's (min, max,
-// sum) record.
+// Offset-list stencils (the t-x diagonal, caller-given neighbourhoods): out = sum_q
+// |c - w_q n(delta_q)|, delta_q the shared-memory offset of neighbour q from the centre.
+__device__ __forceinline__ void dcs_offsets(const float *sE, const Halo &hl, int tq, int x, int yq, const int *delta,
+                                            const float *w, int Q, float (&out)[QT][QY])
+{
+    const float *base = sE + (QT * tq + hl.rt) * hl.PP + (x + hl.rx) * hl.pitch + hl.off + hl.ry + QY * yq;
+    float cv[QT][QY];
+#pragma unroll
+    for (int to = 0; to < QT; ++to)
+#pragma unroll
+        for (int yo = 0; yo < QY; ++yo) {
+            cv[to][yo] = base[to * hl.PP + yo];
+            out[to][yo] = 0.f;
+        }
+    for (int q = 0; q < Q; ++q) {
+        const float *nb = base + delta[q];
+        const float wq = w[q];
+#pragma unroll
+        for (int to = 0; to < QT; ++to)
+#pragma unroll
+            for (int yo = 0; yo < QY; ++yo) out[to][yo] += fabsf(fmaf(-wq, nb[to * hl.PP + yo], cv[to][yo]));
+    }
+}
+
+// One map m of one output tile of one volume (line or offset-list stencil); writes the
+// tile's (min, max, sum) record.  Output planes are o_lo + 8 * (tile row) onwards, up to
+// o_hi; E has T planes (its boundary extension is taken at 0 and T), Sm holds the output
+// planes only.  `compute` fills a thread's 4 x 4 block of unnormalised sums.
+template <class Compute>
 __device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y, int bnd,
-                                         int m, int64_t tile, int tiles_x, int tiles_y, float *__restrict__ Sm,
-                                         double *__restrict__ partials, int64_t nparts, const DcsConsts &k, float *sE,
-                                         double (*red)[3])
+                                         int64_t o_lo, int64_t o_hi, int m, int64_t tile, int tiles_x, int tiles_y,
+                                         float *__restrict__ Sm, double *__restrict__ partials, int64_t nparts,
+                                         const Halo &hl, float invQ, float *sE, double (*red)[3], Compute &&compute)
 {
     const int ty = (int)(tile % tiles_y);
     const int tx = (int)((tile / tiles_y) % tiles_x);
     const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
-    const int64_t t0 = tt * DT, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
-    const int64_t N = T * X * Y;
-    const Halo hl = halo_for(SAL_STENCIL_LINE, m, k.h);
+    const int64_t t0 = o_lo + tt * DT, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
+    const int64_t XY = X * Y, No = (o_hi - o_lo) * XY;
 
-    stage_tile(E + m * N, sE, hl, T, X, Y, bnd, t0, x0, y0);
+    stage_tile(E + m * T * XY, sE, hl, T, X, Y, bnd, t0, x0, y0);
     __syncthreads();
 
     const int yq = threadIdx.x % (DY / QY);
     const int x = (threadIdx.x / (DY / QY)) % DX;
     const int tq = threadIdx.x / ((DY / QY) * DX);
     float out[QT][QY];
-    dcs_line(sE, hl, m, tq, x, yq, k, out);
+    compute(tq, x, yq, out);
 
     float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
     const int64_t gx = x0 + x, gy = y0 + QY * yq;
@@ -154,11 +182,11 @@ __device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T,
 #pragma unroll
         for (int to = 0; to < QT; ++to) {
             const int64_t gt = t0 + QT * tq + to;
-            if (gt >= T) break;
-            float *o = Sm + m * N + (gt * X + gx) * Y + gy;
+            if (gt >= o_hi) break;
+            float *o = Sm + m * No + ((gt - o_lo) * X + gx) * Y + gy;
 #pragma unroll
             for (int yo = 0; yo < QY; ++yo) {
-                out[to][yo] *= k.invQ;
+                out[to][yo] *= invQ;
                 if (gy + yo < Y) {
                     mn = fminf(mn, out[to][yo]);
                     mx = fmaxf(mx, out[to][yo]);
@@ -196,12 +224,14 @@ __device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T,
 }
 
 // Volumes of one launch; work item k of the launch is (volume, map, tile), map-major
-// within each volume.
+// within each volume.  Output planes [o_lo, o_hi) of E's T planes (the whole volume unless
+// the launch serves a slab).
 struct DVol {
     const float *E;
     float *Sm;
     double *part;          // [9][tiles] records of this volume
     int64_t T, X, Y;
+    int64_t o_lo, o_hi;
     int64_t item0, tiles;
     int tiles_x, tiles_y;
 };
@@ -211,22 +241,57 @@ struct DBatch {
     DVol v[kMaxBatch];
 };
 
+__device__ __forceinline__ const DVol &find_volume(const DBatch &bt, int64_t it)
+{
+    int lo = 0, hi = bt.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    return bt.v[lo];
+}
+
 __global__ void __launch_bounds__(DNT) dcs_line_kernel(const __grid_constant__ DBatch bt,
                                                        const __grid_constant__ DcsConsts k)
 {
     extern __shared__ __align__(16) float sE[];
     __shared__ double red[DNT / 32][3];
     for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
-        int lo = 0, hi = bt.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
-        }
-        const DVol &v = bt.v[lo];
+        const DVol &v = find_volume(bt, it);
         const int64_t local = it - v.item0;
         const int m = (int)(local / v.tiles);
-        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm, v.part, v.tiles, k,
-                 sE, red);
+        const Halo hl = halo_for(SAL_STENCIL_LINE, m, k.h);
+        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, v.o_lo, v.o_hi, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm,
+                 v.part, v.tiles, hl, k.invQ, sE, red,
+                 [&](int tq, int x, int yq, float (&out)[QT][QY]) { dcs_line(sE, hl, m, tq, x, yq, k, out); });
+        __syncthreads();
+    }
+}
+
+// Offset-list neighbourhood of every map: halo radii, the neighbours' shared-memory offsets
+// from the centre (for that map's halo geometry), their weights and 1 / Q.
+struct DcsUser {
+    int Q[3];
+    int rt[3], rx[3], ry[3];
+    int delta[3][SAL_STENCIL_MAX_OFFSETS];
+    float w[3][SAL_STENCIL_MAX_OFFSETS];
+    float invQ[3];
+};
+
+__global__ void __launch_bounds__(DNT) dcs_user_kernel(const __grid_constant__ DBatch bt,
+                                                       const __grid_constant__ DcsUser u)
+{
+    extern __shared__ __align__(16) float sE[];
+    __shared__ double red[DNT / 32][3];
+    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
+        const DVol &v = find_volume(bt, it);
+        const int64_t local = it - v.item0;
+        const int m = (int)(local / v.tiles);
+        const Halo hl(u.rt[m], u.rx[m], u.ry[m]);
+        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, v.o_lo, v.o_hi, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm,
+                 v.part, v.tiles, hl, u.invQ[m], sE, red, [&](int tq, int x, int yq, float (&out)[QT][QY]) {
+                     dcs_offsets(sE, hl, tq, x, yq, u.delta[m], u.w[m], u.Q[m], out);
+                 });
         __syncthreads();
     }
 }
@@ -284,12 +349,7 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
     const float g1 = k.g[1], g2 = k.g[2], g3 = k.g[3];
     const int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
-        int lo = 0, hi = bt.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
-        }
-        const DVol &v = bt.v[lo];
+        const DVol &v = find_volume(bt, it);
         // item -> (map, chunk, x block, y block) in 32 bits (the launcher checks 3 x records)
         const unsigned local = (unsigned)(it - v.item0), ntile = (unsigned)v.tiles;
         const int m = (int)(local / ntile);
@@ -298,9 +358,10 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
         const int tx = (int)(q1 - q2 * (unsigned)v.tiles_x);
         const int64_t ck = q2;
         const int64_t T = v.T, X = v.X, Y = v.Y, XY = X * Y;
-        const int64_t t0 = ck * SC, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
+        const int64_t o_lo = v.o_lo, o_hi = v.o_hi;      // output planes of E's T planes
+        const int64_t t0 = o_lo + ck * SC, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
         const float *Em = v.E + m * T * XY;
-        float *Sm = v.Sm + m * T * XY;
+        float *Sm = v.Sm + m * (o_hi - o_lo) * XY;
 
         // this thread's copies within one plane: source pointer of its element in plane 0 of
         // the map and its byte offset in a slot (a shared-memory address is 32 bits)
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
             cp_async_commit();
         };
 
-        const int64_t left = T - t0;
+        const int64_t left = o_hi - t0;
         const int nsteps = (int)(((left < SC ? left : SC) + DT - 1) / DT);
         // thread -> (t quarter, x row, y quad) of the block; a block at the last columns of the
         // volume packs its nyq < 16 live quads into the first threads, so that whole warps sit
@@ -405,8 +466,8 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
                     }
 
                 if (gx < X) {
-                    const bool full = gy + QY <= Y && t0 + rb + QT <= T;   // the whole 4 x 4 block is inside
-                    float *o = Sm + ((t0 + rb) * X + gx) * Y + gy;
+                    const bool full = gy + QY <= Y && t0 + rb + QT <= o_hi;   // the whole 4 x 4 block is inside
+                    float *o = Sm + ((t0 - o_lo + rb) * X + gx) * Y + gy;
                     const int64_t plane = X * Y;
                     if (full) {
 #pragma unroll
@@ -436,7 +497,7 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
 #pragma unroll
                         for (int to = 0; to < QT; ++to) {
                             const int64_t gt = t0 + rb + to;
-                            if (gt >= T) break;
+                            if (gt >= o_hi) break;
 #pragma unroll
                             for (int yo = 0; yo < QY; ++yo) {
                                 out[to][yo] *= k.invQ;
@@ -576,12 +637,80 @@ int64_t dcs_num_records(sal_dims d, int stencil)
     return nt * nx * ny;
 }
 
+// The t-x diagonal of Fig. 3 as an offset list: (k, k, 0), k = +-1..+-h, weights
+// g = exp(-2 k^2 / (2 sigma^2)), the same line for every map.
+sal_user_stencil diag_tx_stencil(const sal_params *p)
+{
+    sal_user_stencil u;
+    memset(&u, 0, sizeof(u));
+    const int h = (p->L - 1) / 2;
+    const double s2 = 2.0 * (double)p->sigma * (double)p->sigma;
+    for (int m = 0; m < 3; ++m) {
+        int q = 0;
+        for (int k = -h; k <= h; ++k) {
+            if (!k) continue;
+            u.offset[m][q][0] = k;
+            u.offset[m][q][1] = k;
+            u.offset[m][q][2] = 0;
+            u.weight[m][q] = (float)exp(-(double)(2 * k * k) / s2);
+            ++q;
+        }
+        u.count[m] = q;
+    }
+    return u;
+}
+
+namespace {
+
+DcsUser user_consts(const sal_user_stencil &st)
+{
+    DcsUser u;
+    memset(&u, 0, sizeof(u));
+    for (int m = 0; m < 3; ++m) {
+        int rt = 0, rx = 0, ry = 0;
+        for (int q = 0; q < st.count[m]; ++q) {
+            rt = abs(st.offset[m][q][0]) > rt ? abs(st.offset[m][q][0]) : rt;
+            rx = abs(st.offset[m][q][1]) > rx ? abs(st.offset[m][q][1]) : rx;
+            ry = abs(st.offset[m][q][2]) > ry ? abs(st.offset[m][q][2]) : ry;
+        }
+        const Halo hl(rt, rx, ry);
+        u.Q[m] = st.count[m];
+        u.rt[m] = rt;
+        u.rx[m] = rx;
+        u.ry[m] = ry;
+        for (int q = 0; q < st.count[m]; ++q) {
+            u.delta[m][q] = st.offset[m][q][0] * hl.PP + st.offset[m][q][1] * hl.pitch + st.offset[m][q][2];
+            u.w[m][q] = st.weight[m][q];
+        }
+        u.invQ[m] = (float)(1.0 / (double)st.count[m]);
+    }
+    return u;
+}
+
+}  // namespace
+
+int dcs_user_radius_t(const sal_user_stencil &st)
+{
+    int r = 0;
+    for (int m = 0; m < 3; ++m)
+        for (int q = 0; q < st.count[m]; ++q) r = abs(st.offset[m][q][0]) > r ? abs(st.offset[m][q][0]) : r;
+    return r;
+}
+
 // Launches the compare over n volumes (persistent grid when batched; the 26-neighbourhood
-// kernel is always persistent).
-cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s)
+// kernel is always persistent).  `user` (offset lists per map) replaces p->stencil when
+// given; p->stencil == SAL_STENCIL_DIAG_TX builds the diagonal's list.
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s,
+                             const sal_user_stencil *user)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
-    const bool s26 = p->stencil == SAL_STENCIL_26;
+    sal_user_stencil diag;
+    if (!user && p->stencil == SAL_STENCIL_DIAG_TX) {
+        diag = diag_tx_stencil(p);
+        user = &diag;
+    }
+    const bool s26 = !user && p->stencil == SAL_STENCIL_26;
+    const int rec_stencil = s26 ? SAL_STENCIL_26 : SAL_STENCIL_LINE;   // tiles of 8 planes unless 26
     DBatch bt;
     bt.n = n;
     bt.bnd = p->boundary;
@@ -590,14 +719,19 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         DVol &v = bt.v[i];
         int64_t nt, nx, ny;
         const sal_dims d{vols[i].T, vols[i].X, vols[i].Y};
-        dcs_tiles(d, &nt, &nx, &ny);
+        const int64_t o_lo = vols[i].o_lo, o_hi = vols[i].o_hi < 0 ? d.T : vols[i].o_hi;
+        if (o_lo < 0 || o_hi > d.T || o_lo >= o_hi) return cudaErrorInvalidValue;
+        const sal_dims dout{o_hi - o_lo, d.X, d.Y};
+        dcs_tiles(dout, &nt, &nx, &ny);
         v.E = vols[i].E;
         v.Sm = vols[i].Sm;
         v.part = vols[i].part;
         v.T = d.T;
         v.X = d.X;
         v.Y = d.Y;
-        v.tiles = dcs_num_records(d, p->stencil);
+        v.o_lo = o_lo;
+        v.o_hi = o_hi;
+        v.tiles = dcs_num_records(dout, rec_stencil);
         if (3 * v.tiles > 0x7fffffffLL) return cudaErrorInvalidValue;   // items of a volume in 32 bits
         v.tiles_x = (int)nx;
         v.tiles_y = (int)ny;
@@ -606,16 +740,25 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     }
     bt.total = total;
     const DcsConsts k = dcs_consts(p);
+    DcsUser u;
     const int h = (p->L - 1) / 2;
     int smem = (int)kSmem26;
-    if (!s26) {
+    if (user) {
+        u = user_consts(*user);
+        smem = 0;
+        for (int m = 0; m < 3; ++m) {
+            const int f = Halo(u.rt[m], u.rx[m], u.ry[m]).floats() * (int)sizeof(float);
+            smem = f > smem ? f : smem;
+        }
+    } else if (!s26) {
         smem = 0;
         for (int m = 0; m < 3; ++m) {
             const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
             smem = f > smem ? f : smem;
         }
     }
-    const void *fn = s26 ? (const void *)dcs26_kernel : (const void *)dcs_line_kernel;
+    const void *fn = user ? (const void *)dcs_user_kernel
+                          : (s26 ? (const void *)dcs26_kernel : (const void *)dcs_line_kernel);
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = total;
@@ -630,7 +773,9 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     }
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (s26)
+    if (user)
+        dcs_user_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, u);
+    else if (s26)
         dcs26_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
     else
         dcs_line_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
@@ -638,18 +783,40 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
 }
 
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials, double *stats,
-                       cudaStream_t s)
+                       cudaStream_t s, const sal_user_stencil *user, int64_t o_lo, int64_t o_hi)
 {
-    const int64_t tiles = dcs_num_records(d, p->stencil);
+    if (o_hi < 0) o_hi = d.T;
+    const int rec_stencil = (!user && p->stencil == SAL_STENCIL_26) ? SAL_STENCIL_26 : SAL_STENCIL_LINE;
+    const int64_t tiles = dcs_num_records(sal_dims{o_hi - o_lo, d.X, d.Y}, rec_stencil);
     if (3 * tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    DVolDesc v{E, Sm, partials, d.T, d.X, d.Y};
-    cudaError_t e = launch_dcs_items(&v, 1, p, false, s);
+    DVolDesc v{E, Sm, partials, d.T, d.X, d.Y, o_lo, o_hi};
+    cudaError_t e = launch_dcs_items(&v, 1, p, false, s, user);
     if (e != cudaSuccess) return e;
     double *second = partials + 9 * tiles;
     reduce_partials_kernel<<<kRedBlocks, 256, 0, s>>>(partials, tiles, second, kRedBlocks);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_partials_kernel<<<1, 256, 0, s>>>(second, kRedBlocks, stats, 1);
+    return cudaGetLastError();
+}
+
+// Merges n statistics records [n][9] (device) into one: min of the minima, max of the
+// maxima, FP64 sum of the sums, in record order.
+__global__ void stats_merge_kernel(const double *__restrict__ in, int n, double *__restrict__ out)
+{
+    const int q = threadIdx.x;
+    if (q >= 9) return;
+    double v = in[q];
+    for (int i = 1; i < n; ++i) {
+        const double u = in[9 * i + q];
+        v = q % 3 == 0 ? fmin(v, u) : (q % 3 == 1 ? fmax(v, u) : v + u);
+    }
+    out[q] = v;
+}
+
+cudaError_t launch_stats_merge(const double *in, int n, double *out, cudaStream_t s)
+{
+    stats_merge_kernel<<<1, 32, 0, s>>>(in, n, out);
     return cudaGetLastError();
 }
 
@@ -677,7 +844,11 @@ static __device__ __align__(256) double g_dcs_static_scratch[9 * (SAL_DCS_STATIC
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-double *g_static_ptr[kMaxDevices] = {};
+struct StaticSlot {
+    unsigned long long ctx = 0;   // id of the context the address belongs to
+    double *ptr = nullptr;
+};
+StaticSlot g_static_slot[kMaxDevices];
 }  // namespace
 
 int64_t dcs_num_tiles(sal_dims d)
@@ -688,8 +859,10 @@ int64_t dcs_num_tiles(sal_dims d)
 }
 
 // Device address of the fixed scratch on the current device.  In host code the array's
-// name is only a host-side stand-in, so the address comes from cudaGetSymbolAddress, once
-// per device (with that device current), and is cached.
+// name is only a host-side stand-in, so the address comes from cudaGetSymbolAddress: once per
+// device (with that device current), cached together with the id of the context it belongs
+// to.  A device reset (or any new primary context) changes that id, and the next call looks
+// the address up again instead of using one from the destroyed context.
 cudaError_t dcs_static_scratch(double **out)
 {
     int dev = 0;
@@ -697,13 +870,19 @@ cudaError_t dcs_static_scratch(double **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    StaticSlot &sl = g_static_slot[dev];
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx) == cudaSuccess;
+    if (!sl.ptr || !have_ctx || sl.ctx != ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_dcs_static_scratch);
+        e = cudaGetSymbolAddress(&p, g_dcs_static_scratch);   // creates the primary context if needed
         if (e != cudaSuccess) return e;
-        g_static_ptr[dev] = static_cast<double *>(p);
+        e = current_context_id(&ctx);
+        if (e != cudaSuccess) return e;
+        sl.ptr = static_cast<double *>(p);
+        sl.ctx = ctx;
     }
-    *out = g_static_ptr[dev];
+    *out = sl.ptr;
     return cudaSuccess;
 }
 

@@ -40,26 +40,47 @@ void make_tables(int L, SpecTables *t)
     t->escale = (float)(2.0 / ((n3 - 1.0) * n3));
 }
 
+namespace {
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+std::once_flag g_ctx_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+}  // namespace
+
+cudaError_t current_context_id(unsigned long long *id)
+{
+    std::call_once(g_ctx_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return cudaErrorNotSupported;
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return cudaErrorInitializationError;
+    return g_ctx_get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorInitializationError;
+}
+
 // Status word the tensor-core kernels set when a bounded wait runs out (one per device).
 static __device__ int g_device_status;
 
 namespace {
-std::mutex g_status_mu;
-int *g_status_ptr[64] = {};
 std::atomic<int> g_stall{0};
 }  // namespace
 
+// Device address of the status word in the current context.  Looked up on every call (the
+// lookup allocates nothing), so it stays right after a device reset.
 int *device_status_ptr()
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lock(g_status_mu);
-    if (!g_status_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
-        g_status_ptr[dev] = static_cast<int *>(p);
-    }
-    return g_status_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
 }
 
 TcControl tc_control()
@@ -123,7 +144,7 @@ sal_status check_params(const sal_params *p)
         return fail(SAL_ERR_INVALID_ARG, "bad precision %d", p->precision);
     if (p->boundary != SAL_BND_REFLECT && p->boundary != SAL_BND_PERIODIC)
         return fail(SAL_ERR_INVALID_ARG, "bad boundary %d", p->boundary);
-    if (p->stencil != SAL_STENCIL_26 && p->stencil != SAL_STENCIL_LINE)
+    if (p->stencil != SAL_STENCIL_26 && p->stencil != SAL_STENCIL_LINE && p->stencil != SAL_STENCIL_DIAG_TX)
         return fail(SAL_ERR_INVALID_ARG, "bad stencil %d", p->stencil);
     if (!(p->sigma > 0.f) || !isfinite(p->sigma)) return fail(SAL_ERR_INVALID_ARG, "sigma must be finite and > 0");
     if (p->reserved != 0) return fail(SAL_ERR_INVALID_ARG, "reserved must be 0");
@@ -151,6 +172,28 @@ WsLayout saliency_layout(sal_dims d)
 }
 
 size_t dcs_ws_bytes(sal_dims d) { return round256(9 * (size_t)sal::dcs_num_partials(d) * sizeof(double)); }
+
+// Planes of V a slab needs beyond its own on each side: h for the energies of the E planes
+// its comparisons read, plus the comparison's reach along t.
+int64_t slab_halo_planes(const sal_params *p)
+{
+    const int64_t h = (p->L - 1) / 2;
+    const int64_t rt = p->stencil == SAL_STENCIL_26 ? 1 : h;   // LINE (map t) and DIAG_TX reach h planes
+    return h + rt;
+}
+
+// Workspace of a slab: E of the given planes, then the reduction partials.
+WsLayout slab_layout(sal_dims ext)
+{
+    const size_t N = (size_t)(ext.T * ext.X * ext.Y);
+    WsLayout w;
+    w.E = 0;
+    w.Sm = 0;
+    w.partials = round256(3 * N * sizeof(float));
+    w.stats = round256(w.partials + 9 * (size_t)sal::dcs_num_partials(ext) * sizeof(double));
+    w.total = w.stats;
+    return w;
+}
 
 sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, float *E, cudaStream_t s)
 {
@@ -434,6 +477,95 @@ sal_status sal_directional_compare_static(const float *E, sal_dims dims, const s
     if (e != cudaSuccess) return cuda_fail(e, "fixed scratch address");
     e = sal::launch_dcs(E, dims, p, Sm, scratch, stats, (cudaStream_t)stream);
     return e == cudaSuccess ? ok() : cuda_fail(e, "sal_directional_compare_static");
+}
+
+sal_status sal_directional_compare_user(const float *E, sal_dims dims, const sal_params *p, const sal_user_stencil *st,
+                                        float *Sm, double *stats, void *ws, size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!E || !Sm || !stats || !ws || !st) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(E) || !aligned16(Sm) || !aligned16(stats) || !aligned16(ws))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    for (int m = 0; m < 3; ++m) {
+        if (st->count[m] < 1 || st->count[m] > SAL_STENCIL_MAX_OFFSETS)
+            return fail(SAL_ERR_INVALID_ARG, "map %d: count must be in [1, %d] (got %d)", m, SAL_STENCIL_MAX_OFFSETS,
+                        st->count[m]);
+        for (int k = 0; k < st->count[m]; ++k) {
+            const int32_t *o = st->offset[m][k];
+            for (int a = 0; a < 3; ++a)
+                if (o[a] < -SAL_STENCIL_MAX_RADIUS || o[a] > SAL_STENCIL_MAX_RADIUS)
+                    return fail(SAL_ERR_INVALID_ARG, "map %d offset %d: component %d outside [-%d, %d]", m, k, a,
+                                SAL_STENCIL_MAX_RADIUS, SAL_STENCIL_MAX_RADIUS);
+            if (!o[0] && !o[1] && !o[2]) return fail(SAL_ERR_INVALID_ARG, "map %d offset %d is (0, 0, 0)", m, k);
+            if (!isfinite(st->weight[m][k])) return fail(SAL_ERR_INVALID_ARG, "map %d weight %d is not finite", m, k);
+        }
+    }
+    const size_t need = dcs_ws_bytes(dims);
+    if (ws_bytes < need) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = sal::launch_dcs(E, dims, p, Sm, (double *)ws, stats, (cudaStream_t)stream, st);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_directional_compare_user");
+}
+
+sal_status sal_slab_halo(const sal_params *p, int64_t *planes)
+{
+    sal_status s = check_params(p);
+    if (s) return s;
+    if (!planes) return fail(SAL_ERR_INVALID_ARG, "planes is NULL");
+    *planes = slab_halo_planes(p);
+    return ok();
+}
+
+sal_status sal_slab_workspace_size(int64_t ext_planes, int64_t X, int64_t Y, const sal_params *p, size_t *bytes)
+{
+    sal_status s = check_dims(sal_dims{ext_planes, X, Y});
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!bytes) return fail(SAL_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = slab_layout(sal_dims{ext_planes, X, Y}).total;
+    return ok();
+}
+
+sal_status sal_slab_maps(const float *V_ext, sal_dims dims, int64_t ext_lo, int64_t ext_hi, int64_t own_lo, int64_t own_hi,
+                         const sal_params *p, float *Sm_own, double *stats_local, void *ws, size_t ws_bytes, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!V_ext || !Sm_own || !stats_local || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V_ext) || !aligned16(Sm_own) || !aligned16(stats_local) || !aligned16(ws))
+        return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    if (own_lo < 0 || own_hi > dims.T || own_lo >= own_hi)
+        return fail(SAL_ERR_INVALID_ARG, "own planes [%lld, %lld) must be a non-empty part of [0, %lld)",
+                    (long long)own_lo, (long long)own_hi, (long long)dims.T);
+    const int64_t H = slab_halo_planes(p);
+    const int64_t want_lo = own_lo - H > 0 ? own_lo - H : 0, want_hi = own_hi + H < dims.T ? own_hi + H : dims.T;
+    if (ext_lo != want_lo || ext_hi != want_hi)
+        return fail(SAL_ERR_INVALID_ARG, "planes of V must be [%lld, %lld) for own planes [%lld, %lld) (halo %lld)",
+                    (long long)want_lo, (long long)want_hi, (long long)own_lo, (long long)own_hi, (long long)H);
+    if (p->boundary == SAL_BND_PERIODIC && (ext_lo != 0 || ext_hi != dims.T))
+        return fail(SAL_ERR_UNSUPPORTED, "PERIODIC wraps t across the volume: a slab must hold every plane");
+    const sal_dims ext{ext_hi - ext_lo, dims.X, dims.Y};
+    const WsLayout w = slab_layout(ext);
+    if (ws_bytes < w.total) return fail(SAL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, w.total);
+    char *base = (char *)ws;
+    float *E = (float *)(base + w.E);
+    const cudaStream_t st = (cudaStream_t)stream;
+    s = energy_dispatch(V_ext, ext, p, E, st);
+    if (s) return s;
+    cudaError_t e = sal::launch_dcs(E, ext, p, Sm_own, (double *)(base + w.partials), stats_local, st, nullptr,
+                                    own_lo - ext_lo, own_hi - ext_lo);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_slab_maps");
+}
+
+sal_status sal_stats_merge(const double *stats, int32_t n, double *out, void *stream)
+{
+    if (!stats || !out) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (n < 1) return fail(SAL_ERR_INVALID_ARG, "n must be >= 1 (got %d)", n);
+    if (!aligned16(stats) || !aligned16(out)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    cudaError_t e = sal::launch_stats_merge(stats, n, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_stats_merge");
 }
 
 sal_status sal_combine(const float *Sm, const double *stats, sal_dims dims, const sal_params *p, float *S, void *stream)

@@ -77,6 +77,10 @@ struct TcControl {
     unsigned long long limit_ns;
 };
 bool energy_tc_supported(int L, int prec);
+// Unique id of the CUDA context current on this thread (driver cuCtxGetId, reached through the
+// runtime's driver entry points); a device reset or a new primary context gives a new id, so
+// device addresses cached per (device, id) are never reused from a destroyed context.
+cudaError_t current_context_id(unsigned long long *id);
 int *device_status_ptr();
 TcControl tc_control();
 void set_test_stall(int on);
@@ -111,20 +115,31 @@ cudaError_t launch_project(const float *mag, int64_t n, int L, float *E, cudaStr
 
 // One volume of a (possibly batched) directional-compare launch; `part` receives the
 // volume's [9][tiles] partial records.
+// Output planes [o_lo, o_hi) of E's T planes (o_hi < 0: all of them); Sm holds the output
+// planes only, [3][o_hi - o_lo][X][Y].
 struct DVolDesc {
     const float *E;
     float *Sm;
     double *part;
     int64_t T, X, Y;
+    int64_t o_lo = 0, o_hi = -1;
 };
-cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s);
+// `user` (offset lists per map) replaces p->stencil when not NULL.
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s,
+                             const sal_user_stencil *user = nullptr);
+// The t-x diagonal line of side L as an offset list, and the largest |dt| of a list.
+sal_user_stencil diag_tx_stencil(const sal_params *p);
+int dcs_user_radius_t(const sal_user_stencil &st);
+// Merges n statistics records [n][9] into one (min, max, FP64 sum).
+cudaError_t launch_stats_merge(const double *in, int n, double *out, cudaStream_t s);
 
 // Directional compare: capacity of partial records in the workspace (per map, any stencil,
 // plus the first reduction pass), and the records one map of a launch writes.
 int64_t dcs_num_partials(sal_dims d);
 int64_t dcs_num_records(sal_dims d, int stencil);
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials,
-                       double *stats, cudaStream_t s);
+                       double *stats, cudaStream_t s, const sal_user_stencil *user = nullptr, int64_t o_lo = 0,
+                       int64_t o_hi = -1);
 // Fixed-scratch variant of the directional compare (no allocation by caller or library).
 int64_t dcs_num_tiles(sal_dims d);
 cudaError_t dcs_static_scratch(double **out);

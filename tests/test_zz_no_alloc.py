@@ -45,6 +45,25 @@ def test_static_matches_workspace_call_twice(shape, stencil, L):
         np.testing.assert_allclose(stats.cpu().numpy(), st_ref.cpu().numpy(), rtol=1e-12)
 
 
+def test_static_calls_allocate_no_device_memory():
+    """After the first call (which looks up the scratch address), further calls leave the
+    device's free memory unchanged: neither the library nor the caller allocates."""
+    dev = torch.device("cuda:0")
+    V = torch.from_numpy(synth.make_volume((32, 40, 96), seed=22)).to(dev)
+    p = api.params()
+    E = api.sal_spectral_energy(V, p)
+    Sm = torch.empty_like(E)
+    stats = torch.empty(N.SAL_STATS_LEN, dtype=torch.float64, device=dev)
+    _static_call(E, p, Sm, stats)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(5):
+        _static_call(E, p, Sm, stats)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+
+
 def test_static_rejects_volumes_beyond_the_fixed_scratch():
     dev = torch.device("cuda:0")
     p = api.params()
