@@ -80,7 +80,12 @@ typedef struct {
     int32_t boundary;   /* sal_boundary */
     int32_t stencil;    /* sal_stencil */
     float sigma;        /* Gaussian width of the Eq. 5 weights, in voxels (> 0) */
-    int32_t reserved;   /* must be 0 */
+    int32_t stride;     /* cube centres (Sec. 2, first step: the cube slides with more than 50 %
+                           overlap): 0 or 1 = one cube per voxel; s in 2..(L-1)/2 = cubes centred
+                           on the lattice min(i s, n - 1) of every axis, E interpolated
+                           trilinearly back to every voxel (sal_saliency and the split calls
+                           sal_lattice_energy / sal_interpolate_lattice; FP32 only; other
+                           entry points return SAL_ERR_UNSUPPORTED for s > 1) */
     double a, b, c;     /* Eq. 6 weights of S_t, S_x, S_y (equal in the paper) */
     double eps;         /* relative range below which a map counts as constant */
 } sal_params;
@@ -127,6 +132,19 @@ SAL_API sal_status sal_project(const float *mag, int64_t n_vox, int32_t L, float
  */
 SAL_API sal_status sal_spectral_energy(const float *V, sal_dims dims, const sal_params *p, float *E,
                                void *stream);
+
+/*
+ * Coarse-stride cubes (p->stride = s > 1; Sec. 2, first step).  Along an axis of n samples
+ * the cube centres are c_i = min(i s, n - 1), i = 0 .. n_c - 1, n_c = ceil((n - 1) / s) + 1
+ * (n_c = 1 for n = 1).  sal_lattice_dims gives (Tc, Xc, Yc); sal_lattice_energy writes E_m of
+ * the cube centred on every lattice point, Ec [3][Tc][Xc][Yc] (device); sal_interpolate_lattice
+ * writes E [3][T][X][Y] (device), each voxel the trilinear interpolation of the 2 x 2 x 2
+ * lattice energies around it (exact at the lattice points).  FP32 on the CUDA cores; with
+ * s = 0 or 1 the lattice is every voxel.  Asynchronous; errors as the other calls.
+ */
+SAL_API sal_status sal_lattice_dims(sal_dims dims, const sal_params *p, sal_dims *lattice);
+SAL_API sal_status sal_lattice_energy(const float *V, sal_dims dims, const sal_params *p, float *Ec, void *stream);
+SAL_API sal_status sal_interpolate_lattice(const float *Ec, sal_dims dims, const sal_params *p, float *E, void *stream);
 
 /*
  * Directional centre-surround comparison, Eq. 5, of each E_m: Sm [3][T*X*Y], plus the

@@ -31,7 +31,7 @@ class SalDims(ctypes.Structure):
 
 class SalParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("precision", ctypes.c_int32), ("boundary", ctypes.c_int32),
-                ("stencil", ctypes.c_int32), ("sigma", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("stencil", ctypes.c_int32), ("sigma", ctypes.c_float), ("stride", ctypes.c_int32),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
@@ -80,6 +80,9 @@ def lib():
             "sal_directional_compare": [vp, SalDims, pp, vp, vp, vp, sz, vp],
             "sal_directional_compare_static": [vp, SalDims, pp, vp, vp, vp],
             "sal_directional_compare_user": [vp, SalDims, pp, ctypes.POINTER(SalUserStencil), vp, vp, vp, sz, vp],
+            "sal_lattice_dims": [SalDims, pp, ctypes.POINTER(SalDims)],
+            "sal_lattice_energy": [vp, SalDims, pp, vp, vp],
+            "sal_interpolate_lattice": [vp, SalDims, pp, vp, vp],
             "sal_slab_halo": [pp, i64p],
             "sal_slab_workspace_size": [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, pp, ctypes.POINTER(sz)],
             "sal_slab_maps": [vp, SalDims, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, pp, vp, vp,
@@ -136,7 +139,8 @@ def check(status: int) -> None:
 def exported_symbols() -> list[str]:
     return ["sal_params_default", "sal_workspace_size", "sal_dcs_workspace_size", "sal_local_spectra",
             "sal_project", "sal_spectral_energy", "sal_directional_compare", "sal_directional_compare_static",
-            "sal_directional_compare_user", "sal_slab_halo", "sal_slab_workspace_size", "sal_slab_maps",
+            "sal_directional_compare_user", "sal_lattice_dims", "sal_lattice_energy", "sal_interpolate_lattice",
+            "sal_slab_halo", "sal_slab_workspace_size", "sal_slab_maps",
             "sal_stats_merge", "sal_combine", "sal_saliency", "sal_host_workspace_size", "sal_saliency_host", "sal_host_release",
             "sal_batch_workspace_size", "sal_saliency_batched",
             "sal_graph_create_batched", "sal_graph_launch", "sal_graph_destroy", "sal_autotune",

@@ -25,9 +25,10 @@ def sal_params_default() -> SalParams:
 
 
 def params(L: int = 7, precision="fp32", boundary="reflect", stencil="26", sigma: float = 1.0,
-           a: float = 1 / 3, b: float = 1 / 3, c: float = 1 / 3, eps: float = 1e-6) -> SalParams:
+           a: float = 1 / 3, b: float = 1 / 3, c: float = 1 / 3, eps: float = 1e-6, stride: int = 1) -> SalParams:
     """A sal_params struct from readable values (names or the enum integers)."""
     p = sal_params_default()
+    p.stride = int(stride)
     p.L = int(L)
     p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     p.boundary = _BND[boundary] if isinstance(boundary, str) else int(boundary)
@@ -98,6 +99,34 @@ def sal_spectral_energy(V: torch.Tensor, p: SalParams, E: torch.Tensor | None = 
         E = torch.empty((3,) + tuple(V.shape), device=V.device, dtype=torch.float32)
     check(N.lib().sal_spectral_energy(_dev(V, name="V"), dims_of(V), ctypes.byref(p), _dev(E, name="E"),
                                       _stream(stream)))
+    return E
+
+
+def sal_lattice_dims(dims: SalDims, p: SalParams) -> SalDims:
+    """(Tc, Xc, Yc): the cube centres of stride p.stride along each axis."""
+    out = SalDims()
+    check(N.lib().sal_lattice_dims(dims, ctypes.byref(p), ctypes.byref(out)))
+    return out
+
+
+def sal_lattice_energy(V: torch.Tensor, p: SalParams, Ec: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """E_m of the cubes centred on the lattice points: [3, Tc, Xc, Yc]."""
+    lat = sal_lattice_dims(dims_of(V), p)
+    if Ec is None:
+        Ec = torch.empty((3, lat.T, lat.X, lat.Y), device=V.device, dtype=torch.float32)
+    check(N.lib().sal_lattice_energy(_dev(V, name="V"), dims_of(V), ctypes.byref(p), _dev(Ec, name="Ec"),
+                                     _stream(stream)))
+    return Ec
+
+
+def sal_interpolate_lattice(Ec: torch.Tensor, shape, p: SalParams, E: torch.Tensor | None = None,
+                            stream=None) -> torch.Tensor:
+    """Trilinear interpolation of lattice energies back to every voxel of `shape`: [3, T, X, Y]."""
+    dims = SalDims(*[int(v) for v in shape])
+    if E is None:
+        E = torch.empty((3,) + tuple(int(v) for v in shape), device=Ec.device, dtype=torch.float32)
+    check(N.lib().sal_interpolate_lattice(_dev(Ec, name="Ec"), dims, ctypes.byref(p), _dev(E, name="E"),
+                                          _stream(stream)))
     return E
 
 

@@ -147,9 +147,21 @@ sal_status check_params(const sal_params *p)
     if (p->stencil != SAL_STENCIL_26 && p->stencil != SAL_STENCIL_LINE && p->stencil != SAL_STENCIL_DIAG_TX)
         return fail(SAL_ERR_INVALID_ARG, "bad stencil %d", p->stencil);
     if (!(p->sigma > 0.f) || !isfinite(p->sigma)) return fail(SAL_ERR_INVALID_ARG, "sigma must be finite and > 0");
-    if (p->reserved != 0) return fail(SAL_ERR_INVALID_ARG, "reserved must be 0");
+    if (p->stride < 0 || p->stride > (p->L - 1) / 2)
+        return fail(SAL_ERR_INVALID_ARG, "stride must be 0, 1 or at most (L-1)/2 = %d (cubes overlapping by more than half; got %d)",
+                    (p->L - 1) / 2, p->stride);
     if (!isfinite(p->a) || !isfinite(p->b) || !isfinite(p->c)) return fail(SAL_ERR_INVALID_ARG, "a, b, c must be finite");
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return fail(SAL_ERR_INVALID_ARG, "eps must be finite and >= 0");
+    return SAL_OK;
+}
+
+// Entry points that compute energies one cube per voxel only (their scratch has no room for
+// the lattice energies of a coarse stride).
+sal_status check_unit_stride(const sal_params *p, const char *what)
+{
+    if (p->stride > 1)
+        return fail(SAL_ERR_UNSUPPORTED, "%s computes one cube per voxel; stride %d is served by sal_saliency and by "
+                                         "sal_lattice_energy + sal_interpolate_lattice", what, p->stride);
     return SAL_OK;
 }
 
@@ -197,6 +209,8 @@ WsLayout slab_layout(sal_dims ext)
 
 sal_status energy_dispatch(const float *V, sal_dims d, const sal_params *p, float *E, cudaStream_t s)
 {
+    sal_status st = check_unit_stride(p, "this call");
+    if (st) return st;
     if (p->precision != SAL_PREC_FP32) {
         if (!sal::energy_tc_supported(p->L, p->precision))
             return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for L = %d", p->precision, p->L);
@@ -289,6 +303,7 @@ sal_status check_batch(const sal_volume *vols, int32_t n, const sal_params *p, b
     if (!vols) return fail(SAL_ERR_INVALID_ARG, "vols is NULL");
     if (n < 1 || n > SAL_BATCH_MAX) return fail(SAL_ERR_INVALID_ARG, "batch size must be in [1, %d]", SAL_BATCH_MAX);
     sal_status s = check_params(p);
+    if (!s) s = check_unit_stride(p, "the batched path");
     if (s) return s;
     if (p->precision != SAL_PREC_FP32 && !sal::energy_tc_supported(p->L, p->precision))
         return fail(SAL_ERR_UNSUPPORTED, "precision %d is not available for L = %d", p->precision, p->L);
@@ -444,6 +459,41 @@ sal_status sal_spectral_energy(const float *V, sal_dims dims, const sal_params *
     return s ? s : ok();
 }
 
+sal_status sal_lattice_dims(sal_dims dims, const sal_params *p, sal_dims *lattice)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!lattice) return fail(SAL_ERR_INVALID_ARG, "lattice is NULL");
+    const int st = p->stride > 1 ? p->stride : 1;
+    *lattice = sal_dims{sal::lattice_size(dims.T, st), sal::lattice_size(dims.X, st), sal::lattice_size(dims.Y, st)};
+    return ok();
+}
+
+sal_status sal_lattice_energy(const float *V, sal_dims dims, const sal_params *p, float *Ec, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (p->precision != SAL_PREC_FP32) return fail(SAL_ERR_UNSUPPORTED, "lattice energies are computed in FP32 only");
+    if (!V || !Ec) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(V) || !aligned16(Ec)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    cudaError_t e = sal::launch_lattice_energy(V, dims, p->L, p->boundary, p->stride > 1 ? p->stride : 1, Ec,
+                                               (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_lattice_energy");
+}
+
+sal_status sal_interpolate_lattice(const float *Ec, sal_dims dims, const sal_params *p, float *E, void *stream)
+{
+    sal_status s = check_dims(dims);
+    if (!s) s = check_params(p);
+    if (s) return s;
+    if (!Ec || !E) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!aligned16(Ec) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    cudaError_t e = sal::launch_interp_lattice(Ec, dims, p->stride > 1 ? p->stride : 1, E, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_interpolate_lattice");
+}
+
 sal_status sal_directional_compare(const float *E, sal_dims dims, const sal_params *p, float *Sm, double *stats,
                                    void *ws, size_t ws_bytes, void *stream)
 {
@@ -597,8 +647,18 @@ sal_status sal_saliency(const float *V, sal_dims dims, const sal_params *p, floa
     double *part = (double *)(base + w.partials);
     double *st = stats ? stats : (double *)(base + w.stats);
     cudaStream_t cs = (cudaStream_t)stream;
-    s = energy_dispatch(V, dims, p, E, cs);
-    if (s) return s;
+    if (p->stride > 1) {
+        // coarse stride: the lattice energies go to the S_m region (3 Nc <= 3 N floats, not yet
+        // in use), are interpolated into E, and S_m then overwrites them in stream order
+        if (p->precision != SAL_PREC_FP32)
+            return fail(SAL_ERR_UNSUPPORTED, "stride > 1 is computed in FP32 on the CUDA cores only");
+        cudaError_t e = sal::launch_lattice_energy(V, dims, p->L, p->boundary, p->stride, Sm, cs);
+        if (e == cudaSuccess) e = sal::launch_interp_lattice(Sm, dims, p->stride, E, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "lattice energy / interpolation launch");
+    } else {
+        s = energy_dispatch(V, dims, p, E, cs);
+        if (s) return s;
+    }
     cudaError_t e = sal::launch_dcs(E, dims, p, Sm, part, st, cs);
     if (e != cudaSuccess) return cuda_fail(e, "directional compare launch");
     e = sal::launch_combine(Sm, st, dims, p, S, cs);
@@ -621,6 +681,7 @@ sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_param
 {
     sal_status s = check_dims(dims);
     if (!s) s = check_params(p);
+    if (!s) s = check_unit_stride(p, "sal_saliency_host");
     if (s) return s;
     if (!V_host || !S_host || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
     if (!aligned16(ws) || (stats && !aligned16(stats)))
@@ -838,6 +899,7 @@ sal_status sal_autotune(const float *V, sal_dims dims, const sal_params *p, floa
 {
     sal_status s = check_dims(dims);
     if (!s) s = check_params(p);
+    if (!s) s = check_unit_stride(p, "sal_autotune");
     if (s) return s;
     if (!V || !E || !out) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
     if (!aligned16(V) || !aligned16(E)) return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
@@ -975,6 +1037,7 @@ sal_status sal_surrogate_infer(const float *V, sal_dims dims, const sal_params *
 {
     sal_status s = check_dims(dims);
     if (!s) s = check_params(p);
+    if (!s) s = check_unit_stride(p, "sal_surrogate_infer");
     if (s) return s;
     if (!V || !params || !E || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
     if (!aligned16(V) || !aligned16(E) || !aligned16(ws) || !aligned16(params))

@@ -179,6 +179,11 @@ cudaError_t surrogate_infer(const float *V, sal_dims d, int L, int bnd, const fl
 cudaError_t surrogate_adam(float *params, const float *grads, float *m, float *v, int64_t n, int step, float lr,
                            float b1, float b2, float eps, cudaStream_t s);
 
+// Coarse-stride cubes: lattice size along an axis, E at the lattice points, interpolation back.
+int64_t lattice_size(int64_t n, int s);
+cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, int s, float *Ec, cudaStream_t st);
+cudaError_t launch_interp_lattice(const float *Ec, sal_dims d, int s, float *E, cudaStream_t st);
+
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s);
 

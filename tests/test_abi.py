@@ -60,7 +60,7 @@ def test_workspace_size_grows_with_volume(lib):
     ("precision", 7, N.SAL_ERR_INVALID_ARG), ("boundary", 2, N.SAL_ERR_INVALID_ARG),
     ("stencil", 5, N.SAL_ERR_INVALID_ARG), ("sigma", 0.0, N.SAL_ERR_INVALID_ARG),
     ("sigma", float("nan"), N.SAL_ERR_INVALID_ARG), ("eps", -1.0, N.SAL_ERR_INVALID_ARG),
-    ("reserved", 3, N.SAL_ERR_INVALID_ARG)])
+    ("stride", 4, N.SAL_ERR_INVALID_ARG), ("stride", -1, N.SAL_ERR_INVALID_ARG)])
 def test_bad_params_rejected(lib, field, val, status):
     p = _p(lib, **{field: val})
     n = ctypes.c_size_t()

@@ -21,7 +21,7 @@ def _stitched(V, p, parts):
     slabs = shard.slab_partition(V.shape[0], parts, H)
     Sms, sts = [], []
     for sl in slabs:
-        Sm, st = api.sal_slab_maps(V[sl.ext_lo:sl.ext_hi].contiguous(), dims, sl.ext_lo, sl.ext_hi, sl.own_lo,
+        Sm, st = api.sal_slab_maps(V[sl.ext_lo:sl.ext_hi].clone(), dims, sl.ext_lo, sl.ext_hi, sl.own_lo,
                                    sl.own_hi, p)
         Sms.append(Sm)
         sts.append(st)
@@ -64,8 +64,8 @@ def test_slab_argument_checks():
     H = api.sal_slab_halo(p)
     assert H == 3
     with pytest.raises(api.N.SalError) as ei:     # halo one plane short
-        api.sal_slab_maps(V[2:13].contiguous(), dims, 2, 13, 5, 10, p)
+        api.sal_slab_maps(V[3:13].clone(), dims, 3, 13, 5, 10, p)
     assert ei.value.status == api.N.SAL_ERR_INVALID_ARG
     with pytest.raises(api.N.SalError) as ei:     # a periodic volume cannot be cut along t
-        api.sal_slab_maps(V[2:13].contiguous(), dims, 2, 13, 5, 10, api.params(L=5, boundary="periodic"))
+        api.sal_slab_maps(V[2:13].clone(), dims, 2, 13, 5, 10, api.params(L=5, boundary="periodic"))
     assert ei.value.status == api.N.SAL_ERR_UNSUPPORTED
