@@ -73,6 +73,47 @@ def algorithmic_flops_per_voxel(L: int, R: int = 4, BX: int = 8) -> float:
     return real_pass + (x_real + H * x_cplx) + y + 3
 
 
+def lattice_size(n: int, s: int) -> int:
+    return 1 if n <= 1 else (n - 2) // s + 2
+
+
+def lattice_kernel_work(shape, L: int, s: int):
+    """(FP32 flops on the FMA pipe, square roots) of one lattice-energy launch, counted from
+    the kernel's own loops: per CTA of nj x nk lattice points and its RX x RY region, for each
+    mu = 0..h, stage t (L taps, real in, complex out), stage x (L taps, complex) at the lattice
+    x, and the folded stage y per (point, nu) line with |F| and the weights."""
+    H = (L - 1) // 2
+    BJ, BK = 8, 16
+    while True:                                         # the launcher's block choice
+        RXM, RYM = (BJ - 1) * s + L, (BK - 1) * s + L
+        need = 4 * (((L * RXM * RYM + 3) & ~3) + 2 * RXM * RYM + 2 * L * BJ * RYM + 3 * BJ * BK * L)
+        if need <= 200 * 1024 or (BJ == 1 and BK == 1):
+            break
+        if BK >= BJ and BK > 1:
+            BK //= 2
+        else:
+            BJ //= 2
+
+    def blocks(n, B):
+        nc = lattice_size(n, s)
+        coord = lambda i: min(i * s, n - 1)
+        sizes, regions = [], []
+        for b0 in range(0, nc, B):
+            nb = min(B, nc - b0)
+            sizes.append(nb)
+            regions.append(coord(b0 + nb - 1) - coord(b0) + 2 * H + 1)
+        return np.array(sizes), np.array(regions)
+
+    nj, RX = blocks(shape[1], BJ)
+    nk, RY = blocks(shape[2], BK)
+    Tc = lattice_size(shape[0], s)
+    per_item = 8 * H * H + 23 * H + 15
+    per_mu = 4 * L * RX.sum() * RY.sum() + 8 * L * L * nj.sum() * RY.sum() + nj.sum() * nk.sum() * L * per_item
+    flops = Tc * ((H + 1) * per_mu + 3 * nj.sum() * nk.sum() * L)
+    sqrts = Tc * (H + 1) * nj.sum() * nk.sum() * L * (1 + 2 * H)
+    return float(flops - sqrts), float(sqrts)
+
+
 def mufu_per_voxel(L: int) -> int:
     """Square roots (MUFU sqrt.approx) per voxel of the energy kernel: one per |F| of the half
     spectrum it forms, (L^3 - 1) / 2 (algorithmic_flops_per_voxel counts each as one flop)."""
@@ -264,8 +305,10 @@ def workload_config(args) -> dict:
                 "volumes": 64, "voxels": nv, "L": args.L, "precision": args.precision, "boundary": "reflect",
                 "stencil": "26", "l2": "flush buffer (512 MB) written between steps"}
     shape = WORKLOADS[args.workload][0]
+    stride = f", cubes at stride {args.stride} (E interpolated back)" if getattr(args, "stride", 1) > 1 else ""
     return {"workload": f"plain method {args.precision.upper()}, {'F3-shaped' if args.workload == 'f3' else 'synthetic'}"
-                        f" volume {shape[0]}x{shape[1]}x{shape[2]}, local cube {args.L}, 26-neighbourhood",
+                        f" volume {shape[0]}x{shape[1]}x{shape[2]}, local cube {args.L}, 26-neighbourhood{stride}",
+            "stride": getattr(args, "stride", 1),
             "volume": list(shape), "L": args.L, "precision": args.precision, "boundary": "reflect",
             "stencil": "26", "l2": "inputs larger than L2 (V 1.14 GB, E and S_m 3.4 GB each); no flush needed"
             if args.workload == "f3" else "flush buffer written between steps"}
@@ -349,7 +392,8 @@ def run_batch(args, rank: int, world: int) -> None:
 
 def run_sweep(args) -> None:
     """Precision sweep on a 256^3 volume: every precision at L = 5, 7, 9, 11, each a JSON line
-    with its speed and its error per map against the FP64 oracle at sampled voxels."""
+    with its speed and its error against the whole-volume FP64 oracle, per component map
+    (E_m and S_m, normwise) and for the final saliency map (normwise and relative L2)."""
     import torch
 
     import oracle
@@ -360,15 +404,16 @@ def run_sweep(args) -> None:
     V_np = synth.make_volume(shape, seed=2)
     V = torch.from_numpy(V_np).to(dev)
     N = V_np.size
-    rng = np.random.default_rng(0)
-    coords = np.stack([rng.integers(0, s, 1500) for s in shape], axis=1)
-    faces = np.array([[0, 0, 0], [255, 255, 255], [0, 128, 255], [255, 0, 7]])
-    coords = np.concatenate([coords, faces]).astype(np.int64)
-    idx = torch.from_numpy(coords).to(dev)
     stream = torch.cuda.current_stream(dev)
+    cores = cpu_cores()
+
+    def nerr(got, ref):
+        return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
     for L in (5, 7, 9, 11):
-        E_ref, Sm_ref = oracle.maps_at(V_np, coords, L)
-        S_fp32 = None
+        t0 = time.perf_counter()
+        S_ref, E_ref, Sm_ref, _ = oracle.saliency(V_np, L=L, threads=cores, full=True)
+        oracle_s = time.perf_counter() - t0
         for prec in ("fp32", "tf32", "bf16"):
             p = api.params(L=L, precision=prec)
             E = torch.empty((3,) + shape, device=dev)
@@ -391,20 +436,17 @@ def run_sweep(args) -> None:
             k1_ms = e0.elapsed_time(e1) / args.steps
             path_ms = e1.elapsed_time(e2) / args.steps
             err = {}
+            Eh, Smh, Sh = E.double().cpu().numpy(), Sm.double().cpu().numpy(), S.double().cpu().numpy()
             for m, name in enumerate("txy"):
-                e = E[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
-                s_ = Sm[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
-                err[f"E_{name}"] = float(np.abs(e - E_ref[m]).max() / np.abs(E_ref[m]).max())
-                err[f"S_{name}"] = float(np.abs(s_ - Sm_ref[m]).max() / np.abs(Sm_ref[m]).max())
-            if prec == "fp32":
-                S_fp32 = S.clone()
-            else:
-                err["S_vs_fp32_relL2"] = float(torch.linalg.vector_norm((S - S_fp32).double()) /
-                                               torch.linalg.vector_norm(S_fp32.double()))
+                err[f"E_{name}"] = nerr(Eh[m], E_ref[m])
+                err[f"S_{name}"] = nerr(Smh[m], Sm_ref[m])
+            err["S"] = nerr(Sh, S_ref)
+            err["S_relL2"] = float(np.linalg.norm(Sh - S_ref) / np.linalg.norm(S_ref))
             print(json.dumps({"sweep": "precision", "volume": list(shape), "L": L, "precision": prec,
                               "voxels_per_s": N / (path_ms / 1e3), "ms_per_step": path_ms,
-                              "spectral_energy_ms": k1_ms, "errors_vs_oracle_sampled": err,
-                              "samples": int(coords.shape[0])}), flush=True)
+                              "spectral_energy_ms": k1_ms, "errors_vs_oracle": err,
+                              "oracle": {"whole volume": True, "seconds": oracle_s, "cores": cores}}), flush=True)
+            del E, Sm, S, ws
 
 
 def run_surrogate(args) -> None:
@@ -556,9 +598,11 @@ def run_ours(args, rank: int, world: int) -> None:
     shape, kind, seed = WORKLOADS[args.workload]
     V_np = synth.make_volume(shape, seed=seed + rank, kind=kind)
     N = V_np.size
-    p = api.params(L=args.L, precision=args.precision)
+    p = api.params(L=args.L, precision=args.precision, stride=args.stride)
     V = torch.from_numpy(V_np).to(dev)
     E = torch.empty((3,) + shape, device=dev, dtype=torch.float32)
+    lat = api.sal_lattice_dims(api.dims_of(V), p)
+    Ec = torch.empty((3, lat.T, lat.X, lat.Y), device=dev, dtype=torch.float32) if args.stride > 1 else None
     Sm = torch.empty_like(E)
     S = torch.empty(shape, device=dev, dtype=torch.float32)
     stats = torch.empty(9, device=dev, dtype=torch.float64)
@@ -573,7 +617,11 @@ def run_ours(args, rank: int, world: int) -> None:
             flush.zero_()
         if ev is not None:
             ev[0].record(stream)
-        api.sal_spectral_energy(V, p, E=E, stream=stream)
+        if Ec is not None:          # coarse stride: lattice energies, then interpolation to every voxel
+            api.sal_lattice_energy(V, p, Ec=Ec, stream=stream)
+            api.sal_interpolate_lattice(Ec, shape, p, E=E, stream=stream)
+        else:
+            api.sal_spectral_energy(V, p, E=E, stream=stream)
         if ev is not None:
             ev[1].record(stream)
         api.sal_directional_compare(E, p, Sm=Sm, stats=stats, ws=ws_dcs, stream=stream)
@@ -660,7 +708,19 @@ def run_ours(args, rank: int, world: int) -> None:
     k2_gbs = 24 * N / (statistics.mean(k2) / 1e3) / 1e9
     k4_gbs = 16 * N / (statistics.mean(k4) / 1e3) / 1e9
     traffic = ENERGY_TRAFFIC.get((args.workload, args.L, args.precision))
-    if args.precision == "fp32":
+    if args.stride > 1:
+        lflops, lsqrt = lattice_kernel_work(shape, args.L, args.stride)
+        mhz = clk.summary()["sm_mhz"] or sm_max
+        roofline = {"bound": "alu", "kernel": f"lattice energies (cubes at stride {args.stride}) + trilinear "
+                                              "interpolation back to every voxel",
+                    "achieved": lflops / (k1_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": lflops / (k1_ms / 1e3) / 1e12 / alu_peak, "traffic": None, "traffic_source": None,
+                    "peak_source": f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x {sm_max:.0f} MHz",
+                    "flops_per_launch": lflops, "lattice_points": int(lat.T * lat.X * lat.Y),
+                    "xu": {"sqrt_per_launch": lsqrt, "frac": lsqrt / (k1_ms / 1e3) / (nsm * MUFU_PER_SM_CLK * mhz * 1e6)},
+                    "note": "time of both launches (lattice energies and interpolation) against the lattice kernel's "
+                            "own flops; the interpolation writes 12 B per voxel"}
+    elif args.precision == "fp32":
         clk_sum = clk.summary()
         mhz = clk_sum["sm_mhz"] or sm_max
         xu_peak = nsm * MUFU_PER_SM_CLK * mhz * 1e6                  # square roots per second
@@ -724,7 +784,7 @@ def run_ours(args, rank: int, world: int) -> None:
                        "bytes_per_voxel": {"directional_compare": 24, "combine": 16}},
         "e2e": {"value": job_rate(world, N, e2e_ms), "unit": "voxels/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "ms_per_step": e2e_ms},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": (6 if args.stride > 1 else 5) * args.steps,
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
@@ -742,6 +802,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="f3")
     ap.add_argument("--L", type=int, default=7)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
+    ap.add_argument("--stride", type=int, default=1, help="cube stride (coarse-stride cubes, E interpolated back)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fma-probe", action="store_true", help="skip the FP32 FMA-rate probe")

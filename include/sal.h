@@ -83,9 +83,10 @@ typedef struct {
     int32_t stride;     /* cube centres (Sec. 2, first step: the cube slides with more than 50 %
                            overlap): 0 or 1 = one cube per voxel; s in 2..(L-1)/2 = cubes centred
                            on the lattice min(i s, n - 1) of every axis, E interpolated
-                           trilinearly back to every voxel (sal_saliency and the split calls
-                           sal_lattice_energy / sal_interpolate_lattice; FP32 only; other
-                           entry points return SAL_ERR_UNSUPPORTED for s > 1) */
+                           trilinearly back to every voxel (sal_saliency, sal_saliency_host
+                           and the split calls sal_lattice_energy / sal_interpolate_lattice;
+                           FP32 only; the other energy entry points return
+                           SAL_ERR_UNSUPPORTED for s > 1) */
     double a, b, c;     /* Eq. 6 weights of S_t, S_x, S_y (equal in the paper) */
     double eps;         /* relative range below which a map counts as constant */
 } sal_params;

@@ -681,8 +681,9 @@ sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_param
 {
     sal_status s = check_dims(dims);
     if (!s) s = check_params(p);
-    if (!s) s = check_unit_stride(p, "sal_saliency_host");
     if (s) return s;
+    if (p->stride > 1 && p->precision != SAL_PREC_FP32)
+        return fail(SAL_ERR_UNSUPPORTED, "stride > 1 is computed in FP32 on the CUDA cores only");
     if (!V_host || !S_host || !ws) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");
     if (!aligned16(ws) || (stats && !aligned16(stats)))
         return fail(SAL_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
@@ -719,7 +720,7 @@ sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_param
     e = cudaStreamWaitEvent(hp.h2d, hp.v_free[b], 0);
     if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
     const int64_t XY = dims.X * dims.Y;
-    if (p->precision == SAL_PREC_FP32 && dims.T >= 64) {
+    if (p->precision == SAL_PREC_FP32 && dims.T >= 64 && p->stride <= 1) {
         // V in pieces of whole planes (multiples of 16, so of every tile height); the energies
         // of a piece's output planes start once it and the next piece (its halo) are in
         int64_t lo[kHostChunks + 1];
@@ -751,8 +752,15 @@ sal_status sal_saliency_host(const float *V_host, sal_dims dims, const sal_param
         if (e == cudaSuccess) e = cudaEventRecord(hp.v_ready, hp.h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, hp.v_ready, 0);
         if (e != cudaSuccess) return cuda_fail(e, "copy of V to the device");
-        s = energy_dispatch(Vd, dims, p, E, cs);
-        if (s) return s;
+        if (p->stride > 1) {
+            // lattice energies in the S_m region (free until the compare), interpolated into E
+            e = sal::launch_lattice_energy(Vd, dims, p->L, p->boundary, p->stride, Sm, cs);
+            if (e == cudaSuccess) e = sal::launch_interp_lattice(Sm, dims, p->stride, E, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "lattice energy / interpolation launch");
+        } else {
+            s = energy_dispatch(Vd, dims, p, E, cs);
+            if (s) return s;
+        }
     }
     e = cudaEventRecord(hp.v_free[b], cs);
     if (e == cudaSuccess) e = sal::launch_dcs(E, dims, p, Sm, part, st, cs);

@@ -66,3 +66,31 @@ def test_saliency_properties(f3_run):
     st = stats.cpu().numpy().reshape(3, 3)
     for m in range(3):
         assert float(Sm[m].max()) == st[m, 1] and float(Sm[m].min()) == st[m, 0]
+
+
+TOL_E_BF16 = 1e-2       # BF16 operands: 8 significant bits per sample of the y-stage products
+TOL_S_BF16 = 2e-2       # the stated relative-L2 bar of the BF16 saliency
+
+
+def test_bf16_sampled_maps_match_oracle(f3_run):
+    """The tensor-core form (BF16 operands, FP32 accumulation) on the full F3-shaped volume:
+    E_m and S_m at the sampled voxels against the oracle, and S against the FP32 path (itself
+    within 1e-4 of the oracle by the FP32 tests) by relative L2."""
+    V, E32, Sm32, stats32, S32, _ = f3_run
+    dev = E32.device
+    p = api.params(L=7, precision="bf16")
+    Vd = torch.from_numpy(V).to(dev)
+    E = api.sal_spectral_energy(Vd, p)
+    Sm, stats = api.sal_directional_compare(E, p)
+    S = api.sal_combine(Sm, stats, p)
+    api.sal_device_status()
+    c = _coords(seed=1)
+    E_ref, Sm_ref = O.maps_at(V, c, 7)
+    idx = torch.from_numpy(c).to(dev)
+    for m in range(3):
+        e = E[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+        s = Sm[m][idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+        assert np.abs(e - E_ref[m]).max() / np.abs(E_ref[m]).max() < TOL_E_BF16, m
+        assert np.abs(s - Sm_ref[m]).max() / np.abs(Sm_ref[m]).max() < TOL_E_BF16, m
+    rel = float(torch.linalg.vector_norm((S - S32).double()) / torch.linalg.vector_norm(S32.double()))
+    assert rel < TOL_S_BF16, rel

@@ -92,3 +92,13 @@ def test_stride_needs_the_calls_with_room_for_the_lattice():
     with pytest.raises(api.N.SalError) as ei:
         api.sal_saliency(V, api.params(L=7, stride=2, precision="bf16"))
     assert ei.value.status == api.N.SAL_ERR_UNSUPPORTED
+
+
+def test_strided_host_buffers_equal_device_call():
+    V = synth.make_volume((70, 40, 66), seed=11)
+    p = api.params(L=7, stride=3)
+    S_dev, _ = api.sal_saliency(to_dev(V), p)
+    Vh = torch.from_numpy(V).pin_memory()
+    S_host = api.sal_saliency_host(Vh, p)
+    torch.cuda.synchronize()
+    assert torch.equal(S_host, S_dev.cpu())

@@ -103,3 +103,21 @@ def test_tc_wait_timeout_is_reported_and_recovers():
     again = api.sal_spectral_energy(V, p)
     api.sal_device_status()
     assert torch.equal(again, ref)
+
+
+def test_bf16_batch_members_match_oracle():
+    """The batched configuration (64 uneven volumes, axes U[32, 192], BF16, one persistent launch
+    per stage): two members, the smallest and one of median size, against the oracle's S."""
+    shapes = synth.batch_shapes()
+    vols = [synth.make_volume(s, seed=i) for i, s in enumerate(shapes)]
+    Vs = [torch.from_numpy(v).to(DEV) for v in vols]
+    p = api.params(L=7, precision="bf16")
+    Ss, _ = api.sal_saliency_batched(Vs, p)
+    api.sal_device_status()
+    sizes = [v.size for v in vols]
+    order = np.argsort(sizes)
+    for i in (int(order[0]), int(order[len(order) // 2])):
+        S_ref = O.saliency(vols[i], L=7)
+        err = l2err(Ss[i].cpu().numpy(), S_ref)
+        print(f"batch member {i} {shapes[i]}: S rel-L2 {err:.2e}")
+        assert err < TOL_S["bf16"]
