@@ -471,11 +471,34 @@ def run_surrogate(args) -> None:
     t_data = time.perf_counter() - t0
     model = surrogate.Surrogate(dev, seed=0)
     t0 = time.perf_counter()
-    hist = surrogate.train(model, vols, labels, steps=args.train_steps, crop=48, lr=3e-3, lr_final=3e-4, seed=1,
+    hist = surrogate.train(model, vols, labels, steps=args.train_steps, crop=48, lr=args.train_lr,
+                           lr_final=args.train_lr_final, seed=1,
                            log_every=max(1, args.train_steps // 20))
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
-    del vols, labels
+
+    # held-out accuracy (volumes not trained on) against the plain method, next to the error on
+    # training volumes and the untrained network's (the gain of training), and the fraction of
+    # check blocks kept per threshold
+    def rel_errs(m_, V_, E_):
+        P = m_.forward(V_, training=True)
+        return [float(torch.linalg.vector_norm((P[c] - E_[c]).double()) / torch.linalg.vector_norm(E_[c].double()))
+                for c in range(3)]
+
+    untrained = surrogate.Surrogate(dev, seed=0)
+    held = [torch.from_numpy(synth.make_volume((128, 128, 128), seed=900 + i, kind="f3")).to(dev) for i in range(4)]
+    held_E = [api.sal_spectral_energy(V, p) for V in held]
+    accuracy = {"held_out_rel_l2": np.mean([rel_errs(model, V, E) for V, E in zip(held, held_E)], axis=0).tolist(),
+                "train_rel_l2": np.mean([rel_errs(model, V, E) for V, E in zip(vols[:4], labels[:4])], axis=0).tolist(),
+                "untrained_held_out_rel_l2": np.mean([rel_errs(untrained, V, E) for V, E in zip(held, held_E)],
+                                                     axis=0).tolist()}
+    kept = {}
+    for thr in (2e-2, 5e-2, 1e-1, 2e-1, 5e-1):
+        c_tr = model.infer(held[0], threshold=thr)[1].cpu().numpy()
+        c_un = untrained.infer(held[0], threshold=thr)[1].cpu().numpy()
+        kept[f"{thr:g}"] = {"trained": 1.0 - c_tr[0] / c_tr[1], "untrained": 1.0 - c_un[0] / c_un[1]}
+    accuracy["blocks_kept_held_out"] = kept
+    del vols, labels, held, held_E
 
     shape, kind, seed = WORKLOADS["f3"]
     V = torch.from_numpy(synth.make_volume(shape, seed=seed, kind=kind)).to(dev)
@@ -507,7 +530,8 @@ def run_surrogate(args) -> None:
                                   f"inference on the F3-shaped {shape[0]}x{shape[1]}x{shape[2]} volume, L={args.L}"},
            "training": {"volumes": args.train_volumes, "steps": args.train_steps, "crop": 48,
                         "seconds": t_train, "label_seconds": t_data, "loss_first": hist[0][1],
-                        "loss_last": hist[-1][1]}}
+                        "loss_last": hist[-1][1], "lr": [args.train_lr, args.train_lr_final]},
+           "accuracy": accuracy}
     for name, thr, pp in (("fallback_2e-2", 2e-2, p), ("surrogate_only", 1e30, p),
                           ("fallback_2e-2_tensor_cores", 2e-2, p_tc), ("surrogate_only_tensor_cores", 1e30, p_tc)):
         counts = surr_path(thr, pp)
@@ -814,6 +838,8 @@ def main():
     ap.add_argument("--surrogate-shape", default="128x128x256", help="T x X x Y of --surrogate-forward")
     ap.add_argument("--train-volumes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-lr", type=float, default=3e-3)
+    ap.add_argument("--train-lr-final", type=float, default=3e-4)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

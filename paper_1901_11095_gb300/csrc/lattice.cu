@@ -35,13 +35,65 @@ struct LatGeo {
     int64_t Tc, Xc, Yc;
 };
 
-// Shared memory of one CTA, in floats: the V region (rounded up to 16 bytes so the complex
-// arrays after it stay aligned), G1 and G2 (complex), the per-(point, nu) sums of three maps.
-__host__ __device__ inline size_t lat_region_floats(int L, int RXM, int RYM) { return ((size_t)L * RXM * RYM + 3) & ~(size_t)3; }
+// Shared memory of one CTA, in floats: G1 of every mu (complex), then a region that first
+// holds the V samples and, once stage t has consumed them, G2 of one mu (complex); both
+// rounded up to 16 bytes.
+__host__ __device__ inline size_t lat_g1_floats(int L, int RXM, int RYM) { return 2 * (size_t)((L + 1) / 2) * RXM * RYM; }
+__host__ __device__ inline size_t lat_reg_floats(int L, int BJ, int RXM, int RYM)
+{
+    const size_t v = (size_t)L * RXM * RYM, g2 = 2 * (size_t)L * BJ * RYM;
+    return ((v > g2 ? v : g2) + 3) & ~(size_t)3;
+}
 inline size_t lat_smem_bytes(int L, int BJ, int BK, int RXM, int RYM)
 {
-    return sizeof(float) * (lat_region_floats(L, RXM, RYM) + 2 * (size_t)RXM * RYM + 2 * (size_t)L * BJ * RYM +
-                            3 * (size_t)BJ * BK * L);
+    return sizeof(float) * (lat_g1_floats(L, RXM, RYM) + lat_reg_floats(L, BJ, RXM, RYM) + 3 * (size_t)BJ * BK * L);
+}
+
+// cos and sin of 2 pi k / L for k = 0..L-1 (compile-time indices once unrolled).
+template <int L>
+struct LatTw {
+    float c[L], s[L];
+    __device__ __forceinline__ void load(const SpecTables &tb)
+    {
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            c[k] = tb.cs[k];
+            s[k] = tb.sn[k];
+        }
+    }
+};
+
+// Folded length-L DFT of the complex samples z[0..L-1] (centre z[H]): out[H + f] = F(f) =
+// sum_r z[r] e^{-i th f (r - H)}, f = -H..H.  U_r = z(+r) + z(-r), D_r = z(+r) - z(-r);
+// F(+-f) = A -+ iB with A = z0 + sum U_r cos(th f r), B = sum D_r sin(th f r).
+template <int L>
+__device__ __forceinline__ void folded_dft(const float2 (&z)[L], const LatTw<L> &tw, float2 (&out)[L])
+{
+    constexpr int H = (L - 1) / 2;
+    float2 U[H + 1], D[H + 1];
+    float2 s0 = z[H];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+        U[r] = make_float2(z[H + r].x + z[H - r].x, z[H + r].y + z[H - r].y);
+        D[r] = make_float2(z[H + r].x - z[H - r].x, z[H + r].y - z[H - r].y);
+        s0.x += U[r].x;
+        s0.y += U[r].y;
+    }
+    out[H] = s0;
+#pragma unroll
+    for (int f = 1; f <= H; ++f) {
+        float2 A = z[H], B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            const int k = (f * r) % L;
+            A.x = fmaf(U[r].x, tw.c[k], A.x);
+            A.y = fmaf(U[r].y, tw.c[k], A.y);
+            B.x = fmaf(D[r].x, tw.s[k], B.x);
+            B.y = fmaf(D[r].y, tw.s[k], B.y);
+        }
+        out[H + f] = make_float2(A.x + B.y, A.y - B.x);   // A - iB
+        out[H - f] = make_float2(A.x - B.y, A.y + B.x);   // A + iB
+    }
 }
 
 template <int L>
@@ -51,6 +103,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
                                                                      const __grid_constant__ SpecTables tb)
 {
     constexpr int H = (L - 1) / 2;
+    constexpr int MAXIT = 4;   // stage-y items per thread (checked by the launcher)
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
     int64_t b = blockIdx.x;
@@ -64,116 +117,166 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     const int64_t xlo = lattice_coord(j0, X, g.s) - H, ylo = lattice_coord(k0, Y, g.s) - H;
     const int RX = (int)(lattice_coord(j0 + nj - 1, X, g.s) + H - xlo + 1);
     const int RY = (int)(lattice_coord(k0 + nk - 1, Y, g.s) + H - ylo + 1);
-    const int P = g.RYM;                                   // row pitch of the region (floats / float2)
+    const int P = g.RYM;                                   // row pitch (floats or float2)
+    const int PL = g.RXM * P;                              // plane pitch of the V region / one G1 mu
 
-    float *sV = smem;                                      // [L][RXM][P]
-    float2 *sG1 = reinterpret_cast<float2 *>(sV + lat_region_floats(L, g.RXM, P));   // [RXM][P]
-    float2 *sG2 = sG1 + (size_t)g.RXM * P;                 // [L (nu)][BJ][P]
-    float *acc = reinterpret_cast<float *>(sG2 + (size_t)L * g.BJ * P);      // [3][BJ * BK * L]
-    const int nitems = nj * nk * L;                        // (point, nu) items of stage y
+    float2 *sG1 = reinterpret_cast<float2 *>(smem);                                   // [H+1][RXM][P]
+    float *sV = smem + lat_g1_floats(L, g.RXM, g.RYM);                                // [L][RXM][P]
+    float2 *sG2 = reinterpret_cast<float2 *>(sV);                                     // [L (nu)][BJ][P], after stage t
+    float *sacc = sV + lat_reg_floats(L, g.BJ, g.RXM, g.RYM);                         // [3][BJ * BK * L]
+    const int nitems = nj * nk * L;
     const int accn = g.BJ * g.BK * L;
 
-    // the region of V, relative to one sample of it, with the boundary extension
+    LatTw<L> tw;
+    tw.load(tb);
+
+    // the V region, relative to one sample of it, by asynchronous 4-byte copies; coordinates
+    // advance without divisions, and the boundary extension is taken only outside the volume
     const float ref = V[(tc * X + (xlo + H)) * Y + (ylo + H)];
-    for (int e = tid; e < L * RX * RY; e += kLatThreads) {
-        const int p = e / (RX * RY), rem = e - p * (RX * RY), q = rem / RY, r = rem - q * RY;
-        const int64_t gt = ext_index(tc - H + p, T, bnd), gx = ext_index(xlo + q, X, bnd), gy = ext_index(ylo + r, Y, bnd);
-        sV[(p * g.RXM + q) * P + r] = V[(gt * X + gx) * Y + gy] - ref;
+    {
+        const bool inside = tc - H >= 0 && tc + H < T && xlo >= 0 && xlo + RX <= X && ylo >= 0 && ylo + RY <= Y;
+        int r = tid % RY, q = (tid / RY) % RX, p = tid / (RX * RY);
+        const int dr = kLatThreads % RY, dq = (kLatThreads / RY) % RX, dp = kLatThreads / (RX * RY);
+        for (int e = tid; e < L * RX * RY; e += kLatThreads) {
+            int64_t gt = tc - H + p, gx = xlo + q, gy = ylo + r;
+            if (!inside) {
+                if ((uint64_t)gt >= (uint64_t)T) gt = ext_index(gt, T, bnd);
+                if ((uint64_t)gx >= (uint64_t)X) gx = ext_index(gx, X, bnd);
+                if ((uint64_t)gy >= (uint64_t)Y) gy = ext_index(gy, Y, bnd);
+            }
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(sV + p * PL + q * P + r);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(V + (gt * X + gx) * Y + gy) : "memory");
+            r += dr;
+            q += dq;
+            p += dp;
+            if (r >= RY) {
+                r -= RY;
+                ++q;
+            }
+            if (q >= RX) {
+                q -= RX;
+                ++p;
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
-    for (int e = tid; e < 3 * accn; e += kLatThreads) acc[e] = 0.f;
     __syncthreads();
 
-    for (int mu = 0; mu <= H; ++mu) {
-        // stage t: G1 of every column of the region
+    // stage t, every mu at once: G1[mu](x', y') for each column of the region (real input:
+    // folded, G1(mu) = A - iB with A = sum_p (a(+p) + a(-p) - 2 a0) cos, B = sum (a(+p) - a(-p)) sin)
+    {
+        int r = tid % RY, q = tid / RY;
+        const int dr = kLatThreads % RY, dq = kLatThreads / RY;
         for (int e = tid; e < RX * RY; e += kLatThreads) {
-            const int q = e / RY, r = e - q * RY;
-            float re = 0.f, im = 0.f;
+            float a[L];
 #pragma unroll
-            for (int p = 0; p < L; ++p) {
-                const int k = ((mu * (p - H)) % L + L) % L;       // e^{-i th k} = cs[k] - i sn[k]
-                const float v = sV[(p * g.RXM + q) * P + r];
-                re = fmaf(v, tb.cs[k], re);
-                im = fmaf(-v, tb.sn[k], im);
+            for (int p = 0; p < L; ++p) a[p] = sV[p * PL + q * P + r] - ref;
+            float U[H + 1], D[H + 1], s0 = a[H];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                U[k] = a[H + k] + a[H - k];
+                D[k] = a[H + k] - a[H - k];
+                s0 += U[k];
             }
-            sG1[q * P + r] = make_float2(re, im);
+            float2 *o = sG1 + q * P + r;
+            o[0] = make_float2(s0, 0.f);
+#pragma unroll
+            for (int mu = 1; mu <= H; ++mu) {
+                float A = a[H], B = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(U[k], tw.c[(mu * k) % L], A);
+                    B = fmaf(D[k], tw.s[(mu * k) % L], B);
+                }
+                o[mu * PL] = make_float2(A, -B);
+            }
+            r += dr;
+            q += dq;
+            if (r >= RY) {
+                r -= RY;
+                ++q;
+            }
         }
-        __syncthreads();
-        // stage x: G2 of every nu at the lattice x of this CTA, every column y'
-        for (int e = tid; e < L * nj * RY; e += kLatThreads) {
-            const int nu = e / (nj * RY), rem = e - nu * (nj * RY), j = rem / RY, r = rem - j * RY;
-            const int xq = (int)(lattice_coord(j0 + j, X, g.s) - H - xlo);
-            const int nus = nu - H;
-            float re = 0.f, im = 0.f;
+    }
+    __syncthreads();
+
+    // stage-y items of this thread (the same for every mu): item it = nu * npts + point, so
+    // the lanes of a warp read neighbouring points of one line (few shared-memory bank
+    // conflicts); line offset into sG2 (without the nu part) and the weight row
+    const int npts = nj * nk;
+    float acc[MAXIT][3];
+    int ioff[MAXIT], inu[MAXIT];
 #pragma unroll
-            for (int q = 0; q < L; ++q) {
-                const int k = ((nus * (q - H)) % L + L) % L;
-                const float2 z = sG1[(xq + q) * P + r];
-                const float c = tb.cs[k], sn = tb.sn[k];
-                re = fmaf(z.x, c, fmaf(z.y, sn, re));            // (zr + i zi)(c - i s)
-                im = fmaf(z.y, c, fmaf(-z.x, sn, im));
-            }
-            sG2[(nu * g.BJ + j) * P + r] = make_float2(re, im);
+    for (int kk = 0; kk < MAXIT; ++kk) {
+        acc[kk][0] = acc[kk][1] = acc[kk][2] = 0.f;
+        const int it = tid + kk * kLatThreads;
+        const int nu = it / npts, pt = it - nu * npts, j = pt / nk, k = pt - j * nk;
+        inu[kk] = nu;
+        ioff[kk] = j * P + (int)(lattice_coord(k0 + k, Y, g.s) - H - ylo);
+    }
+
+#pragma unroll 1
+    for (int mu = 0; mu <= H; ++mu) {
+        // stage x at the lattice x of this CTA: every nu of a column window at once
+        const float2 *g1 = sG1 + mu * PL;
+        for (int e = tid; e < nj * RY; e += kLatThreads) {
+            const int j = e / RY, r = e - j * RY;
+            const int xq = (int)(lattice_coord(j0 + j, X, g.s) - H - xlo);
+            float2 z[L], out[L];
+#pragma unroll
+            for (int q = 0; q < L; ++q) z[q] = g1[(xq + q) * P + r];
+            folded_dft<L>(z, tw, out);
+#pragma unroll
+            for (int nu = 0; nu < L; ++nu) sG2[(nu * g.BJ + j) * P + r] = out[nu];
         }
         __syncthreads();
         // stage y: the folded DFT of each (point, nu) line at the lattice y, |F|, weights
         const float mult = mu == 0 ? 1.f : 2.f;
-        for (int it = tid; it < nitems; it += kLatThreads) {
-            const int nu = it % L, pt = it / L, j = pt / nk, k = pt - j * nk;
-            const int yq = (int)(lattice_coord(k0 + k, Y, g.s) - H - ylo);
-            const float2 *line = sG2 + (nu * g.BJ + j) * P + yq;
-            const float2 z0 = line[H];
-            float2 U[H + 1], D[H + 1];
-            float2 s0 = z0;
 #pragma unroll
-            for (int r = 1; r <= H; ++r) {
-                const float2 a = line[H + r], c = line[H - r];
-                U[r] = make_float2(a.x + c.x, a.y + c.y);
-                D[r] = make_float2(a.x - c.x, a.y - c.y);
-                s0.x += U[r].x;
-                s0.y += U[r].y;
-            }
+        for (int kk = 0; kk < MAXIT; ++kk) {
+            if (tid + kk * kLatThreads >= nitems) break;
+            const int nu = inu[kk];
+            const float2 *line = sG2 + nu * g.BJ * P + ioff[kk];
+            float2 z[L], F[L];
+#pragma unroll
+            for (int r = 0; r < L; ++r) z[r] = line[r];
+            folded_dft<L>(z, tw, F);
             const int anu = nu >= H ? nu - H : H - nu;
             const float *w0 = tb.w + ((mu * kMaxHalf + anu) * kMaxHalf) * 3;
             float et = 0.f, ex = 0.f, ey = 0.f;
-            {
-                const float m0 = sqrtf(fmaf(s0.x, s0.x, s0.y * s0.y));
-                et = fmaf(w0[0], m0, et);
-                ex = fmaf(w0[1], m0, ex);
-                ey = fmaf(w0[2], m0, ey);
-            }
 #pragma unroll
-            for (int om = 1; om <= H; ++om) {
-                float2 A = z0, B = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int r = 1; r <= H; ++r) {
-                    const int k = (om * r) % L;
-                    A.x = fmaf(U[r].x, tb.cs[k], A.x);
-                    A.y = fmaf(U[r].y, tb.cs[k], A.y);
-                    B.x = fmaf(D[r].x, tb.sn[k], B.x);
-                    B.y = fmaf(D[r].y, tb.sn[k], B.y);
-                }
-                // F(+om) = A - iB, F(-om) = A + iB
-                const float pr = A.x + B.y, pi = A.y - B.x, qr = A.x - B.y, qi = A.y + B.x;
-                const float m = sqrtf(fmaf(pr, pr, pi * pi)) + sqrtf(fmaf(qr, qr, qi * qi));
+            for (int om = 0; om <= H; ++om) {
+                float m = sqrtf(fmaf(F[H + om].x, F[H + om].x, F[H + om].y * F[H + om].y));
+                if (om) m += sqrtf(fmaf(F[H - om].x, F[H - om].x, F[H - om].y * F[H - om].y));
                 const float *w = w0 + om * 3;
                 et = fmaf(w[0], m, et);
                 ex = fmaf(w[1], m, ex);
                 ey = fmaf(w[2], m, ey);
             }
-            const int slot = (j * g.BK + k) * L + nu;
-            acc[slot] = fmaf(mult, et, acc[slot]);
-            acc[accn + slot] = fmaf(mult, ex, acc[accn + slot]);
-            acc[2 * accn + slot] = fmaf(mult, ey, acc[2 * accn + slot]);
+            acc[kk][0] = fmaf(mult, et, acc[kk][0]);
+            acc[kk][1] = fmaf(mult, ex, acc[kk][1]);
+            acc[kk][2] = fmaf(mult, ey, acc[kk][2]);
         }
         __syncthreads();
     }
 
     // E_m of each point: the sum over nu, times L^-3 (DFT) and (L^3 - 1)^-1 (non-DC mean)
+#pragma unroll
+    for (int kk = 0; kk < MAXIT; ++kk) {
+        const int it = tid + kk * kLatThreads;
+        if (it >= nitems) break;
+        const int nu = inu[kk], pt = it - nu * npts, j = pt / nk, k = pt - j * nk;
+        const int slot = (j * g.BK + k) * L + nu;
+        sacc[slot] = acc[kk][0];
+        sacc[accn + slot] = acc[kk][1];
+        sacc[2 * accn + slot] = acc[kk][2];
+    }
+    __syncthreads();
     const float scale = tb.escale * 0.5f;   // escale holds the half-spectrum factor 2, applied above
     const int64_t Nc = g.Tc * g.Xc * g.Yc;
     for (int e = tid; e < 3 * nj * nk; e += kLatThreads) {
         const int m = e / (nj * nk), pt = e - m * (nj * nk), j = pt / nk, k = pt - j * nk;
-        const float *a = acc + m * accn + (j * g.BK + k) * L;
+        const float *a = sacc + m * accn + (j * g.BK + k) * L;
         float sum = 0.f;
 #pragma unroll
         for (int nu = 0; nu < L; ++nu) sum += a[nu];
@@ -181,45 +284,61 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     }
 }
 
-// Trilinear interpolation of the lattice energies back to every voxel: one CTA row walk per
-// (t, x) row, the t and x segments computed once per row, y along the threads.
-__global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ Ec, int64_t T, int64_t X, int64_t Y,
-                                                     int s, int64_t Tc, int64_t Xc, int64_t Yc, float *__restrict__ E)
+// Trilinear interpolation of the lattice energies back to every voxel.  A CTA walks rows
+// (t, x): first its threads blend the four lattice rows around the row along t and x into
+// shared memory (one value per lattice point along y and map: 4 loads each), then every voxel
+// y of the row blends its two neighbouring lattice values along y (coalesced stores).  The
+// y segment k = floor(y / s) comes from a float product: y + 1/2 is never a multiple of s and
+// its quotient stays at least 1 / (2 s) from an integer, far beyond the product's rounding
+// for y < 2^22.
+__global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ Ec, int T, int X, int Y, int s, int Tc,
+                                                     int Xc, int Yc, float *__restrict__ E)
 {
-    const int64_t N = T * X * Y, Nc = Tc * Xc * Yc;
-    for (int64_t row = blockIdx.x; row < T * X; row += gridDim.x) {
-        const int64_t t = row / X, x = row - t * X;
-        int64_t it = Tc > 1 ? min(t / s, Tc - 2) : 0, ix = Xc > 1 ? min(x / s, Xc - 2) : 0;
+    extern __shared__ float srow[];   // [3][Yc]
+    const int64_t N = (int64_t)T * X * Y, Nc = (int64_t)Tc * Xc * Yc;
+    const float inv_s = 1.f / (float)s;
+    for (int64_t row = blockIdx.x; row < (int64_t)T * X; row += gridDim.x) {
+        const int t = (int)(row / X), x = (int)(row - (int64_t)t * X);
+        int it = 0, ix = 0, it1 = 0, ix1 = 0;
         float ft = 0.f, fx = 0.f;
         if (Tc > 1) {
-            const int64_t lo = lattice_coord(it, T, s), hi = lattice_coord(it + 1, T, s);
+            it = min(t / s, Tc - 2);
+            it1 = it + 1;
+            const int lo = it * s, hi = min(it1 * s, T - 1);
             ft = (float)(t - lo) / (float)(hi - lo);
         }
         if (Xc > 1) {
-            const int64_t lo = lattice_coord(ix, X, s), hi = lattice_coord(ix + 1, X, s);
+            ix = min(x / s, Xc - 2);
+            ix1 = ix + 1;
+            const int lo = ix * s, hi = min(ix1 * s, X - 1);
             fx = (float)(x - lo) / (float)(hi - lo);
         }
-        const int64_t it1 = Tc > 1 ? it + 1 : it, ix1 = Xc > 1 ? ix + 1 : ix;
         const float w00 = (1.f - ft) * (1.f - fx), w01 = (1.f - ft) * fx, w10 = ft * (1.f - fx), w11 = ft * fx;
-        const int64_t r00 = (it * Xc + ix) * Yc, r01 = (it * Xc + ix1) * Yc, r10 = (it1 * Xc + ix) * Yc,
-                      r11 = (it1 * Xc + ix1) * Yc;
-        for (int64_t y = threadIdx.x; y < Y; y += blockDim.x) {
-            const int64_t iy = Yc > 1 ? min(y / s, Yc - 2) : 0, iy1 = Yc > 1 ? iy + 1 : iy;
+        const float *c00 = Ec + ((int64_t)it * Xc + ix) * Yc, *c01 = Ec + ((int64_t)it * Xc + ix1) * Yc;
+        const float *c10 = Ec + ((int64_t)it1 * Xc + ix) * Yc, *c11 = Ec + ((int64_t)it1 * Xc + ix1) * Yc;
+        for (int e = threadIdx.x; e < 3 * Yc; e += blockDim.x) {
+            const int m = e / Yc, k = e - m * Yc;
+            const int64_t o = m * Nc + k;
+            srow[e] = w00 * c00[o] + w01 * c01[o] + w10 * c10[o] + w11 * c11[o];
+        }
+        __syncthreads();
+        float *erow = E + row * Y;
+        for (int y = threadIdx.x; y < Y; y += blockDim.x) {
+            int ky = 0, ky1 = 0;
             float fy = 0.f;
             if (Yc > 1) {
-                const int64_t lo = lattice_coord(iy, Y, s), hi = lattice_coord(iy + 1, Y, s);
+                ky = min((int)(((float)y + 0.5f) * inv_s), Yc - 2);
+                ky1 = ky + 1;
+                const int lo = ky * s, hi = min(ky1 * s, Y - 1);
                 fy = (float)(y - lo) / (float)(hi - lo);
             }
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const float *c = Ec + m * Nc;
-                const float a = fmaf(fy, c[r00 + iy1] - c[r00 + iy], c[r00 + iy]);
-                const float bq = fmaf(fy, c[r01 + iy1] - c[r01 + iy], c[r01 + iy]);
-                const float cq = fmaf(fy, c[r10 + iy1] - c[r10 + iy], c[r10 + iy]);
-                const float d = fmaf(fy, c[r11 + iy1] - c[r11 + iy], c[r11 + iy]);
-                E[m * N + row * Y + y] = w00 * a + w01 * bq + w10 * cq + w11 * d;
+                const float a = srow[m * Yc + ky], b = srow[m * Yc + ky1];
+                erow[m * N + y] = fmaf(fy, b - a, a);
             }
         }
+        __syncthreads();
     }
 }
 
@@ -229,6 +348,7 @@ cudaError_t launch_lattice_L(const float *V, sal_dims d, int bnd, const LatGeo &
     SpecTables tb;
     make_tables(L, &tb);
     const size_t smem = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
+    if (g.BJ * g.BK * L > 4 * kLatThreads) return cudaErrorInvalidValue;   // the kernel's items per thread
     cudaError_t e = set_smem(lattice_energy_kernel<L>, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = g.Tc * g.nbj * g.nbk;
@@ -248,14 +368,15 @@ cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, in
     g.Tc = lattice_size(d.T, s);
     g.Xc = lattice_size(d.X, s);
     g.Yc = lattice_size(d.Y, s);
-    // the largest BJ x BK block (from 8 x 16) whose region fits 200 KB of shared memory
+    // the largest BJ x BK block (from 8 x 8) whose shared memory fits two CTAs per SM and whose
+    // stage-y items (BJ BK L) are at most 4 per thread
     g.BJ = 8;
-    g.BK = 16;
+    g.BK = 8;
     for (;;) {
         g.RXM = (g.BJ - 1) * s + L;
         g.RYM = (g.BK - 1) * s + L;
         const size_t need = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
-        if (need <= 200 * 1024 || (g.BJ == 1 && g.BK == 1)) break;
+        if ((need <= 110 * 1024 && g.BJ * g.BK * L <= 4 * kLatThreads) || (g.BJ == 1 && g.BK == 1)) break;
         if (g.BK >= g.BJ && g.BK > 1) g.BK /= 2; else g.BJ /= 2;
     }
     g.nbj = (int)((g.Xc + g.BJ - 1) / g.BJ);
@@ -278,11 +399,20 @@ cudaError_t launch_interp_lattice(const float *Ec, sal_dims d, int s, float *E, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    int64_t rows = d.T * d.X, grid = (int64_t)nsm * 8;
+    if (d.T > 0x7fffffffLL || d.X > 0x7fffffffLL || d.Y > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (d.Y >= (1 << 22)) return cudaErrorInvalidValue;   // the float segment index of interp_kernel
+    const int Yc = (int)lattice_size(d.Y, s);
+    int64_t rows = d.T * d.X, grid = (int64_t)nsm * 16;
     if (grid > rows) grid = rows;
     const int threads = d.Y >= 256 ? 256 : (int)((d.Y + 31) / 32 * 32);
-    interp_kernel<<<(unsigned)grid, threads, 0, st>>>(Ec, d.T, d.X, d.Y, s, lattice_size(d.T, s), lattice_size(d.X, s),
-                                                      lattice_size(d.Y, s), E);
+    const size_t smem = 3 * (size_t)Yc * sizeof(float);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    interp_kernel<<<(unsigned)grid, threads, smem, st>>>(Ec, (int)d.T, (int)d.X, (int)d.Y, s, (int)lattice_size(d.T, s),
+                                                      (int)lattice_size(d.X, s), Yc, E);
     return cudaGetLastError();
 }
 
