@@ -932,11 +932,30 @@ __device__ __forceinline__ void issue_v_copies(const float *__restrict__ V, int6
     const bool inside = t0 - H >= 0 && t0 + G::BT + H <= T && x0 - H >= 0 && x0 + G::BX + H <= X && y0 - H >= 0 &&
                         y0 + G::BY + H <= Y && (int64_t)(G::BT + 2 * H) * X * Y < 0x7fffffffLL;
     if (inside) {
-        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H);
+        // whole rows (plane a, halo row xx) per warp, lanes along the row: the row's source
+        // offset and destination advance by a fixed step per row, so each copy costs a couple of
+        // additions; lanes below PY - 32 take the row's last columns too
+        constexpr int NW_ = G::NT / 32, ROWS_ = (G::BT + 2 * H) * HX;
+        static_assert(NW_ < HX && PY > 32 && PY <= 64, "row walk: one plane step per row step, two copies per lane");
+        (void)advance;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int Yi = (int)Y, XYi = (int)(X * Y);
-        for (int i = threadIdx.x; i < G::NV; i += G::NT) {
-            cp_async_f32(sV + i, src + (a * XYi + xx * Yi + yy));
-            advance();
+        const float *src = V + ((t0 - H) * X + (x0 - H)) * Y + (y0 - H) + lane;
+        int rx = warp;                                       // halo row of the current plane
+        int off = warp * Yi;                                 // source offset of row `warp`
+        unsigned dst = (unsigned)__cvta_generic_to_shared(sV + warp * PY + lane);
+        const int wrap = XYi - HX * Yi;                      // extra source step into the next plane
+        const bool two = lane < PY - 32;
+        for (int r = warp; r < ROWS_; r += NW_) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src + off) : "memory");
+            if (two) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 128u), "l"(src + off + 32) : "memory");
+            dst += NW_ * PY * (unsigned)sizeof(float);
+            off += NW_ * Yi;
+            rx += NW_;
+            if (rx >= HX) {
+                rx -= HX;
+                off += wrap;
+            }
         }
     } else {
         for (int i = threadIdx.x; i < G::NV; i += G::NT) {
@@ -1026,7 +1045,9 @@ __device__ __forceinline__ void store_outputs(float *__restrict__ E, int64_t T, 
             *reinterpret_cast<float4 *>(e0 + c + 2 * N) =
                 make_float4(ey[c] * sc, ey[c + 1] * sc, ey[c + 2] * sc, ey[c + 3] * sc);
         }
-    } else {
+        return;
+    }
+    {
 #pragma unroll
         for (int r = 0; r < G::R; ++r) {
             if (gy + r < Y) {
