@@ -79,15 +79,18 @@ def lattice_size(n: int, s: int) -> int:
 
 def lattice_kernel_work(shape, L: int, s: int):
     """(FP32 flops on the FMA pipe, square roots) of one lattice-energy launch, counted from
-    the kernel's own loops: per CTA of nj x nk lattice points and its RX x RY region, for each
-    mu = 0..h, stage t (L taps, real in, complex out), stage x (L taps, complex) at the lattice
-    x, and the folded stage y per (point, nu) line with |F| and the weights."""
+    the kernel's own loops: per CTA of nj x nk lattice points and its RX x RY region, stage t
+    once for every mu (real input, folded: L + 3h + 4h^2 per column); then for each
+    mu = 0..h stage x at the lattice x (folded complex DFT of every nu: 8h^2 + 10h per column)
+    and the folded stage y per (point, nu) line with |F|, the weights and the accumulation."""
     H = (L - 1) // 2
-    BJ, BK = 8, 16
+    BJ, BK = 8, 8
     while True:                                         # the launcher's block choice
         RXM, RYM = (BJ - 1) * s + L, (BK - 1) * s + L
-        need = 4 * (((L * RXM * RYM + 3) & ~3) + 2 * RXM * RYM + 2 * L * BJ * RYM + 3 * BJ * BK * L)
-        if need <= 200 * 1024 or (BJ == 1 and BK == 1):
+        g1 = 2 * (H + 1) * RXM * RYM
+        reg = (max(L * RXM * RYM, 2 * L * BJ * RYM) + 3) // 4 * 4
+        need = 4 * (g1 + reg + 3 * BJ * BK * L)
+        if (need <= 110 * 1024 and BJ * BK * L <= 1024) or (BJ == 1 and BK == 1):
             break
         if BK >= BJ and BK > 1:
             BK //= 2
@@ -108,8 +111,9 @@ def lattice_kernel_work(shape, L: int, s: int):
     nk, RY = blocks(shape[2], BK)
     Tc = lattice_size(shape[0], s)
     per_item = 8 * H * H + 23 * H + 15
-    per_mu = 4 * L * RX.sum() * RY.sum() + 8 * L * L * nj.sum() * RY.sum() + nj.sum() * nk.sum() * L * per_item
-    flops = Tc * ((H + 1) * per_mu + 3 * nj.sum() * nk.sum() * L)
+    t_stage = (L + 3 * H + 4 * H * H) * RX.sum() * RY.sum()
+    per_mu = (8 * H * H + 10 * H) * nj.sum() * RY.sum() + nj.sum() * nk.sum() * L * per_item
+    flops = Tc * (t_stage + (H + 1) * per_mu + nj.sum() * nk.sum() * 3 * (L + 1))
     sqrts = Tc * (H + 1) * nj.sum() * nk.sum() * L * (1 + 2 * H)
     return float(flops - sqrts), float(sqrts)
 
@@ -686,7 +690,7 @@ def run_ours(args, rank: int, world: int) -> None:
     # overlap their copies with each other's kernels (double buffers in the workspace)
     Vh = torch.from_numpy(V_np).pin_memory()
     Shs = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
-    del E, Sm, S, ws_all                      # the host path keeps its own buffers in ws_host
+    del ws_all                                # the host path keeps its own buffers in ws_host
     ws_host = torch.empty(api.sal_host_workspace_size(dims, p), device=dev, dtype=torch.uint8)
     e2e_calls = [0]
 
@@ -713,6 +717,43 @@ def run_ours(args, rank: int, world: int) -> None:
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     if world > 1:
         e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+
+    # the other forms of the method on the same volume (BF16 and TF32 tensor-core y stage, cubes
+    # at stride 3), each timed like the main step and compared with the FP32 path's E and S
+    forms = {}
+    if args.stride == 1 and args.precision == "fp32" and args.workload == "f3" and not args.no_forms:
+        E32 = E.clone()
+        S32 = S.clone()
+        lat3 = api.sal_lattice_dims(dims, api.params(L=args.L, stride=3))
+        Ec3 = torch.empty((3, lat3.T, lat3.X, lat3.Y), device=dev, dtype=torch.float32)
+        for name, pf in (("bf16", api.params(L=args.L, precision="bf16")),
+                         ("tf32", api.params(L=args.L, precision="tf32")),
+                         ("fp32_stride3", api.params(L=args.L, stride=3))):
+            def fstep():
+                if pf.stride > 1:
+                    api.sal_lattice_energy(V, pf, Ec=Ec3, stream=stream)
+                    api.sal_interpolate_lattice(Ec3, shape, pf, E=E, stream=stream)
+                else:
+                    api.sal_spectral_energy(V, pf, E=E, stream=stream)
+                api.sal_directional_compare(E, pf, Sm=Sm, stats=stats, ws=ws_dcs, stream=stream)
+                api.sal_combine(Sm, stats, pf, S=S, stream=stream)
+            for _ in range(2):
+                fstep()
+            torch.cuda.synchronize(dev)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nf = max(3, min(args.steps, 10))
+            f0.record(stream)
+            for _ in range(nf):
+                fstep()
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            api.sal_device_status()
+            fms = f0.elapsed_time(f1) / nf
+            e_err = [float((E[m] - E32[m]).abs().max() / E32[m].abs().max()) for m in range(3)]
+            s_rel = float(torch.linalg.vector_norm((S - S32).double()) / torch.linalg.vector_norm(S32.double()))
+            forms[name] = {"value": N / (fms / 1e3), "unit": "voxels/s", "ms_per_step": fms, "steps": nf,
+                           "speedup_vs_fp32": ms / fms, "E_err_vs_fp32_normwise": e_err, "S_rel_l2_vs_fp32": s_rel}
+        del E32, S32, Ec3
 
     if rank != 0:
         return
@@ -811,6 +852,11 @@ def run_ours(args, rank: int, world: int) -> None:
         "gpu_launches": (6 if args.stride > 1 else 5) * args.steps,
         "clocks": clk.summary(),
     }
+    if forms:
+        out["forms"] = forms
+        out["forms_note"] = ("the same step with the y-stage DFT on the tensor cores (BF16, TF32 operands, FP32 "
+                             "accumulation) and with cubes at stride 3 (E interpolated back); errors against this line's "
+                             "FP32 E and S (the FP32 path is within 1e-4 of the FP64 oracle by the parity tests)")
     if not args.no_cpu_baseline:
         cb, _, _ = oracle_sample(V_np, args.L, target_s=args.cpu_seconds)
         out["cpu_baseline"] = cb
@@ -830,6 +876,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fma-probe", action="store_true", help="skip the FP32 FMA-rate probe")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 / TF32 / stride-3 forms")
     ap.add_argument("--fma-probe", action="store_true", help="only run the FP32 FMA-rate probe (one JSON line)")
     ap.add_argument("--sweep", action="store_true", help="precision sweep on 256^3 (several JSON lines)")
     ap.add_argument("--surrogate", action="store_true", help="train the learned surrogate and time its inference")

@@ -130,32 +130,50 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     LatTw<L> tw;
     tw.load(tb);
 
-    // the V region, relative to one sample of it, by asynchronous 4-byte copies; coordinates
-    // advance without divisions, and the boundary extension is taken only outside the volume
+    // the V region, relative to one sample of it, by asynchronous 4-byte copies.  Regions
+    // inside the volume: whole rows (plane p, row q) per warp, lanes along y, the source offset
+    // advanced per row; regions at a face: element by element with the boundary extension
     const float ref = V[(tc * X + (xlo + H)) * Y + (ylo + H)];
     {
-        const bool inside = tc - H >= 0 && tc + H < T && xlo >= 0 && xlo + RX <= X && ylo >= 0 && ylo + RY <= Y;
-        int r = tid % RY, q = (tid / RY) % RX, p = tid / (RX * RY);
-        const int dr = kLatThreads % RY, dq = (kLatThreads / RY) % RX, dp = kLatThreads / (RX * RY);
-        for (int e = tid; e < L * RX * RY; e += kLatThreads) {
-            int64_t gt = tc - H + p, gx = xlo + q, gy = ylo + r;
-            if (!inside) {
+        const bool inside = tc - H >= 0 && tc + H < T && xlo >= 0 && xlo + RX <= X && ylo >= 0 && ylo + RY <= Y &&
+                            (int64_t)L * X * Y < 0x7fffffffLL;
+        if (inside) {
+            const int warp = tid >> 5, lane = tid & 31, nw = kLatThreads / 32;
+            const float *src = V + ((tc - H) * X + xlo) * Y + ylo;
+            const int Yi = (int)Y, XYi = (int)(X * Y);
+            int q = warp % RX, p = warp / RX;
+            for (int row = warp; row < L * RX; row += nw) {
+                const int off = p * XYi + q * Yi;
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(sV + p * PL + q * P);
+                for (int r = lane; r < RY; r += 32)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * r), "l"(src + off + r) : "memory");
+                q += nw;
+                while (q >= RX) {
+                    q -= RX;
+                    ++p;
+                }
+            }
+        } else {
+            int r = tid % RY, q = (tid / RY) % RX, p = tid / (RX * RY);
+            const int dr = kLatThreads % RY, dq = (kLatThreads / RY) % RX, dp = kLatThreads / (RX * RY);
+            for (int e = tid; e < L * RX * RY; e += kLatThreads) {
+                int64_t gt = tc - H + p, gx = xlo + q, gy = ylo + r;
                 if ((uint64_t)gt >= (uint64_t)T) gt = ext_index(gt, T, bnd);
                 if ((uint64_t)gx >= (uint64_t)X) gx = ext_index(gx, X, bnd);
                 if ((uint64_t)gy >= (uint64_t)Y) gy = ext_index(gy, Y, bnd);
-            }
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(sV + p * PL + q * P + r);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(V + (gt * X + gx) * Y + gy) : "memory");
-            r += dr;
-            q += dq;
-            p += dp;
-            if (r >= RY) {
-                r -= RY;
-                ++q;
-            }
-            if (q >= RX) {
-                q -= RX;
-                ++p;
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(sV + p * PL + q * P + r);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(V + (gt * X + gx) * Y + gy) : "memory");
+                r += dr;
+                q += dq;
+                p += dp;
+                if (r >= RY) {
+                    r -= RY;
+                    ++q;
+                }
+                if (q >= RX) {
+                    q -= RX;
+                    ++p;
+                }
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -215,19 +233,32 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
         ioff[kk] = j * P + (int)(lattice_coord(k0 + k, Y, g.s) - H - ylo);
     }
 
+    // stage-x items of this thread (the same for every mu): column (j, r) of the lattice x
+    // j; offsets into G1 (first tap) and into G2 (line nu = 0)
+    constexpr int MAXX = 2;
+    int xin[MAXX], xout[MAXX];
+    const int nxit = nj * RY;
+#pragma unroll
+    for (int kk = 0; kk < MAXX; ++kk) {
+        const int e = tid + kk * kLatThreads;
+        const int j = e / RY, r = e - j * RY;
+        xin[kk] = (int)(lattice_coord(j0 + min(j, nj - 1), X, g.s) - H - xlo) * P + r;
+        xout[kk] = j * P + r;
+    }
+
 #pragma unroll 1
     for (int mu = 0; mu <= H; ++mu) {
         // stage x at the lattice x of this CTA: every nu of a column window at once
         const float2 *g1 = sG1 + mu * PL;
-        for (int e = tid; e < nj * RY; e += kLatThreads) {
-            const int j = e / RY, r = e - j * RY;
-            const int xq = (int)(lattice_coord(j0 + j, X, g.s) - H - xlo);
+#pragma unroll
+        for (int kk = 0; kk < MAXX; ++kk) {
+            if (tid + kk * kLatThreads >= nxit) break;
             float2 z[L], out[L];
 #pragma unroll
-            for (int q = 0; q < L; ++q) z[q] = g1[(xq + q) * P + r];
+            for (int q = 0; q < L; ++q) z[q] = g1[xin[kk] + q * P];
             folded_dft<L>(z, tw, out);
 #pragma unroll
-            for (int nu = 0; nu < L; ++nu) sG2[(nu * g.BJ + j) * P + r] = out[nu];
+            for (int nu = 0; nu < L; ++nu) sG2[nu * g.BJ * P + xout[kk]] = out[nu];
         }
         __syncthreads();
         // stage y: the folded DFT of each (point, nu) line at the lattice y, |F|, weights
@@ -284,19 +315,29 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     }
 }
 
-// Trilinear interpolation of the lattice energies back to every voxel.  A CTA walks rows
-// (t, x): first its threads blend the four lattice rows around the row along t and x into
-// shared memory (one value per lattice point along y and map: 4 loads each), then every voxel
-// y of the row blends its two neighbouring lattice values along y (coalesced stores).  The
-// y segment k = floor(y / s) comes from a float product: y + 1/2 is never a multiple of s and
-// its quotient stays at least 1 / (2 s) from an integer, far beyond the product's rounding
-// for y < 2^22.
+// Trilinear interpolation of the lattice energies back to every voxel.  Every CTA first
+// tabulates, for each voxel y of a row, its lattice segment along y and the fraction of the way
+// (the same for every row); then it walks rows (t, x): the t and x segments and weights once per
+// row, the four lattice rows around it blended along t and x into shared memory, and every
+// voxel y blends its two neighbouring lattice values along y with a coalesced store.
 __global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ Ec, int T, int X, int Y, int s, int Tc,
                                                      int Xc, int Yc, float *__restrict__ E)
 {
-    extern __shared__ float srow[];   // [3][Yc]
+    extern __shared__ float smem_i[];
+    float *srow = smem_i;                                           // [3][Yc]
+    float2 *ytab = reinterpret_cast<float2 *>(smem_i + ((3 * Yc + 1) & ~1));   // [Y]: (segment, fraction)
     const int64_t N = (int64_t)T * X * Y, Nc = (int64_t)Tc * Xc * Yc;
-    const float inv_s = 1.f / (float)s;
+    for (int y = threadIdx.x; y < Y; y += blockDim.x) {
+        int ky = 0;
+        float fy = 0.f;
+        if (Yc > 1) {
+            ky = min(y / s, Yc - 2);
+            const int lo = ky * s, hi = min((ky + 1) * s, Y - 1);
+            fy = (float)(y - lo) / (float)(hi - lo);
+        }
+        ytab[y] = make_float2(__int_as_float(ky), fy);
+    }
+    const int dk = Yc > 1 ? 1 : 0;
     for (int64_t row = blockIdx.x; row < (int64_t)T * X; row += gridDim.x) {
         const int t = (int)(row / X), x = (int)(row - (int64_t)t * X);
         int it = 0, ix = 0, it1 = 0, ix1 = 0;
@@ -316,29 +357,23 @@ __global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ E
         const float w00 = (1.f - ft) * (1.f - fx), w01 = (1.f - ft) * fx, w10 = ft * (1.f - fx), w11 = ft * fx;
         const float *c00 = Ec + ((int64_t)it * Xc + ix) * Yc, *c01 = Ec + ((int64_t)it * Xc + ix1) * Yc;
         const float *c10 = Ec + ((int64_t)it1 * Xc + ix) * Yc, *c11 = Ec + ((int64_t)it1 * Xc + ix1) * Yc;
+        __syncthreads();                          // the previous row's blends are consumed (and ytab is ready)
         for (int e = threadIdx.x; e < 3 * Yc; e += blockDim.x) {
             const int m = e / Yc, k = e - m * Yc;
             const int64_t o = m * Nc + k;
             srow[e] = w00 * c00[o] + w01 * c01[o] + w10 * c10[o] + w11 * c11[o];
         }
         __syncthreads();
-        float *erow = E + row * Y;
+        float *e0 = E + row * Y, *e1 = e0 + N, *e2 = e1 + N;
         for (int y = threadIdx.x; y < Y; y += blockDim.x) {
-            int ky = 0, ky1 = 0;
-            float fy = 0.f;
-            if (Yc > 1) {
-                ky = min((int)(((float)y + 0.5f) * inv_s), Yc - 2);
-                ky1 = ky + 1;
-                const int lo = ky * s, hi = min(ky1 * s, Y - 1);
-                fy = (float)(y - lo) / (float)(hi - lo);
-            }
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float a = srow[m * Yc + ky], b = srow[m * Yc + ky1];
-                erow[m * N + y] = fmaf(fy, b - a, a);
-            }
+            const float2 tf = ytab[y];
+            const int ky = __float_as_int(tf.x);
+            const float fy = tf.y;
+            const float a0 = srow[ky], a1 = srow[Yc + ky], a2 = srow[2 * Yc + ky];
+            e0[y] = fmaf(fy, srow[ky + dk] - a0, a0);
+            e1[y] = fmaf(fy, srow[Yc + ky + dk] - a1, a1);
+            e2[y] = fmaf(fy, srow[2 * Yc + ky + dk] - a2, a2);
         }
-        __syncthreads();
     }
 }
 
@@ -348,7 +383,8 @@ cudaError_t launch_lattice_L(const float *V, sal_dims d, int bnd, const LatGeo &
     SpecTables tb;
     make_tables(L, &tb);
     const size_t smem = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
-    if (g.BJ * g.BK * L > 4 * kLatThreads) return cudaErrorInvalidValue;   // the kernel's items per thread
+    if (g.BJ * g.BK * L > 4 * kLatThreads || g.BJ * g.RYM > 2 * kLatThreads)
+        return cudaErrorInvalidValue;   // the kernel's stage-y and stage-x items per thread
     cudaError_t e = set_smem(lattice_energy_kernel<L>, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = g.Tc * g.nbj * g.nbk;
@@ -376,7 +412,9 @@ cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, in
         g.RXM = (g.BJ - 1) * s + L;
         g.RYM = (g.BK - 1) * s + L;
         const size_t need = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
-        if ((need <= 110 * 1024 && g.BJ * g.BK * L <= 4 * kLatThreads) || (g.BJ == 1 && g.BK == 1)) break;
+        if ((need <= 110 * 1024 && g.BJ * g.BK * L <= 4 * kLatThreads && g.BJ * g.RYM <= 2 * kLatThreads) ||
+            (g.BJ == 1 && g.BK == 1))
+            break;
         if (g.BK >= g.BJ && g.BK > 1) g.BK /= 2; else g.BJ /= 2;
     }
     g.nbj = (int)((g.Xc + g.BJ - 1) / g.BJ);
@@ -400,12 +438,11 @@ cudaError_t launch_interp_lattice(const float *Ec, sal_dims d, int s, float *E, 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (d.T > 0x7fffffffLL || d.X > 0x7fffffffLL || d.Y > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (d.Y >= (1 << 22)) return cudaErrorInvalidValue;   // the float segment index of interp_kernel
     const int Yc = (int)lattice_size(d.Y, s);
     int64_t rows = d.T * d.X, grid = (int64_t)nsm * 16;
     if (grid > rows) grid = rows;
     const int threads = d.Y >= 256 ? 256 : (int)((d.Y + 31) / 32 * 32);
-    const size_t smem = 3 * (size_t)Yc * sizeof(float);
+    const size_t smem = ((3 * (size_t)Yc + 1) & ~(size_t)1) * sizeof(float) + (size_t)d.Y * sizeof(float2);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
