@@ -141,8 +141,9 @@ SAL_API sal_status sal_spectral_energy(const float *V, sal_dims dims, const sal_
  * the cube centred on every lattice point, Ec [3][Tc][Xc][Yc] (device); sal_interpolate_lattice
  * writes E [3][T][X][Y] (device), each voxel the trilinear interpolation of the 2 x 2 x 2
  * lattice energies around it (exact at the lattice points).  FP32 on the CUDA cores; with
- * s = 0 or 1 the lattice is every voxel.  The interpolation keeps a table of the Y voxels of a
- * row in shared memory: Y up to about 24,000 (beyond, SAL_ERR_CUDA from the launch).
+ * s = 0 or 1 the lattice is every voxel.  The interpolation keeps a table of the lattice
+ * segment of every t, x and y in shared memory: T + X + Y up to about 24,000 (beyond,
+ * SAL_ERR_CUDA from the launch).
  * Asynchronous; errors as the other calls.
  */
 SAL_API sal_status sal_lattice_dims(sal_dims dims, const sal_params *p, sal_dims *lattice);

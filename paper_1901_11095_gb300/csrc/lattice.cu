@@ -49,6 +49,15 @@ inline size_t lat_smem_bytes(int L, int BJ, int BK, int RXM, int RYM)
     return sizeof(float) * (lat_g1_floats(L, RXM, RYM) + lat_reg_floats(L, BJ, RXM, RYM) + 3 * (size_t)BJ * BK * L);
 }
 
+// |F| from |F|^2: the hardware approximate square root (one MUFU operation, a relative error
+// of a few ulp, far inside the path's tolerance), as the stride-1 energy kernel uses.
+__device__ __forceinline__ float lat_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // cos and sin of 2 pi k / L for k = 0..L-1 (compile-time indices once unrolled).
 template <int L>
 struct LatTw {
@@ -277,8 +286,8 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
             float et = 0.f, ex = 0.f, ey = 0.f;
 #pragma unroll
             for (int om = 0; om <= H; ++om) {
-                float m = sqrtf(fmaf(F[H + om].x, F[H + om].x, F[H + om].y * F[H + om].y));
-                if (om) m += sqrtf(fmaf(F[H - om].x, F[H - om].x, F[H - om].y * F[H - om].y));
+                float m = lat_sqrt(fmaf(F[H + om].x, F[H + om].x, F[H + om].y * F[H + om].y));
+                if (om) m += lat_sqrt(fmaf(F[H - om].x, F[H - om].x, F[H - om].y * F[H - om].y));
                 const float *w = w0 + om * 3;
                 et = fmaf(w[0], m, et);
                 ex = fmaf(w[1], m, ex);
@@ -316,63 +325,57 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
 }
 
 // Trilinear interpolation of the lattice energies back to every voxel.  Every CTA first
-// tabulates, for each voxel y of a row, its lattice segment along y and the fraction of the way
-// (the same for every row); then it walks rows (t, x): the t and x segments and weights once per
-// row, the four lattice rows around it blended along t and x into shared memory, and every
-// voxel y blends its two neighbouring lattice values along y with a coalesced store.
+// tabulates, once, the lattice segment and the fraction of the way of every t, x and y (the
+// same for every row); it then walks rows (t, x) on a 2-D grid (no division per row): the four
+// lattice rows around a row are blended along t and x into shared memory, and every voxel y
+// blends its two neighbouring lattice values along y with a coalesced store.
+__device__ __forceinline__ float2 lattice_segment(int v, int n, int nc, int s)
+{
+    if (nc <= 1) return make_float2(__int_as_float(0), 0.f);
+    const int k = min(v / s, nc - 2);
+    const int lo = k * s, hi = min((k + 1) * s, n - 1);
+    return make_float2(__int_as_float(k), (float)(v - lo) / (float)(hi - lo));
+}
+
 __global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ Ec, int T, int X, int Y, int s, int Tc,
                                                      int Xc, int Yc, float *__restrict__ E)
 {
     extern __shared__ float smem_i[];
-    float *srow = smem_i;                                           // [3][Yc]
-    float2 *ytab = reinterpret_cast<float2 *>(smem_i + ((3 * Yc + 1) & ~1));   // [Y]: (segment, fraction)
+    float *srow = smem_i;                                                     // [3][Yc]
+    float2 *ytab = reinterpret_cast<float2 *>(smem_i + ((3 * Yc + 1) & ~1));  // [Y]
+    float2 *ttab = ytab + Y;                                                  // [T]
+    float2 *xtab = ttab + T;                                                  // [X]
     const int64_t N = (int64_t)T * X * Y, Nc = (int64_t)Tc * Xc * Yc;
-    for (int y = threadIdx.x; y < Y; y += blockDim.x) {
-        int ky = 0;
-        float fy = 0.f;
-        if (Yc > 1) {
-            ky = min(y / s, Yc - 2);
-            const int lo = ky * s, hi = min((ky + 1) * s, Y - 1);
-            fy = (float)(y - lo) / (float)(hi - lo);
-        }
-        ytab[y] = make_float2(__int_as_float(ky), fy);
-    }
-    const int dk = Yc > 1 ? 1 : 0;
-    for (int64_t row = blockIdx.x; row < (int64_t)T * X; row += gridDim.x) {
-        const int t = (int)(row / X), x = (int)(row - (int64_t)t * X);
-        int it = 0, ix = 0, it1 = 0, ix1 = 0;
-        float ft = 0.f, fx = 0.f;
-        if (Tc > 1) {
-            it = min(t / s, Tc - 2);
-            it1 = it + 1;
-            const int lo = it * s, hi = min(it1 * s, T - 1);
-            ft = (float)(t - lo) / (float)(hi - lo);
-        }
-        if (Xc > 1) {
-            ix = min(x / s, Xc - 2);
-            ix1 = ix + 1;
-            const int lo = ix * s, hi = min(ix1 * s, X - 1);
-            fx = (float)(x - lo) / (float)(hi - lo);
-        }
-        const float w00 = (1.f - ft) * (1.f - fx), w01 = (1.f - ft) * fx, w10 = ft * (1.f - fx), w11 = ft * fx;
-        const float *c00 = Ec + ((int64_t)it * Xc + ix) * Yc, *c01 = Ec + ((int64_t)it * Xc + ix1) * Yc;
-        const float *c10 = Ec + ((int64_t)it1 * Xc + ix) * Yc, *c11 = Ec + ((int64_t)it1 * Xc + ix1) * Yc;
-        __syncthreads();                          // the previous row's blends are consumed (and ytab is ready)
-        for (int e = threadIdx.x; e < 3 * Yc; e += blockDim.x) {
-            const int m = e / Yc, k = e - m * Yc;
-            const int64_t o = m * Nc + k;
-            srow[e] = w00 * c00[o] + w01 * c01[o] + w10 * c10[o] + w11 * c11[o];
-        }
-        __syncthreads();
-        float *e0 = E + row * Y, *e1 = e0 + N, *e2 = e1 + N;
-        for (int y = threadIdx.x; y < Y; y += blockDim.x) {
-            const float2 tf = ytab[y];
-            const int ky = __float_as_int(tf.x);
-            const float fy = tf.y;
-            const float a0 = srow[ky], a1 = srow[Yc + ky], a2 = srow[2 * Yc + ky];
-            e0[y] = fmaf(fy, srow[ky + dk] - a0, a0);
-            e1[y] = fmaf(fy, srow[Yc + ky + dk] - a1, a1);
-            e2[y] = fmaf(fy, srow[2 * Yc + ky + dk] - a2, a2);
+    for (int v = threadIdx.x; v < Y; v += blockDim.x) ytab[v] = lattice_segment(v, Y, Yc, s);
+    for (int v = threadIdx.x; v < T; v += blockDim.x) ttab[v] = lattice_segment(v, T, Tc, s);
+    for (int v = threadIdx.x; v < X; v += blockDim.x) xtab[v] = lattice_segment(v, X, Xc, s);
+    const int dt = Tc > 1 ? 1 : 0, dx = Xc > 1 ? 1 : 0, dk = Yc > 1 ? 1 : 0;
+    for (int t = blockIdx.y; t < T; t += gridDim.y) {
+        for (int x = blockIdx.x; x < X; x += gridDim.x) {
+            __syncthreads();                      // tables ready; the previous row's blends consumed
+            const float2 tt = ttab[t], xx = xtab[x];
+            const int it = __float_as_int(tt.x), ix = __float_as_int(xx.x);
+            const float ft = tt.y, fx = xx.y;
+            const float w00 = (1.f - ft) * (1.f - fx), w01 = (1.f - ft) * fx, w10 = ft * (1.f - fx), w11 = ft * fx;
+            const float *c00 = Ec + ((int64_t)it * Xc + ix) * Yc;
+            const float *c01 = c00 + (int64_t)dx * Yc, *c10 = c00 + (int64_t)dt * Xc * Yc;
+            const float *c11 = c10 + (int64_t)dx * Yc;
+            for (int e = threadIdx.x; e < 3 * Yc; e += blockDim.x) {
+                const int m = e >= Yc ? (e >= 2 * Yc ? 2 : 1) : 0;
+                const int64_t o = m * Nc + (e - m * Yc);
+                srow[e] = w00 * c00[o] + w01 * c01[o] + w10 * c10[o] + w11 * c11[o];
+            }
+            __syncthreads();
+            float *e0 = E + ((int64_t)t * X + x) * Y, *e1 = e0 + N, *e2 = e1 + N;
+            for (int y = threadIdx.x; y < Y; y += blockDim.x) {
+                const float2 tf = ytab[y];
+                const int ky = __float_as_int(tf.x);
+                const float fy = tf.y;
+                const float a0 = srow[ky], a1 = srow[Yc + ky], a2 = srow[2 * Yc + ky];
+                e0[y] = fmaf(fy, srow[ky + dk] - a0, a0);
+                e1[y] = fmaf(fy, srow[Yc + ky + dk] - a1, a1);
+                e2[y] = fmaf(fy, srow[2 * Yc + ky + dk] - a2, a2);
+            }
         }
     }
 }
@@ -433,22 +436,19 @@ cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, in
 
 cudaError_t launch_interp_lattice(const float *Ec, sal_dims d, int s, float *E, cudaStream_t st)
 {
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
     if (d.T > 0x7fffffffLL || d.X > 0x7fffffffLL || d.Y > 0x7fffffffLL) return cudaErrorInvalidValue;
     const int Yc = (int)lattice_size(d.Y, s);
-    int64_t rows = d.T * d.X, grid = (int64_t)nsm * 16;
-    if (grid > rows) grid = rows;
-    const int threads = d.Y >= 256 ? 256 : (int)((d.Y + 31) / 32 * 32);
-    const size_t smem = ((3 * (size_t)Yc + 1) & ~(size_t)1) * sizeof(float) + (size_t)d.Y * sizeof(float2);
+    const size_t smem = ((3 * (size_t)Yc + 1) & ~(size_t)1) * sizeof(float) +
+                        (size_t)(d.Y + d.T + d.X) * sizeof(float2);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    interp_kernel<<<(unsigned)grid, threads, smem, st>>>(Ec, (int)d.T, (int)d.X, (int)d.Y, s, (int)lattice_size(d.T, s),
+    const int threads = d.Y >= 256 ? 256 : (int)((d.Y + 31) / 32 * 32);
+    const unsigned gx = (unsigned)(d.X < 64 ? d.X : 64), gy = (unsigned)(d.T < 40 ? d.T : 40);
+    interp_kernel<<<dim3(gx, gy), threads, smem, st>>>(Ec, (int)d.T, (int)d.X, (int)d.Y, s, (int)lattice_size(d.T, s),
                                                       (int)lattice_size(d.X, s), Yc, E);
     return cudaGetLastError();
 }
