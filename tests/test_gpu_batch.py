@@ -18,7 +18,10 @@ def _batch(n=9, lo=5, hi=70, seed=0):
     return [synth.make_volume(s, seed=i) for i, s in enumerate(shapes)]
 
 
-@pytest.mark.parametrize("stencil,L", [("26", 7), ("line", 5)])
+ORC_STENCIL = {"26": O.STENCIL_26, "line": O.STENCIL_LINE, "diag_tx": O.STENCIL_DIAG_TX}
+
+
+@pytest.mark.parametrize("stencil,L", [("26", 7), ("line", 5), ("diag_tx", 7)])
 def test_batched_equals_per_volume_and_oracle(stencil, L):
     api.sal_autotune_clear()
     vols = _batch()
@@ -34,7 +37,7 @@ def test_batched_equals_per_volume_and_oracle(stencil, L):
         assert torch.equal(stats[i].view(3, 3)[:, :2], st1.view(3, 3)[:, :2])
         torch.testing.assert_close(stats[i].view(3, 3)[:, 2], st1.view(3, 3)[:, 2], rtol=1e-12, atol=0)
     for i in (1, len(vols) - 1):
-        S_ref = O.saliency(vols[i], L=L, stencil=O.STENCIL_26 if stencil == "26" else O.STENCIL_LINE)
+        S_ref = O.saliency(vols[i], L=L, stencil=ORC_STENCIL[stencil])
         err = np.abs(Ss[i].cpu().numpy() - S_ref).max() / max(np.abs(S_ref).max(), 1e-30)
         assert err < 1e-4
 

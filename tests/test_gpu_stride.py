@@ -36,6 +36,8 @@ CASES = [
     ((20, 26, 27), 11, 5, "periodic", 4),
     ((16, 18, 20), 15, 7, "reflect", 5),      # the largest cube and stride: smaller lattice blocks
     ((1, 9, 12), 5, 2, "reflect", 6),         # one plane: a one-point lattice along t
+    ((1, 1, 1), 7, 3, "reflect", 7),          # a single voxel
+    ((12, 13, 260), 7, 3, "reflect", 8),      # rows longer than a CTA (y walked in two passes)
 ]
 
 
@@ -50,7 +52,8 @@ def test_lattice_energy_matches_oracle(shape, L, s, bnd, seed):
         assert nerr(Ec[m], Ec_ref[m]) < TOL_MAP, (m, nerr(Ec[m], Ec_ref[m]))
 
 
-@pytest.mark.parametrize("shape,s", [((40, 37, 70), 3), ((9, 300, 11), 2), ((1, 1, 1), 2), ((5, 1, 33), 4)])
+@pytest.mark.parametrize("shape,s", [((40, 37, 70), 3), ((9, 300, 11), 2), ((1, 1, 1), 2), ((5, 1, 33), 4),
+                                     ((2, 2, 2), 7), ((31, 2, 700), 5)])
 def test_interpolation_matches_oracle(shape, s):
     rng = np.random.default_rng(s)
     lat = O.lattice_shape(shape, s)
