@@ -884,9 +884,9 @@ def main():
                     help="time the surrogate network alone (seeded weights) on --surrogate-shape")
     ap.add_argument("--surrogate-shape", default="128x128x256", help="T x X x Y of --surrogate-forward")
     ap.add_argument("--train-volumes", type=int, default=200)
-    ap.add_argument("--train-steps", type=int, default=3000)
-    ap.add_argument("--train-lr", type=float, default=3e-3)
-    ap.add_argument("--train-lr-final", type=float, default=3e-4)
+    ap.add_argument("--train-steps", type=int, default=60000)
+    ap.add_argument("--train-lr", type=float, default=2e-3)
+    ap.add_argument("--train-lr-final", type=float, default=2e-5)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
