@@ -23,12 +23,6 @@ namespace {
 
 constexpr int kLatThreads = 256;
 
-__host__ __device__ __forceinline__ int64_t lattice_coord(int64_t i, int64_t n, int s)
-{
-    const int64_t c = i * (int64_t)s;
-    return c < n - 1 ? c : n - 1;
-}
-
 struct LatGeo {
     int s, BJ, BK, RXM, RYM;   // stride, lattice points per CTA along x and y, region bounds
     int nbj, nbk;              // CTA blocks along x and y
@@ -115,17 +109,21 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     constexpr int MAXIT = 4;   // stage-y items per thread (checked by the launcher)
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
-    int64_t b = blockIdx.x;
-    const int kb = (int)(b % g.nbk);
-    b /= g.nbk;
-    const int jb = (int)(b % g.nbj);
-    const int64_t i = b / g.nbj;
-    const int64_t j0 = (int64_t)jb * g.BJ, k0 = (int64_t)kb * g.BK;
-    const int nj = (int)min((int64_t)g.BJ, g.Xc - j0), nk = (int)min((int64_t)g.BK, g.Yc - k0);
-    const int64_t tc = lattice_coord(i, T, g.s);
-    const int64_t xlo = lattice_coord(j0, X, g.s) - H, ylo = lattice_coord(k0, Y, g.s) - H;
-    const int RX = (int)(lattice_coord(j0 + nj - 1, X, g.s) + H - xlo + 1);
-    const int RY = (int)(lattice_coord(k0 + nk - 1, Y, g.s) + H - ylo + 1);
+    // block -> (lattice plane, x block, y block) in 32 bits (the launcher keeps the grid below 2^31)
+    unsigned b = blockIdx.x;
+    const int kb = (int)(b % (unsigned)g.nbk);
+    b /= (unsigned)g.nbk;
+    const int jb = (int)(b % (unsigned)g.nbj);
+    const int64_t i = b / (unsigned)g.nbj;
+    // lattice coordinates in 32 bits (the launcher checks that every axis fits)
+    const int Xi = (int)X, Yi32 = (int)Y, s = g.s;
+    auto coord = [s](int idx, int n) { return min(idx * s, n - 1); };
+    const int j0 = jb * g.BJ, k0 = kb * g.BK;
+    const int nj = min(g.BJ, (int)g.Xc - j0), nk = min(g.BK, (int)g.Yc - k0);
+    const int64_t tc = coord((int)i, (int)T);
+    const int xlo = coord(j0, Xi) - H, ylo = coord(k0, Yi32) - H;
+    const int RX = coord(j0 + nj - 1, Xi) + H - xlo + 1;
+    const int RY = coord(k0 + nk - 1, Yi32) + H - ylo + 1;
     const int P = g.RYM;                                   // row pitch (floats or float2)
     const int PL = g.RXM * P;                              // plane pitch of the V region / one G1 mu
 
@@ -135,6 +133,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     float *sacc = sV + lat_reg_floats(L, g.BJ, g.RXM, g.RYM);                         // [3][BJ * BK * L]
     const int nitems = nj * nk * L;
     const int accn = g.BJ * g.BK * L;
+    const int BJP = g.BJ * P;                              // G2 stride between nu lines
 
     LatTw<L> tw;
     tw.load(tb);
@@ -196,8 +195,9 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
         const int dr = kLatThreads % RY, dq = kLatThreads / RY;
         for (int e = tid; e < RX * RY; e += kLatThreads) {
             float a[L];
+            const float *src = sV + q * P + r;
 #pragma unroll
-            for (int p = 0; p < L; ++p) a[p] = sV[p * PL + q * P + r] - ref;
+            for (int p = 0; p < L; ++p, src += PL) a[p] = *src - ref;
             float U[H + 1], D[H + 1], s0 = a[H];
 #pragma unroll
             for (int k = 1; k <= H; ++k) {
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
         const int it = tid + kk * kLatThreads;
         const int nu = it / npts, pt = it - nu * npts, j = pt / nk, k = pt - j * nk;
         inu[kk] = nu;
-        ioff[kk] = j * P + (int)(lattice_coord(k0 + k, Y, g.s) - H - ylo);
+        ioff[kk] = j * P + (coord(k0 + k, Yi32) - H - ylo);
     }
 
     // stage-x items of this thread (the same for every mu): column (j, r) of the lattice x
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     for (int kk = 0; kk < MAXX; ++kk) {
         const int e = tid + kk * kLatThreads;
         const int j = e / RY, r = e - j * RY;
-        xin[kk] = (int)(lattice_coord(j0 + min(j, nj - 1), X, g.s) - H - xlo) * P + r;
+        xin[kk] = (coord(j0 + min(j, nj - 1), Xi) - H - xlo) * P + r;
         xout[kk] = j * P + r;
     }
 
@@ -263,11 +263,13 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
         for (int kk = 0; kk < MAXX; ++kk) {
             if (tid + kk * kLatThreads >= nxit) break;
             float2 z[L], out[L];
+            const float2 *src = g1 + xin[kk];
 #pragma unroll
-            for (int q = 0; q < L; ++q) z[q] = g1[xin[kk] + q * P];
+            for (int q = 0; q < L; ++q, src += P) z[q] = *src;
             folded_dft<L>(z, tw, out);
+            float2 *dst = sG2 + xout[kk];
 #pragma unroll
-            for (int nu = 0; nu < L; ++nu) sG2[nu * g.BJ * P + xout[kk]] = out[nu];
+            for (int nu = 0; nu < L; ++nu, dst += BJP) *dst = out[nu];
         }
         __syncthreads();
         // stage y: the folded DFT of each (point, nu) line at the lattice y, |F|, weights
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
         for (int kk = 0; kk < MAXIT; ++kk) {
             if (tid + kk * kLatThreads >= nitems) break;
             const int nu = inu[kk];
-            const float2 *line = sG2 + nu * g.BJ * P + ioff[kk];
+            const float2 *line = sG2 + nu * BJP + ioff[kk];
             float2 z[L], F[L];
 #pragma unroll
             for (int r = 0; r < L; ++r) z[r] = line[r];
@@ -388,6 +390,7 @@ cudaError_t launch_lattice_L(const float *V, sal_dims d, int bnd, const LatGeo &
     const size_t smem = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
     if (g.BJ * g.BK * L > 4 * kLatThreads || g.BJ * g.RYM > 2 * kLatThreads)
         return cudaErrorInvalidValue;   // the kernel's stage-y and stage-x items per thread
+    if (d.T > 0x3fffffffLL || d.X > 0x3fffffffLL || d.Y > 0x3fffffffLL) return cudaErrorInvalidValue;   // 32-bit coordinates
     cudaError_t e = set_smem(lattice_energy_kernel<L>, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = g.Tc * g.nbj * g.nbk;

@@ -58,7 +58,7 @@ def test_interpolation_matches_oracle(shape, s):
     rng = np.random.default_rng(s)
     lat = O.lattice_shape(shape, s)
     Ec = rng.uniform(0.0, 2.0, size=(3,) + lat).astype(np.float32)
-    E = api.sal_interpolate_lattice(to_dev(Ec), shape, api.params(L=9, stride=s)).cpu().numpy()
+    E = api.sal_interpolate_lattice(to_dev(Ec), shape, api.params(L=15, stride=s)).cpu().numpy()
     E_ref = O.interp_lattice(Ec.astype(np.float64), shape, s)
     assert np.abs(E - E_ref).max() <= 4e-7 * np.abs(E_ref).max()
 
