@@ -209,7 +209,10 @@ def sal_slab_workspace_size(ext_planes: int, X: int, Y: int, p: SalParams) -> in
 def sal_slab_maps(V_ext: torch.Tensor, dims: SalDims, ext_lo: int, ext_hi: int, own_lo: int, own_hi: int,
                   p: SalParams, Sm_own: torch.Tensor | None = None, stats_local: torch.Tensor | None = None,
                   ws: torch.Tensor | None = None, stream=None):
-    """Steps 1-4 of one slab: (S_m of its own planes [3, own, X, Y], their local (min, max, sum) [9])."""
+    """Steps 1-4 of one slab: (S_m of its own planes [3, own, X, Y], their local (min, max, sum) [9]).
+
+    V_ext holds the planes [ext_lo, ext_hi) of V as its own 16-byte aligned buffer (a slice of a
+    larger tensor along t is generally not aligned: clone it)."""
     X, Y = int(dims.X), int(dims.Y)
     if Sm_own is None:
         Sm_own = torch.empty((3, int(own_hi) - int(own_lo), X, Y), device=V_ext.device, dtype=torch.float32)

@@ -61,17 +61,18 @@ __global__ void __launch_bounds__(kThreads) fma_probe_packed(float *__restrict__
 
 }  // namespace
 
-extern "C" sal_status sal_probe_fma_rate(float *out, int64_t n_threads, int32_t iters, int32_t packed, void *stream)
+namespace sal {
+
+cudaError_t launch_fma_probe(float *out, int64_t n_threads, int iters, bool packed, cudaStream_t stream)
 {
-    if (!out || n_threads < kThreads || n_threads % kThreads != 0 || n_threads / kThreads > 0x7fffffffLL)
-        return SAL_ERR_INVALID_ARG;
-    if (iters < kUnroll || iters % kUnroll != 0) return SAL_ERR_INVALID_ARG;
     const unsigned grid = (unsigned)(n_threads / kThreads);
     // a slightly below 1 and b small keep every chain finite over any number of steps
     const float a = 0.9999999f, b = 1e-7f;
     if (packed)
-        fma_probe_packed<<<grid, kThreads, 0, (cudaStream_t)stream>>>(out, iters, a, b);
+        fma_probe_packed<<<grid, kThreads, 0, stream>>>(out, iters, a, b);
     else
-        fma_probe_scalar<<<grid, kThreads, 0, (cudaStream_t)stream>>>(out, iters, a, b);
-    return cudaGetLastError() == cudaSuccess ? SAL_OK : SAL_ERR_CUDA;
+        fma_probe_scalar<<<grid, kThreads, 0, stream>>>(out, iters, a, b);
+    return cudaGetLastError();
 }
+
+}  // namespace sal

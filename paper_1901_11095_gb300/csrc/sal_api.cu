@@ -609,6 +609,16 @@ sal_status sal_slab_maps(const float *V_ext, sal_dims dims, int64_t ext_lo, int6
     return e == cudaSuccess ? ok() : cuda_fail(e, "sal_slab_maps");
 }
 
+sal_status sal_probe_fma_rate(float *out, int64_t n_threads, int32_t iters, int32_t packed, void *stream)
+{
+    if (!out) return fail(SAL_ERR_INVALID_ARG, "out is NULL");
+    if (n_threads < 256 || n_threads % 256 != 0 || n_threads / 256 > 0x7fffffffLL)
+        return fail(SAL_ERR_INVALID_ARG, "n_threads must be a positive multiple of 256 (got %lld)", (long long)n_threads);
+    if (iters < 16 || iters % 16 != 0) return fail(SAL_ERR_INVALID_ARG, "iters must be a positive multiple of 16 (got %d)", iters);
+    cudaError_t e = sal::launch_fma_probe(out, n_threads, iters, packed != 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "sal_probe_fma_rate");
+}
+
 sal_status sal_stats_merge(const double *stats, int32_t n, double *out, void *stream)
 {
     if (!stats || !out) return fail(SAL_ERR_INVALID_ARG, "NULL pointer argument");

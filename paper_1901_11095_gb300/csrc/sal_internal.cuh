@@ -184,6 +184,9 @@ int64_t lattice_size(int64_t n, int s);
 cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, int s, float *Ec, cudaStream_t st);
 cudaError_t launch_interp_lattice(const float *Ec, sal_dims d, int s, float *E, cudaStream_t st);
 
+// FP32 FMA-rate probe: n_threads / 256 blocks, SAL_PROBE_CHAINS chains of `iters` FMAs per thread.
+cudaError_t launch_fma_probe(float *out, int64_t n_threads, int iters, bool packed, cudaStream_t stream);
+
 cudaError_t launch_combine(const float *Sm, const double *stats, sal_dims d, const sal_params *p, float *S,
                            cudaStream_t s);
 
