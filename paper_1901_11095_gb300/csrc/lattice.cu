@@ -32,15 +32,34 @@ struct LatGeo {
 // Shared memory of one CTA, in floats: G1 of every mu (complex), then a region that first
 // holds the V samples and, once stage t has consumed them, G2 of one mu (complex); both
 // rounded up to 16 bytes.
-__host__ __device__ inline size_t lat_g1_floats(int L, int RXM, int RYM) { return 2 * (size_t)((L + 1) / 2) * RXM * RYM; }
-__host__ __device__ inline size_t lat_reg_floats(int L, int BJ, int RXM, int RYM)
+__host__ __device__ constexpr size_t lat_g1_floats(int L, int RXM, int RYM) { return 2 * (size_t)((L + 1) / 2) * RXM * RYM; }
+__host__ __device__ constexpr size_t lat_reg_floats(int L, int BJ, int RXM, int RYM)
 {
-    const size_t v = (size_t)L * RXM * RYM, g2 = 2 * (size_t)L * BJ * RYM;
-    return ((v > g2 ? v : g2) + 3) & ~(size_t)3;
+    return (((size_t)L * RXM * RYM > 2 * (size_t)L * BJ * RYM ? (size_t)L * RXM * RYM : 2 * (size_t)L * BJ * RYM) + 3) &
+           ~(size_t)3;
 }
-inline size_t lat_smem_bytes(int L, int BJ, int BK, int RXM, int RYM)
+__host__ __device__ constexpr size_t lat_smem_bytes(int L, int BJ, int BK, int RXM, int RYM)
 {
     return sizeof(float) * (lat_g1_floats(L, RXM, RYM) + lat_reg_floats(L, BJ, RXM, RYM) + 3 * (size_t)BJ * BK * L);
+}
+
+// The lattice block of a CTA (BJ x BK points): the largest from 8 x 8 whose shared memory fits
+// two CTAs per SM (110 KB) and whose stage-y (BJ BK L) and stage-x (BJ RYM) items are at most 4
+// and 2 per thread.
+struct LatBlock {
+    int BJ, BK;
+};
+__host__ __device__ constexpr LatBlock lat_choose(int L, int s)
+{
+    int BJ = 8, BK = 8;
+    for (;;) {
+        const int RXM = (BJ - 1) * s + L, RYM = (BK - 1) * s + L;
+        if ((lat_smem_bytes(L, BJ, BK, RXM, RYM) <= 110 * 1024 && BJ * BK * L <= 4 * kLatThreads &&
+             BJ * RYM <= 2 * kLatThreads) ||
+            (BJ == 1 && BK == 1))
+            return LatBlock{BJ, BK};
+        if (BK >= BJ && BK > 1) BK /= 2; else BJ /= 2;
+    }
 }
 
 // |F| from |F|^2: the hardware approximate square root (one MUFU operation, a relative error
@@ -99,7 +118,11 @@ __device__ __forceinline__ void folded_dft(const float2 (&z)[L], const LatTw<L> 
     }
 }
 
-template <int L>
+// S_ > 0: the stride and hence the block geometry are compile-time constants (common cube
+// sizes and strides): every region spans the full RXM x RYM (columns past a block's last
+// lattice point are read, through the boundary extension at a face, and not used), so every
+// loop bound and shared-memory pitch is a constant.  S_ = 0: run-time geometry from g.
+template <int L, int S_ = 0>
 __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float *__restrict__ V, int64_t T, int64_t X,
                                                                      int64_t Y, int bnd, const LatGeo g,
                                                                      float *__restrict__ Ec,
@@ -107,6 +130,8 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
 {
     constexpr int H = (L - 1) / 2;
     constexpr int MAXIT = 4;   // stage-y items per thread (checked by the launcher)
+    constexpr bool CT = S_ > 0;
+    constexpr LatBlock CB = lat_choose(L, CT ? S_ : 1);
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
     // block -> (lattice plane, x block, y block) in 32 bits (the launcher keeps the grid below 2^31)
@@ -116,24 +141,26 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     const int jb = (int)(b % (unsigned)g.nbj);
     const int64_t i = b / (unsigned)g.nbj;
     // lattice coordinates in 32 bits (the launcher checks that every axis fits)
-    const int Xi = (int)X, Yi32 = (int)Y, s = g.s;
+    const int Xi = (int)X, Yi32 = (int)Y, s = CT ? S_ : g.s;
+    const int BJ = CT ? CB.BJ : g.BJ, BK = CT ? CB.BK : g.BK;
+    const int RXM = CT ? (CB.BJ - 1) * S_ + L : g.RXM, RYM = CT ? (CB.BK - 1) * S_ + L : g.RYM;
     auto coord = [s](int idx, int n) { return min(idx * s, n - 1); };
-    const int j0 = jb * g.BJ, k0 = kb * g.BK;
-    const int nj = min(g.BJ, (int)g.Xc - j0), nk = min(g.BK, (int)g.Yc - k0);
+    const int j0 = jb * BJ, k0 = kb * BK;
+    const int nj = min(BJ, (int)g.Xc - j0), nk = min(BK, (int)g.Yc - k0);
     const int64_t tc = coord((int)i, (int)T);
     const int xlo = coord(j0, Xi) - H, ylo = coord(k0, Yi32) - H;
-    const int RX = coord(j0 + nj - 1, Xi) + H - xlo + 1;
-    const int RY = coord(k0 + nk - 1, Yi32) + H - ylo + 1;
-    const int P = g.RYM;                                   // row pitch (floats or float2)
-    const int PL = g.RXM * P;                              // plane pitch of the V region / one G1 mu
+    const int RX = CT ? RXM : coord(j0 + nj - 1, Xi) + H - xlo + 1;
+    const int RY = CT ? RYM : coord(k0 + nk - 1, Yi32) + H - ylo + 1;
+    const int P = RYM;                                     // row pitch (floats or float2)
+    const int PL = RXM * P;                                // plane pitch of the V region / one G1 mu
 
     float2 *sG1 = reinterpret_cast<float2 *>(smem);                                   // [H+1][RXM][P]
-    float *sV = smem + lat_g1_floats(L, g.RXM, g.RYM);                                // [L][RXM][P]
+    float *sV = smem + lat_g1_floats(L, RXM, RYM);                                    // [L][RXM][P]
     float2 *sG2 = reinterpret_cast<float2 *>(sV);                                     // [L (nu)][BJ][P], after stage t
-    float *sacc = sV + lat_reg_floats(L, g.BJ, g.RXM, g.RYM);                         // [3][BJ * BK * L]
-    const int nitems = nj * nk * L;
-    const int accn = g.BJ * g.BK * L;
-    const int BJP = g.BJ * P;                              // G2 stride between nu lines
+    float *sacc = sV + lat_reg_floats(L, BJ, RXM, RYM);                               // [3][BJ * BK * L]
+    const int nitems = CT ? BJ * BK * L : nj * nk * L;     // compile-time geometry: every point of the block
+    const int accn = BJ * BK * L;
+    const int BJP = BJ * P;                                // G2 stride between nu lines
 
     LatTw<L> tw;
     tw.load(tb);
@@ -230,23 +257,23 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     // stage-y items of this thread (the same for every mu): item it = nu * npts + point, so
     // the lanes of a warp read neighbouring points of one line (few shared-memory bank
     // conflicts); line offset into sG2 (without the nu part) and the weight row
-    const int npts = nj * nk;
+    const int npts = CT ? BJ * BK : nj * nk, pnk = CT ? BK : nk;
     float acc[MAXIT][3];
     int ioff[MAXIT], inu[MAXIT];
 #pragma unroll
     for (int kk = 0; kk < MAXIT; ++kk) {
         acc[kk][0] = acc[kk][1] = acc[kk][2] = 0.f;
         const int it = tid + kk * kLatThreads;
-        const int nu = it / npts, pt = it - nu * npts, j = pt / nk, k = pt - j * nk;
+        const int nu = it / npts, pt = it - nu * npts, j = pt / pnk, k = pt - j * pnk;
         inu[kk] = nu;
-        ioff[kk] = j * P + (coord(k0 + k, Yi32) - H - ylo);
+        ioff[kk] = j * P + (coord(k0 + min(k, nk - 1), Yi32) - H - ylo);
     }
 
     // stage-x items of this thread (the same for every mu): column (j, r) of the lattice x
     // j; offsets into G1 (first tap) and into G2 (line nu = 0)
     constexpr int MAXX = 2;
     int xin[MAXX], xout[MAXX];
-    const int nxit = nj * RY;
+    const int nxit = CT ? BJ * RY : nj * RY;
 #pragma unroll
     for (int kk = 0; kk < MAXX; ++kk) {
         const int e = tid + kk * kLatThreads;
@@ -307,8 +334,8 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     for (int kk = 0; kk < MAXIT; ++kk) {
         const int it = tid + kk * kLatThreads;
         if (it >= nitems) break;
-        const int nu = inu[kk], pt = it - nu * npts, j = pt / nk, k = pt - j * nk;
-        const int slot = (j * g.BK + k) * L + nu;
+        const int nu = inu[kk], pt = it - nu * npts, j = pt / pnk, k = pt - j * pnk;
+        const int slot = (j * BK + k) * L + nu;
         sacc[slot] = acc[kk][0];
         sacc[accn + slot] = acc[kk][1];
         sacc[2 * accn + slot] = acc[kk][2];
@@ -318,7 +345,7 @@ __global__ void __launch_bounds__(kLatThreads) lattice_energy_kernel(const float
     const int64_t Nc = g.Tc * g.Xc * g.Yc;
     for (int e = tid; e < 3 * nj * nk; e += kLatThreads) {
         const int m = e / (nj * nk), pt = e - m * (nj * nk), j = pt / nk, k = pt - j * nk;
-        const float *a = sacc + m * accn + (j * g.BK + k) * L;
+        const float *a = sacc + m * accn + (j * BK + k) * L;
         float sum = 0.f;
 #pragma unroll
         for (int nu = 0; nu < L; ++nu) sum += a[nu];
@@ -382,7 +409,7 @@ __global__ void __launch_bounds__(256) interp_kernel(const float *__restrict__ E
     }
 }
 
-template <int L>
+template <int L, int S = 0>
 cudaError_t launch_lattice_L(const float *V, sal_dims d, int bnd, const LatGeo &g, float *Ec, cudaStream_t st)
 {
     SpecTables tb;
@@ -391,11 +418,11 @@ cudaError_t launch_lattice_L(const float *V, sal_dims d, int bnd, const LatGeo &
     if (g.BJ * g.BK * L > 4 * kLatThreads || g.BJ * g.RYM > 2 * kLatThreads)
         return cudaErrorInvalidValue;   // the kernel's stage-y and stage-x items per thread
     if (d.T > 0x3fffffffLL || d.X > 0x3fffffffLL || d.Y > 0x3fffffffLL) return cudaErrorInvalidValue;   // 32-bit coordinates
-    cudaError_t e = set_smem(lattice_energy_kernel<L>, smem);
+    cudaError_t e = set_smem(lattice_energy_kernel<L, S>, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = g.Tc * g.nbj * g.nbk;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    lattice_energy_kernel<L><<<(unsigned)blocks, kLatThreads, smem, st>>>(V, d.T, d.X, d.Y, bnd, g, Ec, tb);
+    lattice_energy_kernel<L, S><<<(unsigned)blocks, kLatThreads, smem, st>>>(V, d.T, d.X, d.Y, bnd, g, Ec, tb);
     return cudaGetLastError();
 }
 
@@ -410,26 +437,25 @@ cudaError_t launch_lattice_energy(const float *V, sal_dims d, int L, int bnd, in
     g.Tc = lattice_size(d.T, s);
     g.Xc = lattice_size(d.X, s);
     g.Yc = lattice_size(d.Y, s);
-    // the largest BJ x BK block (from 8 x 8) whose shared memory fits two CTAs per SM and whose
-    // stage-y items (BJ BK L) are at most 4 per thread
-    g.BJ = 8;
-    g.BK = 8;
-    for (;;) {
-        g.RXM = (g.BJ - 1) * s + L;
-        g.RYM = (g.BK - 1) * s + L;
-        const size_t need = lat_smem_bytes(L, g.BJ, g.BK, g.RXM, g.RYM);
-        if ((need <= 110 * 1024 && g.BJ * g.BK * L <= 4 * kLatThreads && g.BJ * g.RYM <= 2 * kLatThreads) ||
-            (g.BJ == 1 && g.BK == 1))
-            break;
-        if (g.BK >= g.BJ && g.BK > 1) g.BK /= 2; else g.BJ /= 2;
-    }
+    const LatBlock lb = lat_choose(L, s);
+    g.BJ = lb.BJ;
+    g.BK = lb.BK;
+    g.RXM = (g.BJ - 1) * s + L;
+    g.RYM = (g.BK - 1) * s + L;
     g.nbj = (int)((g.Xc + g.BJ - 1) / g.BJ);
     g.nbk = (int)((g.Yc + g.BK - 1) / g.BK);
     switch (L) {
     case 3: return launch_lattice_L<3>(V, d, bnd, g, Ec, st);
-    case 5: return launch_lattice_L<5>(V, d, bnd, g, Ec, st);
-    case 7: return launch_lattice_L<7>(V, d, bnd, g, Ec, st);
-    case 9: return launch_lattice_L<9>(V, d, bnd, g, Ec, st);
+    case 5: return s == 2 ? launch_lattice_L<5, 2>(V, d, bnd, g, Ec, st) : launch_lattice_L<5>(V, d, bnd, g, Ec, st);
+    case 7:
+        return s == 2   ? launch_lattice_L<7, 2>(V, d, bnd, g, Ec, st)
+               : s == 3 ? launch_lattice_L<7, 3>(V, d, bnd, g, Ec, st)
+                        : launch_lattice_L<7>(V, d, bnd, g, Ec, st);
+    case 9:
+        return s == 2   ? launch_lattice_L<9, 2>(V, d, bnd, g, Ec, st)
+               : s == 3 ? launch_lattice_L<9, 3>(V, d, bnd, g, Ec, st)
+               : s == 4 ? launch_lattice_L<9, 4>(V, d, bnd, g, Ec, st)
+                        : launch_lattice_L<9>(V, d, bnd, g, Ec, st);
     case 11: return launch_lattice_L<11>(V, d, bnd, g, Ec, st);
     case 13: return launch_lattice_L<13>(V, d, bnd, g, Ec, st);
     case 15: return launch_lattice_L<15>(V, d, bnd, g, Ec, st);
