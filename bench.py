@@ -37,6 +37,8 @@ WORKLOADS = {
     "slab": ((462, 951, 160), "f3", 1),     # a profiling case: the F3 shape cut to 160 inlines
     "batch64": (None, "basic", 0),           # 64 volumes, every axis U[32, 192], seeds 0..63
 }
+STENCIL_NAMES = {"26": "26-neighbourhood", "line": "d x 1 lines along each axis (Sec. 2)",
+                 "diag_tx": "d x 1 line along the t-x diagonal (Fig. 3)"}
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 sub-partitions x 32)
 MUFU_PER_SM_CLK = 16             # square roots per SM and clock on the XU (MUFU) pipe
 
@@ -90,7 +92,7 @@ def lattice_kernel_work(shape, L: int, s: int):
         g1 = 2 * (H + 1) * RXM * RYM
         reg = (max(L * RXM * RYM, 2 * L * BJ * RYM) + 3) // 4 * 4
         need = 4 * (g1 + reg + 3 * BJ * BK * L)
-        if (need <= 110 * 1024 and BJ * BK * L <= 1024) or (BJ == 1 and BK == 1):
+        if (need <= 110 * 1024 and BJ * BK * L <= 1024 and BJ * RYM <= 512) or (BJ == 1 and BK == 1):
             break
         if BK >= BJ and BK > 1:
             BK //= 2
@@ -109,6 +111,10 @@ def lattice_kernel_work(shape, L: int, s: int):
 
     nj, RX = blocks(shape[1], BJ)
     nk, RY = blocks(shape[2], BK)
+    if (L, s) in ((5, 2), (7, 2), (7, 3), (9, 2), (9, 3), (9, 4)):
+        # compile-time geometry: every CTA works on its full block and region
+        nj, RX = np.full(nj.size, BJ), np.full(nj.size, RXM)
+        nk, RY = np.full(nk.size, BK), np.full(nk.size, RYM)
     Tc = lattice_size(shape[0], s)
     per_item = 8 * H * H + 23 * H + 15
     t_stage = (L + 3 * H + 4 * H * H) * RX.sum() * RY.sum()
@@ -311,10 +317,10 @@ def workload_config(args) -> dict:
     shape = WORKLOADS[args.workload][0]
     stride = f", cubes at stride {args.stride} (E interpolated back)" if getattr(args, "stride", 1) > 1 else ""
     return {"workload": f"plain method {args.precision.upper()}, {'F3-shaped' if args.workload == 'f3' else 'synthetic'}"
-                        f" volume {shape[0]}x{shape[1]}x{shape[2]}, local cube {args.L}, 26-neighbourhood{stride}",
+                        f" volume {shape[0]}x{shape[1]}x{shape[2]}, local cube {args.L}, {STENCIL_NAMES[args.stencil]}{stride}",
             "stride": getattr(args, "stride", 1),
             "volume": list(shape), "L": args.L, "precision": args.precision, "boundary": "reflect",
-            "stencil": "26", "l2": "inputs larger than L2 (V 1.14 GB, E and S_m 3.4 GB each); no flush needed"
+            "stencil": args.stencil, "l2": "inputs larger than L2 (V 1.14 GB, E and S_m 3.4 GB each); no flush needed"
             if args.workload == "f3" else "flush buffer written between steps"}
 
 
@@ -626,7 +632,7 @@ def run_ours(args, rank: int, world: int) -> None:
     shape, kind, seed = WORKLOADS[args.workload]
     V_np = synth.make_volume(shape, seed=seed + rank, kind=kind)
     N = V_np.size
-    p = api.params(L=args.L, precision=args.precision, stride=args.stride)
+    p = api.params(L=args.L, precision=args.precision, stride=args.stride, stencil=args.stencil)
     V = torch.from_numpy(V_np).to(dev)
     E = torch.empty((3,) + shape, device=dev, dtype=torch.float32)
     lat = api.sal_lattice_dims(api.dims_of(V), p)
@@ -721,7 +727,8 @@ def run_ours(args, rank: int, world: int) -> None:
     # the other forms of the method on the same volume (BF16 and TF32 tensor-core y stage, cubes
     # at stride 3), each timed like the main step and compared with the FP32 path's E and S
     forms = {}
-    if args.stride == 1 and args.precision == "fp32" and args.workload == "f3" and not args.no_forms:
+    if args.stride == 1 and args.precision == "fp32" and args.workload == "f3" and args.stencil == "26" and \
+            not args.no_forms:
         E32 = E.clone()
         S32 = S.clone()
         lat3 = api.sal_lattice_dims(dims, api.params(L=args.L, stride=3))
@@ -873,6 +880,7 @@ def main():
     ap.add_argument("--L", type=int, default=7)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="fp32")
     ap.add_argument("--stride", type=int, default=1, help="cube stride (coarse-stride cubes, E interpolated back)")
+    ap.add_argument("--stencil", choices=["26", "line", "diag_tx"], default="26", help="neighbourhood of Eq. 5")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fma-probe", action="store_true", help="skip the FP32 FMA-rate probe")
