@@ -3,11 +3,13 @@
 //
 //   S_m[v] = Q^-1 sum_{o in N_m} | E_m[v] - g(o) E_m[v + o] |,  g(o) = exp(-|o|^2 / (2 sigma^2))
 //
-// N_m is the 26-neighbourhood or the d x 1 line of side d = L along axis m (Sec. 2 text
-// after Eq. 5).  E outside the volume comes from the boundary extension.  Each CTA stages
-// its halo tile of E_m in shared memory (each value read from HBM about once), every
-// thread produces four consecutive outputs along y, and the CTA reduces its min, max and
-// sum (warp shuffles, then FP64 across warps) into one partial record; two small passes
+// N_m is the 26-neighbourhood, the d x 1 line of side d = L along axis m (Sec. 2 text
+// after Eq. 5), the t-x diagonal line of Fig. 3 or a caller-given offset list.  E outside
+// the volume comes from the boundary extension.  A CTA walks a chunk of planes along t for
+// one 8 x 64 column block, the halo planes of E_m passing through a ring of shared-memory
+// slots (each value read from HBM about once); every thread produces 4 x 4 outputs per step
+// (4 planes, 4 consecutive columns along y), and the CTA reduces its min, max and sum (warp
+// shuffles, then FP64 across warps) into one partial record per chunk; two small passes
 // finish the FP64 reduction.
 #include <float.h>
 #include <stdlib.h>
@@ -21,8 +23,8 @@ namespace sal {
 
 namespace {
 
-// Output tile of one CTA (one map per CTA: blockIdx.y = m).  Every thread owns a 4 x 4
-// block (4 planes along t, 4 columns along y) at one x.
+// Column block of one CTA and the step along t: DT planes x DX rows x DY columns.  Every
+// thread owns a 4 x 4 block (4 planes along t, 4 columns along y) at one x.
 constexpr int DT = 8, DX = 8, DY = 64, QT = 4, QY = 4;
 constexpr int DNT = (DT / QT) * DX * (DY / QY);         // 256 threads
 constexpr int kRedBlocks = 160;                         // first pass of the partial reduction
@@ -48,7 +50,8 @@ struct Halo {
         PP = PX * pitch;
         planes = DT + 2 * rt_;
     }
-    __host__ __device__ constexpr int floats() const { return planes * PP; }
+    // shared memory of a ring holding the step's planes and the next step's DT planes
+    __host__ __device__ constexpr int ring_floats() const { return (planes + DT) * PP; }
 };
 
 __host__ __device__ inline Halo halo_for(int stencil, int m, int h)
@@ -76,160 +79,16 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
-// Stages the halo tile of E_m in shared memory with asynchronous 4-byte copies: each warp
-// takes whole rows (t, x) of the tile, its lanes consecutive columns, so every warp-wide
-// copy reads one contiguous run of E.  Rows and columns outside the volume are mapped by
-// the boundary extension (once per row for t and x, per column only at the y faces).
-__device__ __forceinline__ void stage_tile(const float *__restrict__ Em, float *sE, const Halo &hl, int64_t T, int64_t X,
-                                           int64_t Y, int bnd, int64_t t0, int64_t x0, int64_t y0)
-{
-    const int rows = hl.planes * hl.PX, W = DY + 2 * hl.ry;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < rows; r += DNT / 32) {
-        const int a = r / hl.PX, b = r - a * hl.PX;
-        const int64_t gt = ext_index(t0 - hl.rt + a, T, bnd);
-        const int64_t gx = ext_index(x0 - hl.rx + b, X, bnd);
-        const float *src = Em + (gt * X + gx) * Y;
-        float *dst = sE + a * hl.PP + b * hl.pitch + hl.off;
-        for (int c = lane; c < W; c += 32) {
-            int64_t gy = y0 - hl.ry + c;
-            if (gy < 0 || gy >= Y) gy = ext_index(gy, Y, bnd);
-            cp_async4(dst + c, src + gy);
-        }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
-// d x 1 line along axis m: out = sum_{q=1..h} |c - g(q) n(+q)| + |c - g(q) n(-q)|.
-__device__ __forceinline__ void dcs_line(const float *sE, const Halo &hl, int m, int tq, int x, int yq,
-                                         const DcsConsts &k, float (&out)[QT][QY])
-{
-    const int stride = m == 0 ? hl.PP : (m == 1 ? hl.pitch : 1);
-    const float *base = sE + (QT * tq + hl.rt) * hl.PP + (x + hl.rx) * hl.pitch + hl.off + hl.ry + QY * yq;
-#pragma unroll
-    for (int to = 0; to < QT; ++to)
-#pragma unroll
-        for (int yo = 0; yo < QY; ++yo) {
-            const float *c = base + to * hl.PP + yo;
-            const float cv = *c;
-            float s = 0.f;
-            for (int q = 1; q <= k.h; ++q) {
-                s += fabsf(fmaf(-k.gl[q], c[q * stride], cv));
-                s += fabsf(fmaf(-k.gl[q], c[-q * stride], cv));
-            }
-            out[to][yo] = s;
-        }
-}
-
-// Offset-list stencils (the t-x diagonal, caller-given neighbourhoods): out = sum_q
-// |c - w_q n(delta_q)|, delta_q the shared-memory offset of neighbour q from the centre.
-__device__ __forceinline__ void dcs_offsets(const float *sE, const Halo &hl, int tq, int x, int yq, const int *delta,
-                                            const float *w, int Q, float (&out)[QT][QY])
-{
-    const float *base = sE + (QT * tq + hl.rt) * hl.PP + (x + hl.rx) * hl.pitch + hl.off + hl.ry + QY * yq;
-    float cv[QT][QY];
-#pragma unroll
-    for (int to = 0; to < QT; ++to)
-#pragma unroll
-        for (int yo = 0; yo < QY; ++yo) {
-            cv[to][yo] = base[to * hl.PP + yo];
-            out[to][yo] = 0.f;
-        }
-    for (int q = 0; q < Q; ++q) {
-        const float *nb = base + delta[q];
-        const float wq = w[q];
-#pragma unroll
-        for (int to = 0; to < QT; ++to)
-#pragma unroll
-            for (int yo = 0; yo < QY; ++yo) out[to][yo] += fabsf(fmaf(-wq, nb[to * hl.PP + yo], cv[to][yo]));
-    }
-}
-
-// One map m of one output tile of one volume (line or offset-list stencil); writes the
-// tile's (min, max, sum) record.  Output planes are o_lo + 8 * (tile row) onwards, up to
-// o_hi; E has T planes (its boundary extension is taken at 0 and T), Sm holds the output
-// planes only.  `compute` fills a thread's 4 x 4 block of unnormalised sums.
-template <class Compute>
-__device__ __forceinline__ void dcs_tile(const float *__restrict__ E, int64_t T, int64_t X, int64_t Y, int bnd,
-                                         int64_t o_lo, int64_t o_hi, int m, int64_t tile, int tiles_x, int tiles_y,
-                                         float *__restrict__ Sm, double *__restrict__ partials, int64_t nparts,
-                                         const Halo &hl, float invQ, float *sE, double (*red)[3], Compute &&compute)
-{
-    const int ty = (int)(tile % tiles_y);
-    const int tx = (int)((tile / tiles_y) % tiles_x);
-    const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
-    const int64_t t0 = o_lo + tt * DT, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
-    const int64_t XY = X * Y, No = (o_hi - o_lo) * XY;
-
-    stage_tile(E + m * T * XY, sE, hl, T, X, Y, bnd, t0, x0, y0);
-    __syncthreads();
-
-    const int yq = threadIdx.x % (DY / QY);
-    const int x = (threadIdx.x / (DY / QY)) % DX;
-    const int tq = threadIdx.x / ((DY / QY) * DX);
-    float out[QT][QY];
-    compute(tq, x, yq, out);
-
-    float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
-    const int64_t gx = x0 + x, gy = y0 + QY * yq;
-    if (gx < X) {
-#pragma unroll
-        for (int to = 0; to < QT; ++to) {
-            const int64_t gt = t0 + QT * tq + to;
-            if (gt >= o_hi) break;
-            float *o = Sm + m * No + ((gt - o_lo) * X + gx) * Y + gy;
-#pragma unroll
-            for (int yo = 0; yo < QY; ++yo) {
-                out[to][yo] *= invQ;
-                if (gy + yo < Y) {
-                    mn = fminf(mn, out[to][yo]);
-                    mx = fmaxf(mx, out[to][yo]);
-                    sm += out[to][yo];
-                }
-            }
-            if (gy + QY <= Y && (Y & 3) == 0) {
-                *reinterpret_cast<float4 *>(o) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
-            } else {
-#pragma unroll
-                for (int yo = 0; yo < QY; ++yo)
-                    if (gy + yo < Y) o[yo] = out[to][yo];
-            }
-        }
-    }
-    mn = warp_min(mn);
-    mx = warp_max(mx);
-    sm = warp_sum(sm);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        red[warp][0] = mn;
-        red[warp][1] = mx;
-        red[warp][2] = sm;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        const int q = threadIdx.x;
-        double v = red[0][q];
-        for (int w = 1; w < DNT / 32; ++w) {
-            const double u = red[w][q];
-            v = q == 0 ? fmin(v, u) : (q == 1 ? fmax(v, u) : v + u);
-        }
-        partials[(3 * m + q) * nparts + tile] = v;
-    }
-}
-
-// Volumes of one launch; work item k of the launch is (volume, map, tile), map-major
-// within each volume.  Output planes [o_lo, o_hi) of E's T planes (the whole volume unless
+// Volumes of one launch; work item k of the launch is (volume, map, record), map-major
+// within each volume (a record: one chunk of SC planes of one column block).  Output planes [o_lo, o_hi) of E's T planes (the whole volume unless
 // the launch serves a slab).
 struct DVol {
     const float *E;
     float *Sm;
-    double *part;          // [9][tiles] records of this volume
+    double *part;          // [9][tiles] records of this volume (tiles = records per map)
     int64_t T, X, Y;
     int64_t o_lo, o_hi;
     int64_t item0, tiles;
@@ -249,51 +108,6 @@ __device__ __forceinline__ const DVol &find_volume(const DBatch &bt, int64_t it)
         if (bt.v[mid].item0 <= it) lo = mid; else hi = mid - 1;
     }
     return bt.v[lo];
-}
-
-__global__ void __launch_bounds__(DNT) dcs_line_kernel(const __grid_constant__ DBatch bt,
-                                                       const __grid_constant__ DcsConsts k)
-{
-    extern __shared__ __align__(16) float sE[];
-    __shared__ double red[DNT / 32][3];
-    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
-        const DVol &v = find_volume(bt, it);
-        const int64_t local = it - v.item0;
-        const int m = (int)(local / v.tiles);
-        const Halo hl = halo_for(SAL_STENCIL_LINE, m, k.h);
-        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, v.o_lo, v.o_hi, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm,
-                 v.part, v.tiles, hl, k.invQ, sE, red,
-                 [&](int tq, int x, int yq, float (&out)[QT][QY]) { dcs_line(sE, hl, m, tq, x, yq, k, out); });
-        __syncthreads();
-    }
-}
-
-// Offset-list neighbourhood of every map: halo radii, the neighbours' shared-memory offsets
-// from the centre (for that map's halo geometry), their weights and 1 / Q.
-struct DcsUser {
-    int Q[3];
-    int rt[3], rx[3], ry[3];
-    int delta[3][SAL_STENCIL_MAX_OFFSETS];
-    float w[3][SAL_STENCIL_MAX_OFFSETS];
-    float invQ[3];
-};
-
-__global__ void __launch_bounds__(DNT) dcs_user_kernel(const __grid_constant__ DBatch bt,
-                                                       const __grid_constant__ DcsUser u)
-{
-    extern __shared__ __align__(16) float sE[];
-    __shared__ double red[DNT / 32][3];
-    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
-        const DVol &v = find_volume(bt, it);
-        const int64_t local = it - v.item0;
-        const int m = (int)(local / v.tiles);
-        const Halo hl(u.rt[m], u.rx[m], u.ry[m]);
-        dcs_tile(v.E, v.T, v.X, v.Y, bt.bnd, v.o_lo, v.o_hi, m, local - m * v.tiles, v.tiles_x, v.tiles_y, v.Sm,
-                 v.part, v.tiles, hl, u.invQ[m], sE, red, [&](int tq, int x, int yq, float (&out)[QT][QY]) {
-                     dcs_offsets(sE, hl, tq, x, yq, u.delta[m], u.w[m], u.Q[m], out);
-                 });
-        __syncthreads();
-    }
 }
 
 // ---- 26-neighbourhood, planes streamed along t ------------------------------------------
@@ -339,6 +153,53 @@ __device__ __forceinline__ void write_record(float mn, float mx, float sm, doubl
             v = q == 0 ? fmin(v, u) : (q == 1 ? fmax(v, u) : v + u);
         }
         part[(3 * m + q) * nrec + rec] = v;
+    }
+}
+
+// Scales a thread's 4 x 4 block of sums by 1 / Q, folds the values inside the output (the
+// first nt planes, ny columns) into its running (min, max, sum) and stores them at o (plane
+// stride `plane`).  A whole block takes the widest stores its row start's alignment allows.
+__device__ __forceinline__ void emit_block(float (&out)[QT][QY], float invQ, float *o, int64_t plane, int nt, int ny,
+                                           float &mn, float &mx, float &sm)
+{
+    if (nt == QT && ny == QY) {
+#pragma unroll
+        for (int to = 0; to < QT; ++to) {
+#pragma unroll
+            for (int yo = 0; yo < QY; ++yo) {
+                out[to][yo] *= invQ;
+                mn = fminf(mn, out[to][yo]);
+                mx = fmaxf(mx, out[to][yo]);
+                sm += out[to][yo];
+            }
+            float *q = o + to * plane;
+            const unsigned a = (unsigned)(reinterpret_cast<uintptr_t>(q) & 15);
+            if (a == 0) {
+                *reinterpret_cast<float4 *>(q) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
+            } else if (a == 8) {
+                *reinterpret_cast<float2 *>(q) = make_float2(out[to][0], out[to][1]);
+                *reinterpret_cast<float2 *>(q + 2) = make_float2(out[to][2], out[to][3]);
+            } else {   // 4 or 12: q + 1 is 8-byte aligned
+                q[0] = out[to][0];
+                *reinterpret_cast<float2 *>(q + 1) = make_float2(out[to][1], out[to][2]);
+                q[3] = out[to][3];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int to = 0; to < QT; ++to) {
+            if (to >= nt) break;
+#pragma unroll
+            for (int yo = 0; yo < QY; ++yo) {
+                out[to][yo] *= invQ;
+                if (yo < ny) {
+                    mn = fminf(mn, out[to][yo]);
+                    mx = fmaxf(mx, out[to][yo]);
+                    sm += out[to][yo];
+                    o[to * plane + yo] = out[to][yo];
+                }
+            }
+        }
     }
 }
 
@@ -466,50 +327,269 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
                     }
 
                 if (gx < X) {
-                    const bool full = gy + QY <= Y && t0 + rb + QT <= o_hi;   // the whole 4 x 4 block is inside
-                    float *o = Sm + ((t0 - o_lo + rb) * X + gx) * Y + gy;
-                    const int64_t plane = X * Y;
-                    if (full) {
+                    const int64_t lt = o_hi - (t0 + rb), ly = Y - gy;
+                    emit_block(out, k.invQ, Sm + ((t0 - o_lo + rb) * X + gx) * Y + gy, X * Y,
+                               (int)(lt < QT ? lt : QT), (int)(ly < QY ? ly : QY), mn, mx, sm);
+                }
+            }
+            __syncthreads();
+        }
+        write_record(mn, mx, sm, red, v.part, m, v.tiles, rec);
+        __syncthreads();
+    }
+}
+
+// ---- line and offset-list stencils, planes streamed along t --------------------------------
+// The same walk as the 26-neighbourhood kernel: one work item = (volume, map, chunk of SC
+// planes, 8 x 64 column block), halo planes of the map's own stencil passing through a ring
+// of `ring` = (DT + 2 rt) + DT plane slots (the step's halo planes, and the next step's DT
+// planes in flight).  Slot s holds one halo plane (PX rows x pitch floats, geometry of
+// Halo) at s * PP.  A thread's copies within a plane (row b, column c of the halo, at most
+// KMAX) are set up once per item with their boundary extension; a plane then costs one
+// offset and KMAX copies.  The in-plane source offsets are 32-bit (the launcher checks
+// X * Y < 2^31).
+
+// Slot of halo plane sb + j (sb < ring, j < ring).
+__device__ __forceinline__ int wrap_slot(int s, int ring) { return s >= ring ? s - ring : s; }
+
+// d x 1 lines of half-width H along each axis (Sec. 2): out = sum_{q=1..H} |c - g(q) n(+q)|
+// + |c - g(q) n(-q)|.  Along t and x the neighbours of a thread's 4 outputs are 4 aligned
+// columns of another plane or row; along y the thread reads the window of columns
+// -4 ceil(H/4) .. 3 + 4 ceil(H/4) once per plane.
+template <int H>
+struct LineStencil {
+    DcsConsts k;
+    // copies per thread and plane: the largest halo plane is (DX + 2H) rows x DY columns
+    static constexpr int KMAX = ((DX + 2 * H) * DY + DNT - 1) / DNT;
+    // resident CTAs the register budget is cut for (the ring of the x line, the largest,
+    // leaves room for 3 CTAs per SM up to H = 3 and 2 beyond)
+    static constexpr int MINB = H <= 3 ? 3 : 2;
+    __device__ Halo halo(int m) const { return halo_for(SAL_STENCIL_LINE, m, H); }
+    __device__ float invQ(int) const { return k.invQ; }
+    // sb: slot of halo plane rb, the first plane any of the thread's neighbours lie in
+    __device__ __forceinline__ void compute(const float *sE, const Halo &hl, int ring, int m, int sb, int x, int yq,
+                                            float (&out)[QT][QY]) const
+    {
+        if (m == 0) {
+            int pb[QT + 2 * H];   // float offsets of the thread's column quad in halo planes rb + j
 #pragma unroll
-                        for (int to = 0; to < QT; ++to) {
+            for (int j = 0; j < QT + 2 * H; ++j) pb[j] = wrap_slot(sb + j, ring) * hl.PP + x * hl.pitch + QY * yq;
 #pragma unroll
-                            for (int yo = 0; yo < QY; ++yo) {
-                                out[to][yo] *= k.invQ;
-                                mn = fminf(mn, out[to][yo]);
-                                mx = fmaxf(mx, out[to][yo]);
-                                sm += out[to][yo];
-                            }
-                            // widest aligned stores for this row start
-                            float *q = o + to * plane;
-                            const unsigned a = (unsigned)(reinterpret_cast<uintptr_t>(q) & 15);
-                            if (a == 0) {
-                                *reinterpret_cast<float4 *>(q) = make_float4(out[to][0], out[to][1], out[to][2], out[to][3]);
-                            } else if (a == 8) {
-                                *reinterpret_cast<float2 *>(q) = make_float2(out[to][0], out[to][1]);
-                                *reinterpret_cast<float2 *>(q + 2) = make_float2(out[to][2], out[to][3]);
-                            } else {   // 4 or 12: q + 1 is 8-byte aligned
-                                q[0] = out[to][0];
-                                *reinterpret_cast<float2 *>(q + 1) = make_float2(out[to][1], out[to][2]);
-                                q[3] = out[to][3];
-                            }
-                        }
-                    } else {
+            for (int to = 0; to < QT; ++to) {
+                const float4 cv = lds4(sE + pb[to + H]);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-                        for (int to = 0; to < QT; ++to) {
-                            const int64_t gt = t0 + rb + to;
-                            if (gt >= o_hi) break;
+                for (int q = 1; q <= H; ++q) {
+                    const float g = k.gl[q];
+                    const float4 a = lds4(sE + pb[to + H + q]), b = lds4(sE + pb[to + H - q]);
+                    s0 += fabsf(fmaf(-g, a.x, cv.x));
+                    s0 += fabsf(fmaf(-g, b.x, cv.x));
+                    s1 += fabsf(fmaf(-g, a.y, cv.y));
+                    s1 += fabsf(fmaf(-g, b.y, cv.y));
+                    s2 += fabsf(fmaf(-g, a.z, cv.z));
+                    s2 += fabsf(fmaf(-g, b.z, cv.z));
+                    s3 += fabsf(fmaf(-g, a.w, cv.w));
+                    s3 += fabsf(fmaf(-g, b.w, cv.w));
+                }
+                out[to][0] = s0;
+                out[to][1] = s1;
+                out[to][2] = s2;
+                out[to][3] = s3;
+            }
+        } else if (m == 1) {
 #pragma unroll
-                            for (int yo = 0; yo < QY; ++yo) {
-                                out[to][yo] *= k.invQ;
-                                if (gy + yo < Y) {
-                                    mn = fminf(mn, out[to][yo]);
-                                    mx = fmaxf(mx, out[to][yo]);
-                                    sm += out[to][yo];
-                                    o[to * plane + yo] = out[to][yo];
-                                }
-                            }
-                        }
+            for (int to = 0; to < QT; ++to) {
+                const float *c = sE + wrap_slot(sb + to, ring) * hl.PP + (x + H) * hl.pitch + QY * yq;
+                const float4 cv = lds4(c);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                for (int q = 1; q <= H; ++q) {
+                    const float g = k.gl[q];
+                    const float4 a = lds4(c + q * hl.pitch), b = lds4(c - q * hl.pitch);
+                    s0 += fabsf(fmaf(-g, a.x, cv.x));
+                    s0 += fabsf(fmaf(-g, b.x, cv.x));
+                    s1 += fabsf(fmaf(-g, a.y, cv.y));
+                    s1 += fabsf(fmaf(-g, b.y, cv.y));
+                    s2 += fabsf(fmaf(-g, a.z, cv.z));
+                    s2 += fabsf(fmaf(-g, b.z, cv.z));
+                    s3 += fabsf(fmaf(-g, a.w, cv.w));
+                    s3 += fabsf(fmaf(-g, b.w, cv.w));
+                }
+                out[to][0] = s0;
+                out[to][1] = s1;
+                out[to][2] = s2;
+                out[to][3] = s3;
+            }
+        } else {
+            constexpr int W0 = (H + 3) / 4;   // 16-byte groups left (and right) of the centre's
+            float w[4 * (2 * W0 + 1)];
+#pragma unroll
+            for (int to = 0; to < QT; ++to) {
+                const float *c = sE + wrap_slot(sb + to, ring) * hl.PP + x * hl.pitch + hl.off + H + QY * yq;
+#pragma unroll
+                for (int j = 0; j <= 2 * W0; ++j) {
+                    const float4 v = lds4(c + 4 * (j - W0));
+                    w[4 * j] = v.x;
+                    w[4 * j + 1] = v.y;
+                    w[4 * j + 2] = v.z;
+                    w[4 * j + 3] = v.w;
+                }
+#pragma unroll
+                for (int yo = 0; yo < QY; ++yo) {
+                    const float cv = w[4 * W0 + yo];
+                    float s = 0.f;
+#pragma unroll
+                    for (int q = 1; q <= H; ++q) {
+                        s += fabsf(fmaf(-k.gl[q], w[4 * W0 + yo + q], cv));
+                        s += fabsf(fmaf(-k.gl[q], w[4 * W0 + yo - q], cv));
                     }
+                    out[to][yo] = s;
+                }
+            }
+        }
+    }
+};
+
+// Offset-list neighbourhood of every map (the t-x diagonal, caller-given stencils): halo
+// radii, each neighbour's plane offset dt and in-plane shared-memory offset dx * pitch + dy
+// (for that map's halo geometry), its weight, and 1 / Q.
+struct UserStencil {
+    int Q[3];
+    int rt[3], rx[3], ry[3];
+    int dt[3][SAL_STENCIL_MAX_OFFSETS];
+    int delta[3][SAL_STENCIL_MAX_OFFSETS];
+    float w[3][SAL_STENCIL_MAX_OFFSETS];
+    float iq[3];
+    static constexpr int KMAX =
+        ((DX + 2 * SAL_STENCIL_MAX_RADIUS) * (DY + 2 * SAL_STENCIL_MAX_RADIUS) + DNT - 1) / DNT;
+    static constexpr int MINB = 2;
+    __device__ Halo halo(int m) const { return Halo(rt[m], rx[m], ry[m]); }
+    __device__ float invQ(int m) const { return iq[m]; }
+    // out = sum_q |c - w_q n(dt_q, delta_q)|.  delta_q mod 4 is the neighbour's y offset mod 4
+    // (the same for every thread), so the 4 neighbours of a thread's outputs are one aligned
+    // 16-byte load, or two and a shift.
+    __device__ __forceinline__ void compute(const float *sE, const Halo &hl, int ring, int m, int sb, int x, int yq,
+                                            float (&out)[QT][QY]) const
+    {
+        const int col = (x + hl.rx) * hl.pitch + hl.off + hl.ry + QY * yq;   // centre column quad in a plane
+        float4 cv[QT];
+#pragma unroll
+        for (int to = 0; to < QT; ++to) {
+            cv[to] = lds4(sE + wrap_slot(sb + hl.rt + to, ring) * hl.PP + col);
+#pragma unroll
+            for (int yo = 0; yo < QY; ++yo) out[to][yo] = 0.f;
+        }
+        for (int q = 0; q < Q[m]; ++q) {
+            const int d = delta[m][q], da = d & ~3, sh = d - da;
+            const int s0 = sb + hl.rt + dt[m][q];   // slot of the neighbour plane of output plane 0
+            const float wq = w[m][q];
+#pragma unroll
+            for (int to = 0; to < QT; ++to) {
+                const float *p = sE + wrap_slot(s0 + to, ring) * hl.PP + col + da;
+                const float4 a = lds4(p);
+                float4 n = a;
+                if (sh != 0) {
+                    const float4 b = lds4(p + 4);
+                    n = sh == 1 ? make_float4(a.y, a.z, a.w, b.x)
+                                : (sh == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z));
+                }
+                out[to][0] += fabsf(fmaf(-wq, n.x, cv[to].x));
+                out[to][1] += fabsf(fmaf(-wq, n.y, cv[to].y));
+                out[to][2] += fabsf(fmaf(-wq, n.z, cv[to].z));
+                out[to][3] += fabsf(fmaf(-wq, n.w, cv[to].w));
+            }
+        }
+    }
+};
+
+template <class St>
+__global__ void __launch_bounds__(DNT, St::MINB) dcs_stream_kernel(const __grid_constant__ DBatch bt,
+                                                            const __grid_constant__ St sp)
+{
+    constexpr int KMAX = St::KMAX;
+    extern __shared__ __align__(16) float sE[];
+    __shared__ double red[DNT / 32][3];
+    const int tid = threadIdx.x;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(sE);
+    for (int64_t it = blockIdx.x; it < bt.total; it += gridDim.x) {
+        const DVol &v = find_volume(bt, it);
+        // item -> (map, chunk, x block, y block) in 32 bits (the launcher checks 3 x records)
+        const unsigned local = (unsigned)(it - v.item0), ntile = (unsigned)v.tiles;
+        const int m = (int)(local / ntile);
+        const unsigned rec = local - (unsigned)m * ntile, q1 = rec / (unsigned)v.tiles_y, q2 = q1 / (unsigned)v.tiles_x;
+        const int ty = (int)(rec - q1 * (unsigned)v.tiles_y);
+        const int tx = (int)(q1 - q2 * (unsigned)v.tiles_x);
+        const int64_t T = v.T, X = v.X, Y = v.Y, XY = X * Y;
+        const int64_t o_lo = v.o_lo, o_hi = v.o_hi;
+        const int64_t t0 = o_lo + (int64_t)q2 * SC, x0 = (int64_t)tx * DX, y0 = (int64_t)ty * DY;
+        const float *Em = v.E + m * T * XY;
+        const Halo hl = sp.halo(m);
+        const int ring = hl.planes + DT, W = DY + 2 * hl.ry, PE = hl.PX * W;
+
+        // this thread's copies within a halo plane: in-plane source offset (boundary extension
+        // along x and y applied) and byte offset in a slot, -1 past the plane's PE elements
+        int srco[KMAX], dsto[KMAX];
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q) {
+            const int e = tid + q * DNT;
+            srco[q] = 0;
+            dsto[q] = -1;
+            if (e < PE) {
+                const int b = e / W, c = e - b * W;
+                int64_t gx = x0 - hl.rx + b, gy = y0 - hl.ry + c;
+                if ((uint64_t)gx >= (uint64_t)X) gx = ext_index(gx, X, bt.bnd);
+                if ((uint64_t)gy >= (uint64_t)Y) gy = ext_index(gy, Y, bt.bnd);
+                srco[q] = (int)(gx * Y + gy);
+                dsto[q] = (b * hl.pitch + hl.off + c) * (int)sizeof(float);
+            }
+        }
+        // copies halo planes r0 .. r1 - 1 of the chunk (plane r is t0 - rt + r) into their slots
+        auto stage = [&](int r0, int r1) {
+            int slot = r0 % ring;
+            for (int r = r0; r < r1; ++r) {
+                int64_t gt = t0 - hl.rt + r;
+                if ((uint64_t)gt >= (uint64_t)T) gt = ext_index(gt, T, bt.bnd);
+                const float *pl = Em + gt * XY;
+                const unsigned dst = sbase + (unsigned)(slot * hl.PP * (int)sizeof(float));
+#pragma unroll
+                for (int q = 0; q < KMAX; ++q)
+                    if (dsto[q] >= 0)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + (unsigned)dsto[q]),
+                                     "l"(pl + srco[q])
+                                     : "memory");
+                slot = slot + 1 == ring ? 0 : slot + 1;
+            }
+            cp_async_commit();
+        };
+
+        const int64_t left = o_hi - t0;
+        const int nsteps = (int)(((left < SC ? left : SC) + DT - 1) / DT);
+        // thread -> (t quarter, x row, y quad); a block at the last columns packs its live quads
+        // into the first threads (see the 26-neighbourhood kernel)
+        const int64_t left_y = Y - y0;
+        const int nyq = left_y >= DY ? DY / QY : (int)((left_y + QY - 1) / QY);
+        const int yq = tid % nyq, x = (tid / nyq) % DX, tq = tid / (nyq * DX);
+        const bool live = tq < DT / QT;
+        const int64_t gx = x0 + x, gy = y0 + QY * yq;
+        float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
+
+        stage(0, hl.planes);
+        for (int st = 0; st < nsteps; ++st) {
+            if (st + 1 < nsteps) {
+                stage(DT * st + hl.planes, DT * st + hl.planes + DT);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            if (live) {
+                const int rb = DT * st + QT * tq;
+                float out[QT][QY];
+                sp.compute(sE, hl, ring, m, rb % ring, x, yq, out);
+                if (gx < X) {
+                    const int64_t lt = o_hi - (t0 + rb), ly = Y - gy;
+                    emit_block(out, sp.invQ(m), v.Sm + m * (o_hi - o_lo) * XY + ((t0 - o_lo + rb) * X + gx) * Y + gy,
+                               XY, (int)(lt < QT ? lt : QT), (int)(ly < QY ? ly : QY), mn, mx, sm);
                 }
             }
             __syncthreads();
@@ -629,11 +709,11 @@ DcsConsts dcs_consts(const sal_params *p)
     return k;
 }
 
-int64_t dcs_num_records(sal_dims d, int stencil)
+int64_t dcs_num_records(sal_dims d)
 {
     int64_t nt, nx, ny;
     dcs_tiles(d, &nt, &nx, &ny);
-    if (stencil == SAL_STENCIL_26) nt = (d.T + SC - 1) / SC;
+    nt = (d.T + SC - 1) / SC;
     return nt * nx * ny;
 }
 
@@ -662,9 +742,9 @@ sal_user_stencil diag_tx_stencil(const sal_params *p)
 
 namespace {
 
-DcsUser user_consts(const sal_user_stencil &st)
+UserStencil user_consts(const sal_user_stencil &st)
 {
-    DcsUser u;
+    UserStencil u;
     memset(&u, 0, sizeof(u));
     for (int m = 0; m < 3; ++m) {
         int rt = 0, rx = 0, ry = 0;
@@ -679,12 +759,30 @@ DcsUser user_consts(const sal_user_stencil &st)
         u.rx[m] = rx;
         u.ry[m] = ry;
         for (int q = 0; q < st.count[m]; ++q) {
-            u.delta[m][q] = st.offset[m][q][0] * hl.PP + st.offset[m][q][1] * hl.pitch + st.offset[m][q][2];
+            u.dt[m][q] = st.offset[m][q][0];
+            u.delta[m][q] = st.offset[m][q][1] * hl.pitch + st.offset[m][q][2];
             u.w[m][q] = st.weight[m][q];
         }
-        u.invQ[m] = (float)(1.0 / (double)st.count[m]);
+        u.iq[m] = (float)(1.0 / (double)st.count[m]);
     }
     return u;
+}
+
+template <class St>
+cudaError_t launch_stream(const DBatch &bt, const St &sp, int smem, int64_t total, cudaStream_t s)
+{
+    const void *fn = (const void *)dcs_stream_kernel<St>;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = set_smem(fn, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DNT, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t resident = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    const int64_t grid = total < resident ? total : resident;
+    if (grid <= 0) return cudaSuccess;
+    dcs_stream_kernel<St><<<(unsigned)grid, DNT, smem, s>>>(bt, sp);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -697,10 +795,10 @@ int dcs_user_radius_t(const sal_user_stencil &st)
     return r;
 }
 
-// Launches the compare over n volumes (persistent grid when batched; the 26-neighbourhood
-// kernel is always persistent).  `user` (offset lists per map) replaces p->stencil when
+// Launches the compare over n volumes as one persistent grid (resident CTAs walk every
+// (volume, map, tile) item).  `user` (offset lists per map) replaces p->stencil when
 // given; p->stencil == SAL_STENCIL_DIAG_TX builds the diagonal's list.
-cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s,
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, cudaStream_t s,
                              const sal_user_stencil *user)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
@@ -710,7 +808,8 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         user = &diag;
     }
     const bool s26 = !user && p->stencil == SAL_STENCIL_26;
-    const int rec_stencil = s26 ? SAL_STENCIL_26 : SAL_STENCIL_LINE;   // tiles of 8 planes unless 26
+    const int h = (p->L - 1) / 2;
+    if (!user && !s26 && (h < 1 || h > kMaxH)) return cudaErrorInvalidValue;
     DBatch bt;
     bt.n = n;
     bt.bnd = p->boundary;
@@ -721,6 +820,8 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         const sal_dims d{vols[i].T, vols[i].X, vols[i].Y};
         const int64_t o_lo = vols[i].o_lo, o_hi = vols[i].o_hi < 0 ? d.T : vols[i].o_hi;
         if (o_lo < 0 || o_hi > d.T || o_lo >= o_hi) return cudaErrorInvalidValue;
+        // the line and offset-list kernels hold in-plane offsets in 32 bits
+        if (!s26 && d.X * d.Y > 0x7fffffffLL) return cudaErrorInvalidValue;
         const sal_dims dout{o_hi - o_lo, d.X, d.Y};
         dcs_tiles(dout, &nt, &nx, &ny);
         v.E = vols[i].E;
@@ -731,7 +832,7 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
         v.Y = d.Y;
         v.o_lo = o_lo;
         v.o_hi = o_hi;
-        v.tiles = dcs_num_records(dout, rec_stencil);
+        v.tiles = dcs_num_records(dout);
         if (3 * v.tiles > 0x7fffffffLL) return cudaErrorInvalidValue;   // items of a volume in 32 bits
         v.tiles_x = (int)nx;
         v.tiles_y = (int)ny;
@@ -740,57 +841,53 @@ cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, b
     }
     bt.total = total;
     const DcsConsts k = dcs_consts(p);
-    DcsUser u;
-    const int h = (p->L - 1) / 2;
-    int smem = (int)kSmem26;
-    if (user) {
-        u = user_consts(*user);
-        smem = 0;
-        for (int m = 0; m < 3; ++m) {
-            const int f = Halo(u.rt[m], u.rx[m], u.ry[m]).floats() * (int)sizeof(float);
-            smem = f > smem ? f : smem;
-        }
-    } else if (!s26) {
-        smem = 0;
-        for (int m = 0; m < 3; ++m) {
-            const int f = halo_for(p->stencil, m, h).floats() * (int)sizeof(float);
-            smem = f > smem ? f : smem;
-        }
-    }
-    const void *fn = user ? (const void *)dcs_user_kernel
-                          : (s26 ? (const void *)dcs26_kernel : (const void *)dcs_line_kernel);
-    cudaError_t e = set_smem(fn, smem);
-    if (e != cudaSuccess) return e;
-    int64_t grid = total;
-    if (persistent || s26) {
+    if (s26) {
+        const void *fn = (const void *)dcs26_kernel;
         int dev = 0, nsm = 0, per_sm = 0;
-        e = cudaGetDevice(&dev);
+        cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DNT, smem);
+        if (e == cudaSuccess) e = set_smem(fn, (int)kSmem26);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DNT, (int)kSmem26);
         if (e != cudaSuccess) return e;
         const int64_t resident = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
-        if (grid > resident) grid = resident;
+        const int64_t grid = total < resident ? total : resident;
+        if (grid <= 0) return cudaSuccess;
+        dcs26_kernel<<<(unsigned)grid, DNT, kSmem26, s>>>(bt, k);
+        return cudaGetLastError();
     }
-    if (grid <= 0) return cudaSuccess;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (user)
-        dcs_user_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, u);
-    else if (s26)
-        dcs26_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
-    else
-        dcs_line_kernel<<<(unsigned)grid, DNT, smem, s>>>(bt, k);
-    return cudaGetLastError();
+    if (user) {
+        const UserStencil u = user_consts(*user);
+        int smem = 0;
+        for (int m = 0; m < 3; ++m) {
+            const int f = Halo(u.rt[m], u.rx[m], u.ry[m]).ring_floats() * (int)sizeof(float);
+            smem = f > smem ? f : smem;
+        }
+        return launch_stream(bt, u, smem, total, s);
+    }
+    int smem = 0;
+    for (int m = 0; m < 3; ++m) {
+        const int f = halo_for(SAL_STENCIL_LINE, m, h).ring_floats() * (int)sizeof(float);
+        smem = f > smem ? f : smem;
+    }
+    switch (h) {
+        case 1: return launch_stream(bt, LineStencil<1>{k}, smem, total, s);
+        case 2: return launch_stream(bt, LineStencil<2>{k}, smem, total, s);
+        case 3: return launch_stream(bt, LineStencil<3>{k}, smem, total, s);
+        case 4: return launch_stream(bt, LineStencil<4>{k}, smem, total, s);
+        case 5: return launch_stream(bt, LineStencil<5>{k}, smem, total, s);
+        case 6: return launch_stream(bt, LineStencil<6>{k}, smem, total, s);
+        default: return launch_stream(bt, LineStencil<7>{k}, smem, total, s);
+    }
 }
 
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials, double *stats,
                        cudaStream_t s, const sal_user_stencil *user, int64_t o_lo, int64_t o_hi)
 {
     if (o_hi < 0) o_hi = d.T;
-    const int rec_stencil = (!user && p->stencil == SAL_STENCIL_26) ? SAL_STENCIL_26 : SAL_STENCIL_LINE;
-    const int64_t tiles = dcs_num_records(sal_dims{o_hi - o_lo, d.X, d.Y}, rec_stencil);
+    const int64_t tiles = dcs_num_records(sal_dims{o_hi - o_lo, d.X, d.Y});
     if (3 * tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     DVolDesc v{E, Sm, partials, d.T, d.X, d.Y, o_lo, o_hi};
-    cudaError_t e = launch_dcs_items(&v, 1, p, false, s, user);
+    cudaError_t e = launch_dcs_items(&v, 1, p, s, user);
     if (e != cudaSuccess) return e;
     double *second = partials + 9 * tiles;
     reduce_partials_kernel<<<kRedBlocks, 256, 0, s>>>(partials, tiles, second, kRedBlocks);

@@ -358,7 +358,7 @@ sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p,
         double *part = (double *)(base + b.part[i]);
         dv[i] = sal::DVolDesc{ev[i].E, Sm, part, vols[i].T, vols[i].X, vols[i].Y};
         bv[i] = sal::BatchVolDesc{Sm, vols[i].S, part,
-                                  sal::dcs_num_records(sal_dims{vols[i].T, vols[i].X, vols[i].Y}, p->stencil),
+                                  sal::dcs_num_records(sal_dims{vols[i].T, vols[i].X, vols[i].Y}),
                                   vols[i].T * vols[i].X * vols[i].Y};
     }
     cudaError_t e;
@@ -370,7 +370,7 @@ sal_status enqueue_batch(const sal_volume *vols, int32_t n, const sal_params *p,
         e = sal::launch_energy_tc(ev, n, p->L, p->boundary, p->precision, true, c, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batched spectral energy launch");
-    e = sal::launch_dcs_items(dv, n, p, true, s);
+    e = sal::launch_dcs_items(dv, n, p, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched directional compare launch");
     e = sal::launch_batch_stats_combine(bv, n, p, stats ? stats : (double *)(base + b.stats), s);
     if (e != cudaSuccess) return cuda_fail(e, "batched statistics / combine launch");

@@ -125,7 +125,7 @@ struct DVolDesc {
     int64_t o_lo = 0, o_hi = -1;
 };
 // `user` (offset lists per map) replaces p->stencil when not NULL.
-cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, bool persistent, cudaStream_t s,
+cudaError_t launch_dcs_items(const DVolDesc *vols, int n, const sal_params *p, cudaStream_t s,
                              const sal_user_stencil *user = nullptr);
 // The t-x diagonal line of side L as an offset list, and the largest |dt| of a list.
 sal_user_stencil diag_tx_stencil(const sal_params *p);
@@ -136,7 +136,7 @@ cudaError_t launch_stats_merge(const double *in, int n, double *out, cudaStream_
 // Directional compare: capacity of partial records in the workspace (per map, any stencil,
 // plus the first reduction pass), and the records one map of a launch writes.
 int64_t dcs_num_partials(sal_dims d);
-int64_t dcs_num_records(sal_dims d, int stencil);
+int64_t dcs_num_records(sal_dims d);
 cudaError_t launch_dcs(const float *E, sal_dims d, const sal_params *p, float *Sm, double *partials,
                        double *stats, cudaStream_t s, const sal_user_stencil *user = nullptr, int64_t o_lo = 0,
                        int64_t o_hi = -1);

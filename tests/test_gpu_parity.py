@@ -127,6 +127,11 @@ def test_local_spectra_and_project_match_oracle(L, bnd):
     ("line", 15, "reflect", 2.0, (21, 19, 67)), ("26", 5, "periodic", 0.6, (21, 19, 67)),
     # several chunks of planes along t, the last one ragged; ragged x and y blocks
     ("26", 7, "reflect", 1.0, (150, 11, 70)), ("26", 5, "periodic", 0.8, (129, 9, 131)),
+    # the line kernel is compiled once per half-width h = 1 .. 7: every one of them, on
+    # ragged shapes (Y not a multiple of 4, so the stores take the per-column path)
+    ("line", 3, "reflect", 0.9, (19, 10, 37)), ("line", 5, "reflect", 1.1, (18, 17, 66)),
+    ("line", 9, "periodic", 1.5, (25, 12, 71)), ("line", 11, "reflect", 1.7, (23, 13, 65)),
+    ("line", 13, "periodic", 1.9, (27, 16, 90)),
 ])
 def test_directional_compare_matches_oracle(stc, L, bnd, sigma, shape):
     rng = np.random.default_rng(5)
