@@ -132,6 +132,9 @@ def test_local_spectra_and_project_match_oracle(L, bnd):
     ("line", 3, "reflect", 0.9, (19, 10, 37)), ("line", 5, "reflect", 1.1, (18, 17, 66)),
     ("line", 9, "periodic", 1.5, (25, 12, 71)), ("line", 11, "reflect", 1.7, (23, 13, 65)),
     ("line", 13, "periodic", 1.9, (27, 16, 90)),
+    # the line kernels over several chunks of 128 planes, the last one ragged
+    ("line", 7, "reflect", 1.0, (150, 11, 70)), ("line", 13, "periodic", 1.9, (140, 9, 67)),
+    ("line", 3, "periodic", 0.8, (257, 5, 41)),
 ])
 def test_directional_compare_matches_oracle(stc, L, bnd, sigma, shape):
     rng = np.random.default_rng(5)

@@ -33,7 +33,9 @@ def _stitched(V, p, parts):
 
 @pytest.mark.parametrize("shape,L,stc,parts", [((64, 40, 70), 7, "26", 3), ((50, 21, 64), 5, "line", 4),
                                                ((45, 19, 33), 9, "diag_tx", 2), ((130, 12, 64), 7, "26", 2),
-                                               ((31, 17, 36), 3, "26", 8)])
+                                               ((31, 17, 36), 3, "26", 8),
+                                               # slabs of several chunks of 128 planes for the streamed stencils
+                                               ((300, 10, 40), 7, "line", 2), ((270, 9, 35), 5, "diag_tx", 3)])
 def test_slabs_equal_the_whole_volume(shape, L, stc, parts):
     V = torch.from_numpy(synth.make_volume(shape, seed=13)).to(DEV)
     p = api.params(L=L, stencil=stc)

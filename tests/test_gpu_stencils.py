@@ -30,7 +30,9 @@ def to_dev(a):
 
 
 @pytest.mark.parametrize("L,bnd,sigma,shape", [(7, "reflect", 1.0, (21, 19, 67)), (5, "periodic", 0.7, (16, 23, 64)),
-                                               (15, "reflect", 2.0, (30, 17, 70)), (3, "periodic", 1.3, (9, 9, 9))])
+                                               (15, "reflect", 2.0, (30, 17, 70)), (3, "periodic", 1.3, (9, 9, 9)),
+                                               # several chunks of 128 planes, the last one ragged
+                                               (7, "reflect", 1.0, (150, 13, 70)), (5, "periodic", 0.9, (260, 9, 33))])
 def test_diag_tx_compare_matches_oracle(L, bnd, sigma, shape):
     rng = np.random.default_rng(11)
     E = rng.uniform(0.0, 1.0, size=(3,) + shape).astype(np.float32)
@@ -58,7 +60,9 @@ def _random_stencil(rng, q, radius):
 
 @pytest.mark.parametrize("q,radius,bnd,shape", [((1, 5, 12), 2, "reflect", (19, 21, 70)),
                                                 ((64, 30, 3), 7, "periodic", (24, 20, 66)),
-                                                ((9, 9, 9), 4, "reflect", (8, 9, 64))])
+                                                ((9, 9, 9), 4, "reflect", (8, 9, 64)),
+                                                ((10, 7, 20), 3, "reflect", (150, 12, 70)),
+                                                ((5, 40, 6), 7, "periodic", (131, 10, 67))])
 def test_user_stencil_matches_oracle(q, radius, bnd, shape):
     rng = np.random.default_rng(sum(q))
     offs, wts = _random_stencil(rng, q, radius)
