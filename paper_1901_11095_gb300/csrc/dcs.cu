@@ -269,15 +269,13 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
         const int64_t gx = x0 + x, gy = y0 + QY * yq;
         float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
 
+        // one barrier per step: it publishes the step's planes and also ends every thread's
+        // reads of the previous step, whose first DT slots the next step's copies then reuse
         stage(0, DT + 2);
         for (int st = 0; st < nsteps; ++st) {
-            if (st + 1 < nsteps) {
-                stage(DT * st + DT + 2, DT * st + 2 * DT + 2);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            cp_async_wait<0>();
             __syncthreads();
+            if (st + 1 < nsteps) stage(DT * st + DT + 2, DT * st + 2 * DT + 2);
 
             if (live) {
                 // halo planes rb .. rb + 5 of this thread's 4 output planes, rows x .. x + 2,
@@ -332,7 +330,6 @@ __global__ void __launch_bounds__(DNT, 4) dcs26_kernel(const __grid_constant__ D
                                (int)(lt < QT ? lt : QT), (int)(ly < QY ? ly : QY), mn, mx, sm);
                 }
             }
-            __syncthreads();
         }
         write_record(mn, mx, sm, red, v.part, m, v.tiles, rec);
         __syncthreads();
@@ -573,15 +570,12 @@ __global__ void __launch_bounds__(DNT, St::MINB) dcs_stream_kernel(const __grid_
         const int64_t gx = x0 + x, gy = y0 + QY * yq;
         float mn = FLT_MAX, mx = -FLT_MAX, sm = 0.f;
 
+        // one barrier per step, as in the 26-neighbourhood kernel
         stage(0, hl.planes);
         for (int st = 0; st < nsteps; ++st) {
-            if (st + 1 < nsteps) {
-                stage(DT * st + hl.planes, DT * st + hl.planes + DT);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            cp_async_wait<0>();
             __syncthreads();
+            if (st + 1 < nsteps) stage(DT * st + hl.planes, DT * st + hl.planes + DT);
             if (live) {
                 const int rb = DT * st + QT * tq;
                 float out[QT][QY];
@@ -592,7 +586,6 @@ __global__ void __launch_bounds__(DNT, St::MINB) dcs_stream_kernel(const __grid_
                                XY, (int)(lt < QT ? lt : QT), (int)(ly < QY ? ly : QY), mn, mx, sm);
                 }
             }
-            __syncthreads();
         }
         write_record(mn, mx, sm, red, v.part, m, v.tiles, rec);
         __syncthreads();
