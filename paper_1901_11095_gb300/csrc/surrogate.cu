@@ -14,7 +14,6 @@
 // result is exact.
 #include <string.h>
 
-#include <cuda.h>   // CUtensorMap and the tiled-map encoder's types (the encoder is found at run time)
 #include <cuda_bf16.h>
 
 #include "energy_tc.cuh"   // tcgen05 helpers: descriptors, bounded mbarrier wait, tensor-memory load
@@ -29,6 +28,14 @@ constexpr int HT = ST + 2, HXX = SX + 2, HYY = SY + 2, HN = HT * HXX * HYY;
 constexpr int CC = 8;                                        // input channels staged at once
 constexpr int kLayers = SAL_SURR_LAYERS, kWidth = SAL_SURR_WIDTH;
 constexpr int kWidths[kLayers + 1] = {1, kWidth, kWidth, kWidth, kWidth, 3};
+
+// BF16 activations of the tensor-core layers, grouped: for every line (t, x) the channel groups
+// of 8 one after another, each [y][8 channels] (16 bytes per voxel), so that a line's group is
+// one contiguous run of 16-byte rows (the layout the products read, copied in bulk).
+__host__ __device__ __forceinline__ int64_t gidx(int64_t line, int64_t Y, int64_t y, int o)
+{
+    return ((line * (kWidth / 8) + (o >> 3)) * Y + y) * 8 + (o & 7);
+}
 
 __device__ __forceinline__ float ldf(const float *p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
@@ -50,8 +57,8 @@ enum { FWD_HIDDEN = 0, FWD_OUTPUT = 1, BWD_DATA = 2 };
 //   BWD_DATA:   in = dL/dz of the next layer, weights transposed and flipped (the adjoint),
 //               samples outside the volume are zero; out = result * gelu'(zprev)
 // Weights are the FP32 master parameters rounded to BF16 as they are staged.  ILV: BF16
-// activations (input or output) are interleaved [voxel][channel] instead of planar
-// [channel][voxel] (the layout of the tensor-core layers).
+// activations (input or output) in the grouped layout of the tensor-core layers (gidx)
+// instead of planar [channel][voxel].
 template <int CI, int CO, typename TIN, typename TOUT, int MODE, bool ILV = false>
 __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, int64_t T, int64_t X, int64_t Y,
                                                    int bnd, const float *__restrict__ in_scale_p,
@@ -95,7 +102,7 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
                 const int64_t gt = ext_index(gt0, T, bnd), gx = ext_index(gx0, X, bnd), gy = ext_index(gy0, Y, bnd);
                 const int64_t vox = (gt * X + gx) * Y + gy;
                 const bool ilv_in = ILV && sizeof(TIN) == 2;
-                v = ldf(in + (ilv_in ? vox * CI + (c0 + c) : (c0 + c) * N + vox)) * in_scale;
+                v = ldf(in + (ilv_in ? gidx(gt * X + gx, Y, gy, c0 + c) : (c0 + c) * N + vox)) * in_scale;
             }
             xs[e] = v;
         }
@@ -136,7 +143,6 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
             const int64_t gy = y0 + 2 * yp;
             if (gy >= Y) return;
             const int nr = gy + 1 < Y ? 2 : 1;
-            uint4 *dst = reinterpret_cast<uint4 *>(out + ((gt * X + gx) * Y + gy) * CO);
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 if (r >= nr) break;
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
                         const __nv_bfloat162 h = __floats2bfloat162_rn(gelu(acc[8 * g + 2 * j][r]), gelu(acc[8 * g + 2 * j + 1][r]));
                         memcpy(&p[j], &h, 4);
                     }
-                    dst[r * (CO / 8) + g] = make_uint4(p[0], p[1], p[2], p[3]);
+                    *reinterpret_cast<uint4 *>(out + gidx(gt * X + gx, Y, gy + r, 8 * g)) = make_uint4(p[0], p[1], p[2], p[3]);
                 }
             }
             return;
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(SNT) conv_kernel(const TIN *__restrict__ in, i
             if (MODE == FWD_HIDDEN) {
                 if (zout) zout[o * N + v] = z;
                 const bool ilv_out = ILV && sizeof(TOUT) == 2;
-                stf(out + (ilv_out ? v * CO + o : o * N + v), gelu(z));
+                stf(out + (ilv_out ? gidx(gt * X + gx, Y, gy, o) : o * N + v), gelu(z));
             } else if (MODE == FWD_OUTPUT) {
                 stf(out + o * N + v, z * out_scale);
             } else {
@@ -445,40 +451,31 @@ cudaError_t launch_wgrad(const float *a, const float *a_scale, const float *g, s
 //     D[y][o] += sum_c A_tap[y][c] W[o][c][tap],  A_tap[y][c] = act[t + dt][x + dx][y + dy][c],
 // 27 taps x 2 products of K = 16 (channels 0..15 and 16..31, 24..31 meeting zero weights),
 // M = 128, BF16 operands, FP32 accumulation in tensor memory.  CO = 24: hidden layer (N = 32,
-// bias, GELU, BF16 interleaved out); CO = 3: output layer (N = 16, outputs 3..15 zero; bias and
-// the RMS scale applied, FP32 E written planar [3][voxel]).  Activations interleaved [voxel][24].
+// bias, GELU, BF16 grouped out); CO = 3: output layer (N = 16, outputs 3..15 zero; bias and
+// the RMS scale applied, FP32 E written planar [3][voxel]).  Activations in the grouped
+// layout (gidx).
 //
-// The 3 x 3 halo lines of a tile sit in shared memory as [line][channel group of 8][y][8
-// channels]: K-major core matrices of 8 rows x 16 bytes, 8-row groups 128 bytes apart, channel
-// groups 2176 bytes apart (130 rows on a 128-byte boundary, as the tensor-memory-access unit
-// requires of its destinations).  The operand of every tap is the same buffer at a byte offset
-// added to the descriptor's start address, so no operand is rebuilt per tap.  Only the three
-// real channel groups are kept: the second k-step's upper group reads the next line's first
-// group (or a zero pad after the last line), which meets the zero weights of channels 24..31.
+// The halo lines of a tile sit in shared memory as [line][channel group of 8][y][8 channels]:
+// K-major core matrices of 8 rows x 16 bytes, 8-row groups 128 bytes apart, channel groups
+// 2176 bytes apart.  The operand of every tap is a line's buffer at a byte offset added to
+// the descriptor's start address, so no operand is rebuilt per tap.  Only the three real
+// channel groups are kept: the second k-step's upper group reads the next t-line's first
+// group (or a zero pad after the last one), which meets the zero weights of channels 24..31.
 // Likewise the hidden layer's B tiles keep their 24 real rows (768 bytes each): the 4th 8-row
 // group a product reads is the next tile's first and lands in outputs 24..31, never used.
-// One halo and one accumulator per CTA, two CTAs per SM, persistent over the line tiles; the
-// next tile's halo is loaded while this tile's epilogue runs: interior tiles by 27
-// tensor-memory-access boxes (130 rows x 8 channels) counted in bytes on an mbarrier, tiles at
-// a face of the volume by 16-byte cp.async copies with the boundary extension.  Every wait is
-// bounded; on expiry the status word gets SAL_ERR_TIMEOUT.
+// Each (line, group) is one contiguous run of the grouped activations, copied in bulk and
+// counted in bytes on an mbarrier (a tensor-map load of boxes of 8 channels moves 16 bytes per
+// row: it took about 7,000 cycles per 9-line halo).  The kernel is persistent (one CTA per SM)
+// and warp-specialised, and tiles along x share their halo lines (see conv_tc2_kernel).
+// Every wait is bounded; on expiry the status word gets SAL_ERR_TIMEOUT.
 constexpr int TCY = 128, TCH = TCY + 2;                     // outputs per line tile, halo rows
-constexpr int TC_NT = 256;
 constexpr int TC1_GRP = 17 * 128;                           // bytes of one channel group of a line
-constexpr int TC1_LINE = 3 * TC1_GRP;
-constexpr int TC1_HALO = 9 * TC1_LINE + TCH * 16;
 
-// A line tile: its first output plane t, row x and first column y0 (32-bit: the launcher
-// checks that T, X, Y and the tile count fit).
+// A line tile: its output plane t, row x and first column y0 (32-bit: the launcher checks
+// that T, X, Y and the tile count fit).
 struct TileC {
     int t, x, y0;
 };
-
-__device__ __forceinline__ TileC tile_coords(long long k, int X, int ny)
-{
-    const unsigned kk = (unsigned)k, r = kk / (unsigned)ny;
-    return TileC{(int)(r / (unsigned)X), (int)(r % (unsigned)X), (int)(kk - r * (unsigned)ny) * TCY};
-}
 
 // Boundary extension of one coordinate in 32 bits (one reflection or wrap; wider cases take
 // the general routine).
@@ -496,12 +493,6 @@ __device__ __forceinline__ int ext32(int i, int n, int bnd)
     return (int)ext_index(i, n, bnd);
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-
 __device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -509,63 +500,16 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t a, uint64_t 
                  "r"(idesc), "r"(acc));
 }
 
-// The halo of tile c by 16-byte copies with the boundary extension (group 3 is never written).
-// Line by line: the extension of t and x is taken once per line, consecutive threads copy
-// consecutive 16-byte pieces of consecutive rows, and rows need the extension only at a face.
-__device__ __forceinline__ void tc1_stage(const __nv_bfloat16 *__restrict__ in, int T, int X, int Y, int bnd, TileC c,
-                                          unsigned char *buf)
-{
-    const bool yin = c.y0 >= 1 && c.y0 - 1 + TCH <= Y;
-#pragma unroll 1
-    for (int line = 0; line < 9; ++line) {
-        const int gt = ext32(c.t + line / 3 - 1, T, bnd), gx = ext32(c.x + line % 3 - 1, X, bnd);
-        const __nv_bfloat16 *src = in + ((int64_t)gt * X + gx) * Y * kWidth;
-        unsigned char *dst = buf + line * TC1_LINE;
-        for (int e = threadIdx.x; e < TCH * 3; e += TC_NT) {
-            const int yy = e / 3, kc = e - yy * 3;
-            const int gy = yin ? c.y0 - 1 + yy : ext32(c.y0 - 1 + yy, Y, bnd);
-            cp_async16(dst + kc * TC1_GRP + yy * 16, src + gy * kWidth + kc * 8);
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// Whether the whole halo of tile c lies inside the volume (no boundary extension needed).
-__device__ __forceinline__ bool tc1_interior(int T, int X, int Y, TileC c)
-{
-    return c.y0 >= 1 && c.y0 + TCY + 1 <= Y && c.x >= 1 && c.x + 1 < X && c.t >= 1 && c.t + 1 < T;
-}
-
-// The halo of an interior tile by the tensor-memory-access unit: 27 boxes of 130 rows x 8
-// channels (one per line and channel group), each landing as [y][8 channels] in its place;
-// completion is counted in bytes on the barrier.  Issued by one thread.
-__device__ __forceinline__ void tc1_stage_tma(const CUtensorMap *tmap, TileC c, unsigned char *buf, uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9 * 3 * TCH * 16) : "memory");
-    const uint64_t tm = reinterpret_cast<uint64_t>(tmap);
-    for (int line = 0; line < 9; ++line) {
-        const int t = c.t + line / 3 - 1, x = c.x + line % 3 - 1;
-        for (int kc = 0; kc < 3; ++kc) {
-            const uint32_t dst = energy_detail::smem_u32(buf + line * TC1_LINE + kc * TC1_GRP);
-            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                         "%4, %5}], [%6];" ::"r"(dst),
-                         "l"(tm), "r"(kc * 8), "r"(c.y0 - 1), "r"(x), "r"(t), "r"(bar)
-                         : "memory");
-        }
-    }
-}
-
-// Bias, GELU, BF16 and store of the hidden layer's accumulator: warp w reads lane quadrant
-// w % 4 (rows = y) and column half w / 4 (channels 0..15 or 16..23).
-__device__ __forceinline__ void tc_epilogue_hidden(uint32_t tmem, TileC c, int X, int Y, const float *sb,
+// Bias, GELU, BF16 and store of the hidden layer's accumulator `acc` for the 32 voxels of lane
+// quadrant q (rows = y) and channel half h (channels 0..15 or 16..23).
+__device__ __forceinline__ void tc_epilogue_hidden(uint32_t acc, int q, int h, TileC c, int X, int Y, const float *sb,
                                                    __nv_bfloat16 *__restrict__ out)
 {
-    const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
     float v[16];
-    energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h), v);
+    energy_detail::tmem_ld16(acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h), v);
     const int y = c.y0 + 32 * q + (threadIdx.x & 31);
     if (y >= Y) return;
-    __nv_bfloat16 *o = out + (((int64_t)c.t * X + c.x) * Y + y) * kWidth + 16 * h;
+    const int64_t line = (int64_t)c.t * X + c.x;
     uint32_t pk[8];
     const int npairs = h == 0 ? 8 : (kWidth - 16) / 2;
 #pragma unroll
@@ -576,52 +520,131 @@ __device__ __forceinline__ void tc_epilogue_hidden(uint32_t tmem, TileC c, int X
         const __nv_bfloat162 p2 = __floats2bfloat162_rn(a, bb);
         pk[j] = *reinterpret_cast<const uint32_t *>(&p2);
     }
-    *reinterpret_cast<uint4 *>(o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    if (h == 0) *reinterpret_cast<uint4 *>(o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    *reinterpret_cast<uint4 *>(out + gidx(line, Y, y, 16 * h)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    if (h == 0) *reinterpret_cast<uint4 *>(out + gidx(line, Y, y, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+// Warp roles of the pipelined layer: warp 0 stages halo lines, warp 1 issues the products,
+// warps 2..9 run the epilogue (warp w reads tensor-memory lane quadrant w % 4, channel half
+// (w - 2) / 4).  A CTA walks runs of up to XC consecutive tiles along x at one (t, y0), so
+// that each tile brings in only the three lines (t - 1..t + 1) at x + 1 and reuses the other
+// six from its neighbours: a "line step" stages the lines of one x (3 t-lines x 3 channel
+// groups = 9 bulk copies) into one of RS slots, tile j of a run reads the slots of line steps
+// j, j + 1, j + 2, and each slot is refilled once the last tile reading it has finished its
+// products.  Two accumulators: while the products of one tile run, the epilogue of the
+// previous one drains the other.
+constexpr int TC2_EPI = 8;                                    // epilogue warps
+constexpr int TC2_NT = 32 * (2 + TC2_EPI);
+constexpr int TC2_RS = 6;                                     // line-step slots
+constexpr int TC2_TLINE = 3 * TC1_GRP;                        // one t-line: 3 channel groups
+constexpr int TC2_SLOT = 3 * TC2_TLINE;                       // one line step: 3 t-lines
+constexpr int TC2_PAD = (TCH * 16 + 127) / 128 * 128;         // read by the last t-line's upper group
+
+template <int CO>
+constexpr size_t tc2_wbytes() { return (size_t)27 * 2 * (CO > 16 ? 768 : 512) + (CO > 16 ? 256 : 0); }
+template <int CO>
+constexpr size_t tc2_smem() { return tc2_wbytes<CO>() + (size_t)TC2_RS * TC2_SLOT + TC2_PAD + (2 * TC2_RS + 4) * 8 + 16; }
+
+// A run of tiles: plane t, first output column y0, first x and its length n.
+struct TcRun {
+    int t, y0, x0, n;
+};
+__device__ __forceinline__ TcRun tc_run(long long k, int X, int ny, int nxc, int XC)
+{
+    const unsigned kk = (unsigned)k, q = kk / (unsigned)nxc, xc = kk - q * (unsigned)nxc;
+    TcRun r;
+    r.t = (int)(q / (unsigned)ny);
+    r.y0 = (int)(q - (unsigned)r.t * (unsigned)ny) * TCY;
+    r.x0 = (int)xc * XC;
+    r.n = X - r.x0 < XC ? X - r.x0 : XC;
+    return r;
+}
+
+// Line step l of run r into `slot`: lanes 0..8 copy (t-line, group) e in bulk (rows inside
+// the volume along y, counted in bytes on `bar`, armed first by lane 0), lanes 0..17 store the
+// y-extension rows (y = -1 when y0 = 0, y = Y when the halo passes Y), which the copies never
+// write; the stores are made visible to the tensor cores before lane 0's arrival.
+__device__ __forceinline__ void tc2_stage_line(const __nv_bfloat16 *__restrict__ in, int T, int X, int Y, int bnd,
+                                               const TcRun &r, int l, unsigned char *slot, uint32_t bar)
+{
+    const int lane = threadIdx.x & 31;
+    const int gx = ext32(r.x0 - 1 + l, X, bnd);
+    const int ys = r.y0 >= 1 ? r.y0 - 1 : 0, ye = r.y0 + TCY + 1 < Y ? r.y0 + TCY + 1 : Y;
+    const uint32_t bytes = (uint32_t)(ye - ys) * 16u;
+    if (lane == 0) asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(9u * bytes) : "memory");
+    __syncwarp();
+    if (lane < 9) {
+        const int tl = lane / 3, g = lane - tl * 3;
+        const int gt = ext32(r.t + tl - 1, T, bnd);
+        const __nv_bfloat16 *src = in + gidx((int64_t)gt * X + gx, Y, ys, 8 * g);
+        const uint32_t dst = energy_detail::smem_u32(slot + tl * TC2_TLINE + g * TC1_GRP + (ys - (r.y0 - 1)) * 16);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                     "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+    }
+    if (lane < 18) {
+        const int side = lane / 9, piece = lane - side * 9, tl = piece / 3, g = piece - tl * 3;
+        const int row = side == 0 ? 0 : Y - r.y0 + 1;
+        if (side == 0 ? r.y0 == 0 : row < TCH) {
+            const int gt = ext32(r.t + tl - 1, T, bnd), gy = ext32(side == 0 ? -1 : Y, Y, bnd);
+            *reinterpret_cast<uint4 *>(slot + tl * TC2_TLINE + g * TC1_GRP + row * 16) =
+                *reinterpret_cast<const uint4 *>(in + gidx((int64_t)gt * X + gx, Y, gy, 8 * g));
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 template <int CO>
-__global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 *__restrict__ in, int T, int X,
-                                                            int Y, int bnd, const float *__restrict__ w,
-                                                            const float *__restrict__ b, __nv_bfloat16 *__restrict__ out,
-                                                            float *__restrict__ E,
-                                                            const float *__restrict__ out_scale_p, int *status,
-                                                            int stall, uint64_t limit_ns,
-                                                            const __grid_constant__ CUtensorMap tmap, int use_tma)
+__global__ void __launch_bounds__(TC2_NT, 1) conv_tc2_kernel(const __nv_bfloat16 *__restrict__ in, int T, int X,
+                                                             int Y, int bnd, const float *__restrict__ w,
+                                                             const float *__restrict__ b, __nv_bfloat16 *__restrict__ out,
+                                                             float *__restrict__ E,
+                                                             const float *__restrict__ out_scale_p, int *status,
+                                                             int stall, uint64_t limit_ns, int XC)
 {
     constexpr int NB = CO > 16 ? 32 : 16;       // N of the products
     constexpr int BT = CO > 16 ? 768 : 512;     // bytes between B tiles (24 or 16 stored rows x 16 BF16)
-    constexpr int WB = 27 * 2 * BT + (CO > 16 ? 256 : 0);   // + the 4th group the last tile reads
-    static_assert(WB % 128 == 0, "halo on a 128-byte boundary");
+    constexpr int WB = (int)tc2_wbytes<CO>();   // + the 4th group the last tile reads
+    static_assert(WB % 128 == 0 && TC2_SLOT % 128 == 0, "slots on 128-byte boundaries");
+    using energy_detail::mbar_wait;
     using energy_detail::smem_u32;
     extern __shared__ __align__(128) unsigned char tc_sm[];
-    unsigned char *sW = tc_sm, *sHb = tc_sm + WB;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sHb + TC1_HALO);   // [0]: products, [1]: halo copies
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    unsigned char *sW = tc_sm, *sL = tc_sm + WB;                  // slot s at sL + s * TC2_SLOT, then the pad
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sL + TC2_RS * TC2_SLOT + TC2_PAD);
+    // lfull[s]: line step in slot s landed (bytes + the producer's arrival); lfree[s]: its last
+    // tile's products done; bacc[a]: accumulator a full; bdrain[a]: drained (one arrival per
+    // epilogue warp).  Line step L uses slot L % RS (its L / RS-th use), tile G accumulator G % 2.
+    uint64_t *lfull = bar, *lfree = bar + TC2_RS, *bacc = bar + 2 * TC2_RS, *bdrain = bar + 2 * TC2_RS + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2 * TC2_RS + 4);
     __shared__ float sb[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     constexpr int NS = BT / 32;                 // stored rows per B tile
-    for (int e = threadIdx.x; e < 27 * 2 * NS * 16; e += TC_NT) {
+    for (int e = threadIdx.x; e < 27 * 2 * NS * 16; e += TC2_NT) {
         const int kk = e & 15, n = (e >> 4) % NS, ts = e / (16 * NS), tap = ts >> 1, ks = ts & 1;
         const int cin = ks * 16 + kk;
         const float v = (n < CO && cin < kWidth) ? w[((int64_t)n * kWidth + cin) * 27 + tap] : 0.f;
         *reinterpret_cast<__nv_bfloat16 *>(sW + ts * BT + ((n >> 3) * 2 + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
             __float2bfloat16_rn(v);
     }
-    for (int e = threadIdx.x; e < (WB - 27 * 2 * BT) / 16; e += TC_NT)   // finite rows after the last tile
+    for (int e = threadIdx.x; e < (WB - 27 * 2 * BT) / 16; e += TC2_NT)   // finite rows after the last tile
         *reinterpret_cast<uint4 *>(sW + 27 * 2 * BT + e * 16) = make_uint4(0, 0, 0, 0);
     if (threadIdx.x < 32) sb[threadIdx.x] = threadIdx.x < CO ? b[threadIdx.x] : 0.f;
-    for (int e = threadIdx.x; e < TCH; e += TC_NT)   // the pad read by the last line's upper group
-        *reinterpret_cast<uint4 *>(sHb + 9 * TC1_LINE + e * 16) = make_uint4(0, 0, 0, 0);
-    // the tensor-memory-access unit writes only to 128-byte aligned destinations
-    if (smem_u32(sHb) & 127u) use_tma = 0;
+    // slots and pad start at zero: every byte a product reads is finite (the upper group of a
+    // t-line's second k-step is the next t-line's first group, or the pad, at zero weights)
+    for (int e = threadIdx.x; e < (TC2_RS * TC2_SLOT + TC2_PAD) / 16; e += TC2_NT)
+        *reinterpret_cast<uint4 *>(sL + e * 16) = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
+        for (int i = 0; i < 2 * TC2_RS + 4; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)),
+                         "r"(i >= 2 * TC2_RS + 2 ? TC2_EPI : 1)
+                         : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tslot)) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tslot)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -629,139 +652,126 @@ __global__ void __launch_bounds__(TC_NT, 2) conv_tc1_kernel(const __nv_bfloat16 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const float out_scale = out_scale_p ? *out_scale_p : 1.f;
 
-    const int ny = (Y + TCY - 1) / TCY;
-    const long long ntiles = (long long)T * X * ny, Nv = (long long)T * X * Y;
-    constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, NB);
-    uint32_t phase = 0u, tphase = 0u;
-    bool ok = true, tma_pending = false;
-    // stages tile c by the tensor-memory-access unit when its halo is interior, else by copies
-    auto stage = [&](TileC c) -> bool {
-        if (use_tma && tc1_interior(T, X, Y, c)) {
-            if (threadIdx.x == 0) tc1_stage_tma(&tmap, c, sHb, smem_u32(bar + 1));
-            return true;
-        }
-        tc1_stage(in, T, X, Y, bnd, c, sHb);
-        return false;
-    };
-    TileC cur{0, 0, 0};
-    bool cur_tma = false;
-    if ((long long)blockIdx.x < ntiles) {
-        cur = tile_coords(blockIdx.x, X, ny);
-        cur_tma = stage(cur);
-    }
-    tma_pending = cur_tma;
-    for (long long k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        // one thread watches each barrier (bounded) and the CTA follows it through a barrier:
-        // the other warps sleep in the barrier instead of taking issue slots with polling
-        if (cur_tma) {
-            const bool in_ok = threadIdx.x == 0 ? energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns) : true;
-            if (__syncthreads_or(!in_ok)) {
-                ok = false;
-                break;
+    const int ny = (Y + TCY - 1) / TCY, nxc = (X + XC - 1) / XC;
+    const long long nruns = (long long)T * ny * nxc;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- line steps, in run order, each once its slot's previous line step is released
+        int L = 0;
+        for (long long k = blockIdx.x; k < nruns && ok; k += gridDim.x) {
+            const TcRun r = tc_run(k, X, ny, nxc, XC);
+            for (int l = 0; l < r.n + 2; ++l, ++L) {
+                const int s = L % TC2_RS, u = L / TC2_RS;
+                if (u >= 1) {
+                    const bool got = lane == 0 ? mbar_wait(smem_u32(lfree + s), (u - 1) & 1, limit_ns) : true;
+                    if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                tc2_stage_line(in, T, X, Y, bnd, r, l, sL + s * TC2_SLOT, smem_u32(lfull + s));
             }
-            tphase ^= 1u;
-            tma_pending = false;
-        } else {
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0 && !stall) {
-            const uint64_t a0 = energy_detail::smem_desc(smem_u32(sHb), TC1_GRP, 128);
+        // copies still in flight after a timeout land before the CTA exits
+        if (lane == 0)
+            for (int i = L - TC2_RS; i < L; ++i)
+                if (i >= 0) mbar_wait(smem_u32(lfull + i % TC2_RS), (i / TC2_RS) & 1, limit_ns);
+    } else if (warp == 1) {
+        // ---- products: 27 taps x 2 k-steps of tile j from the slots of line steps j .. j + 2
+        if (lane == 0) {
+            constexpr uint32_t idesc = energy_detail::instr_desc(1, 128, NB);
             const uint64_t b0 = energy_detail::smem_desc(smem_u32(sW), 128, 256);
+            int Lw = 0, Lb = 0, G = 0, last = -1;   // line steps waited for, first of the run, tiles
+            for (long long k = blockIdx.x; k < nruns && ok; k += gridDim.x) {
+                const TcRun r = tc_run(k, X, ny, nxc, XC);
+                for (int j = 0; j < r.n; ++j, ++G) {
+                    const int a = G & 1;
+                    for (; Lw <= Lb + j + 2 && ok; ++Lw)
+                        ok = mbar_wait(smem_u32(lfull + Lw % TC2_RS), (Lw / TC2_RS) & 1, limit_ns);
+                    if (ok && G >= 2) ok = mbar_wait(smem_u32(bdrain + a), ((G >> 1) - 1) & 1, limit_ns);
+                    if (!ok) break;
+                    if (stall) continue;   // test hook: no products, so every later wait runs out
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t acc = tmem + (uint32_t)(32 * a);
 #pragma unroll
-            for (int tap = 0; tap < 27; ++tap) {
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const uint64_t a0 =
+                            energy_detail::smem_desc(smem_u32(sL + ((Lb + j + dx) % TC2_RS) * TC2_SLOT), TC1_GRP, 128);
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t aoff = (((tap / 9) * 3 + (tap / 3) % 3) * TC1_LINE + (tap % 3) * 16 +
-                                           ks * 2 * TC1_GRP) >> 4;
-                    const uint32_t boff = ((tap * 2 + ks) * BT) >> 4;
-                    tc_mma_bf16(tmem, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
+                        for (int dt = 0; dt < 3; ++dt)
+#pragma unroll
+                            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                                for (int ks = 0; ks < 2; ++ks) {
+                                    const int tap = (dt * 3 + dx) * 3 + dy;
+                                    const uint32_t aoff = (dt * TC2_TLINE + dy * 16 + ks * 2 * TC1_GRP) >> 4;
+                                    const uint32_t boff = ((tap * 2 + ks) * BT) >> 4;
+                                    tc_mma_bf16(acc, a0 + aoff, b0 + boff, idesc, (tap | ks) != 0);
+                                }
+                    }
+                    // tile j is the last reader of line step j (and of the run's last two)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(lfree + (Lb + j) % TC2_RS))
+                                 : "memory");
+                    if (j == r.n - 1)
+                        for (int e = 1; e <= 2; ++e)
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                             smem_u32(lfree + (Lb + j + e) % TC2_RS))
+                                         : "memory");
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(bacc + a))
+                                 : "memory");
+                    last = G;
                 }
+                Lb += r.n + 2;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(bar))
-                         : "memory");
+            // products still running after a timeout finish before the accumulators are freed
+            if (last >= 0) mbar_wait(smem_u32(bacc + (last & 1)), (last >> 1) & 1, limit_ns);
         }
-        const bool done = threadIdx.x == 0 ? energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns) : true;
-        if (__syncthreads_or(!done)) {
-            ok = false;
-            break;
-        }
-        phase ^= 1u;
-        // the halo is free: the next tile's copies overlap this tile's epilogue
-        const TileC done_c = cur;
-        const long long kn = k + gridDim.x;
-        if (kn < ntiles) {
-            cur = tile_coords(kn, X, ny);
-            cur_tma = stage(cur);
-            tma_pending = cur_tma;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (CO == kWidth) {
-            tc_epilogue_hidden(tmem, done_c, X, Y, sb, out);
-        } else {
-            const int warp = threadIdx.x >> 5, q = warp & 3;
-            if (warp < 4) {   // N = 16: one load per lane quadrant
-                float v[16];
-                energy_detail::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16), v);
-                const int y = done_c.y0 + 32 * q + (threadIdx.x & 31);
-                if (y < Y) {
-                    const long long vox = ((long long)done_c.t * X + done_c.x) * Y + y;
-#pragma unroll
-                    for (int ch = 0; ch < CO; ++ch) E[ch * Nv + vox] = (v[ch] + sb[ch]) * out_scale;
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    } else {
+        // ---- epilogue: accumulator G % 2 of tile G
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const float out_scale = out_scale_p ? *out_scale_p : 1.f;
+        const long long Nv = (long long)T * X * Y;
+        int G = 0;
+        for (long long k = blockIdx.x; k < nruns && ok; k += gridDim.x) {
+            const TcRun r = tc_run(k, X, ny, nxc, XC);
+            for (int j = 0; j < r.n; ++j, ++G) {
+                const int a = G & 1;
+                const bool got = lane == 0 ? mbar_wait(smem_u32(bacc + a), (G >> 1) & 1, limit_ns) : true;
+                if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) {
+                    ok = false;
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const TileC c{r.t, r.x0 + j, r.y0};
+                const uint32_t acc = tmem + (uint32_t)(32 * a);
+                if (CO == kWidth) {
+                    tc_epilogue_hidden(acc, q, h, c, X, Y, sb, out);
+                } else if (h == 0) {   // N = 16: one load per lane quadrant
+                    float v[16];
+                    energy_detail::tmem_ld16(acc + ((uint32_t)(32 * q) << 16), v);
+                    const int y = c.y0 + 32 * q + lane;
+                    if (y < Y) {
+                        const long long vox = ((long long)c.t * X + c.x) * Y + y;
+#pragma unroll
+                        for (int ch = 0; ch < CO; ++ch) E[ch * Nv + vox] = (v[ch] + sb[ch]) * out_scale;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bdrain + a)) : "memory");
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
-    if (!ok && threadIdx.x == 0) {
-        atomicExch(status, (int)SAL_ERR_TIMEOUT);
-        if (!stall) energy_detail::mbar_wait(smem_u32(bar), phase, limit_ns);
-    }
-    // copies still in flight (a timeout after a prefetch) must land before the CTA exits
-    if (tma_pending && threadIdx.x == 0) energy_detail::mbar_wait(smem_u32(bar + 1), tphase, limit_ns);
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!ok && lane == 0) atomicExch(status, (int)SAL_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
-}
-
-template <int CO>
-constexpr size_t tc1_smem() { return (size_t)27 * 2 * (CO > 16 ? 768 : 512) + (CO > 16 ? 256 : 0) + TC1_HALO + 64; }
-
-// The activation tensor [T][X][Y][24] BF16 as a 4-D tiled map with boxes of 8 channels x 130
-// rows; false when the encoder is unavailable or refuses (then every halo is copied by cp.async).
-bool encode_act_map(const __nv_bfloat16 *act, sal_dims d, CUtensorMap *map)
-{
-    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static EncodeFn fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeFn)p;
-        looked = true;
-    }
-    if (!fn) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)kWidth, (cuuint64_t)d.Y, (cuuint64_t)d.X, (cuuint64_t)d.T};
-    const cuuint64_t row = (cuuint64_t)kWidth * sizeof(__nv_bfloat16);
-    const cuuint64_t strides[3] = {row, row * (cuuint64_t)d.Y, row * (cuuint64_t)d.Y * (cuuint64_t)d.X};
-    const cuuint32_t box[4] = {8, (cuuint32_t)TCH, 1, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    memset(map, 0, sizeof(*map));
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)act, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // One layer on the tensor cores: CO = 24 (hidden) or 3 (output, writes E).
@@ -776,15 +786,18 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, sal_dims d, int bnd, const f
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    constexpr size_t smem = tc1_smem<CO>();
-    cudaError_t e = set_smem(conv_tc1_kernel<CO>, smem);
+    constexpr size_t smem = tc2_smem<CO>();
+    cudaError_t e = set_smem(conv_tc2_kernel<CO>, smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = 2 * (int64_t)nsm;                 // two CTAs per SM (shared memory), persistent
-    if (grid > ntiles) grid = ntiles;
-    CUtensorMap map;
-    const int use_tma = encode_act_map(in, d, &map) ? 1 : 0;
-    conv_tc1_kernel<CO><<<(unsigned)grid, TC_NT, smem, s>>>(in, (int)d.T, (int)d.X, (int)d.Y, bnd, w, b, out, E,
-                                                           out_scale, c.status, c.stall, c.limit_ns, map, use_tma);
+    // runs along x of at most 64 tiles, shorter where that leaves fewer than 8 runs per SM
+    int64_t XC = ntiles / ((int64_t)nsm * 8);
+    XC = XC < 4 ? 4 : (XC > 64 ? 64 : XC);
+    if (XC > d.X) XC = d.X;
+    const int64_t nruns = d.T * ny * ((d.X + XC - 1) / XC);
+    int64_t grid = nsm;                              // one CTA per SM (shared memory), persistent
+    if (grid > nruns) grid = nruns;
+    conv_tc2_kernel<CO><<<(unsigned)grid, TC2_NT, smem, s>>>(in, (int)d.T, (int)d.X, (int)d.Y, bnd, w, b, out, E,
+                                                            out_scale, c.status, c.stall, c.limit_ns, (int)XC);
     return cudaGetLastError();
 }
 

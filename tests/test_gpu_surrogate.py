@@ -46,19 +46,23 @@ def test_forward_matches_reference():
     assert np.abs(got_inf - ref).max() / np.abs(ref).max() < 3e-2
 
 
-@pytest.mark.parametrize("shape", [(12, 14, 40), (9, 7, 300)])
-def test_tensor_core_inference_matches_cuda_cores_and_reference(shape):
+@pytest.mark.parametrize("shape,bnd", [((12, 14, 40), "reflect"), ((9, 7, 300), "reflect"),
+                                       ((5, 6, 128), "periodic"), ((8, 4, 129), "reflect"),
+                                       ((6, 3, 257), "periodic"), ((10, 1, 1), "reflect")])
+def test_tensor_core_inference_matches_cuda_cores_and_reference(shape, bnd):
     """Hidden layers as tcgen05 products (BF16 operands, FP32 accumulation) against the CUDA-core
     inference (same BF16 activations) and the FP64 reference; lines of 128 outputs along y,
-    ragged at the end (40 and 300 = 2 x 128 + 44)."""
+    ragged at the end (40 and 300 = 2 x 128 + 44), lines whose halo meets both y faces, the
+    extension row y = Y at every position of a line (Y = 128, 129, 257) and single-sample axes."""
     V = synth.make_volume(shape, seed=2)
     model, params = _model(seed=4)
     Vd = torch.from_numpy(V).to(DEV)
     rms = np.sqrt(np.mean(V.astype(np.float64) ** 2))
-    ref = O.surrogate_forward(V[None].astype(np.float64) / rms, surrogate.WIDTHS, _bf16(params)) * rms
-    cc = model.forward(Vd, training=False).cpu().numpy()
+    ref = O.surrogate_forward(V[None].astype(np.float64) / rms, surrogate.WIDTHS, _bf16(params),
+                              bnd=O.PERIODIC if bnd == "periodic" else O.REFLECT) * rms
+    cc = model.forward(Vd, training=False, p=api.params(boundary=bnd)).cpu().numpy()
     api.sal_device_status()
-    tc = model.forward(Vd, training=False, p=api.params(precision="bf16")).cpu().numpy()
+    tc = model.forward(Vd, training=False, p=api.params(precision="bf16", boundary=bnd)).cpu().numpy()
     api.sal_device_status()
     assert np.isfinite(tc).all()
     assert np.abs(tc - cc).max() / np.abs(cc).max() < 1e-2
