@@ -68,12 +68,19 @@ struct EGeo {
     // mode 3: each region holds G1, a G2 slice or a V halo tile
     static constexpr int NREG_RAW = NG1 > 2 * NG2 ? (NG1 > NVR ? NG1 : NVR) : (2 * NG2 > NVR ? 2 * NG2 : NVR);
     static constexpr int NREG = (NREG_RAW + 3) / 4 * 4;
+    // mode 4: G2 slices in batches of at most four lines, RSB float2 per output row (an odd
+    // multiple of 16 bytes, as PY2 is an odd multiple of 16 bytes)
+    static constexpr int RSB = 4 * PY2 + 2;
+    static constexpr int NG2Q = ROWS * RSB;             // float2
+    static constexpr int NALIASQ = (NV * 4 > NG2Q * 8) ? NV : NG2Q * 2;
     static constexpr size_t SMEM =
         sizeof(float) * (size_t)(MODE == 0   ? NG1 + NALIAS + NW
                                  : MODE == 1 ? NG1 + (NVR > 2 * NG2B ? NVR : 2 * NG2B) + NW
                                  : MODE == 2 ? NVR + NG1M + 2 * NG2B + NW
+                                 : MODE == 4 ? NG1 + NALIASQ + NW
                                              : 2 * NREG + NW);
-    static_assert(MODE >= 0 && MODE <= 3, "tile mode");
+    static_assert(MODE >= 0 && MODE <= 4, "tile mode");
+    static_assert(MODE != 4 || (L_ == 7 && PAIR4 && !PAIR0), "mode 4 is laid out for L = 7");
 };
 
 // ---- packed pairs of floats -------------------------------------------------------------
@@ -1337,6 +1344,189 @@ __device__ __forceinline__ void energy_tile_b(const float *__restrict__ V, int64
     store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
 }
 
+// ---- mode 4: the G2 slice of a mu in batches of at most four lines ----------------------
+// Rows of RSB float2 (an odd multiple of 16 bytes apart).  mu = 0: lines nu = 0..H at slots
+// 0..H (batch 0 only).  mu > 0, batch 0: the nu = 0 line at slot 0 and the pair |nu| = 1 at
+// slots 1-2; batch 1: the pairs |nu| = 2, 3 at slots 0-1 and 2-3 (pairs interleaved per column
+// as in mode 0).  Stage x walks a column once per batch (its loads and differences twice per
+// mu > 0, the per-frequency work once), so a CTA needs 50 KB instead of 65 KB and four fit an
+// SM instead of three; the arithmetic and its order are mode 0's.
+template <class G, int B>
+__device__ __forceinline__ void x_stage_q(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
+{
+    constexpr int L = G::L, H = G::H, PY = G::PY, BX = G::BX, NZX = BX + 2 * H;
+    constexpr int XS = L * PY;           // G1 stride between x'
+    constexpr int RS = G::RSB;           // G2 stride between output rows x (float2)
+    constexpr int NLO = B == 0 ? 1 : 2, NHI = B == 0 ? 1 : H;   // pairs of this batch (mu > 0)
+    for (int i = threadIdx.x; i < G::BT * PY; i += G::NT) {
+        const int t = i / PY, yy = i - t * PY;
+        const float *g = sG1 + (t * G::HX * L) * PY + yy;
+        float2 *o = sG2 + (t * BX) * RS + yy;   // slot 0 of output row (t, x = 0)
+        if (mu == 0) {
+            float z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
+            const float z0 = z[H];
+            float sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const float p = z[H + k] + z[H - k];
+                sum += p;
+                U[k] = fmaf(-2.f, z0, p);
+                D[k] = z[H + k] - z[H - k];
+            }
+            o[0] = make_float2(sum, 0.f);
+            float pr[H + 1], pi[H + 1];
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                float A = 0.f, Bs = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
+                    Bs = fmaf(D[k], lo(tw.s2[(nu * k) % L]), Bs);
+                }
+                o[nu * G::PY2] = make_float2(A, -Bs);   // F_0(nu) = A - iB = Q_0(nu)
+                pr[nu] = A;
+                pi[nu] = -Bs;
+            }
+#pragma unroll
+            for (int r = 1; r < BX; ++r) {
+                const float d = z[r + 2 * H] - z[r - 1];
+                sum += d;
+                float2 *orow = o + r * RS;
+                orow[0] = make_float2(sum, 0.f);
+#pragma unroll
+                for (int nu = 1; nu <= H; ++nu) {
+                    const int k = tw_index<L>(nu, r - 1 - H);
+                    pr[nu] = fmaf(d, lo(tw.c2[k]), pr[nu]);    // + d e^{-i th k}
+                    pi[nu] = fmaf(-d, lo(tw.s2[k]), pi[nu]);
+                    orow[nu * G::PY2] = make_float2(pr[nu], pi[nu]);
+                }
+            }
+        } else {
+            const int cre = (2 * mu - 1) * PY, cim = 2 * mu * PY;
+            const f2x m2 = pk(-2.f, -2.f);
+            f2x z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = pk(g[n * XS + cre], g[n * XS + cim]);
+            const f2x z0 = z[H];
+            f2x sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const f2x p = add2(z[H + k], z[H - k]);
+                sum = add2(sum, p);
+                U[k] = fma2(z0, m2, p);
+                D[k] = sub2(z[H + k], z[H - k]);
+            }
+            f2x *o2 = reinterpret_cast<f2x *>(o);
+            // first pair of the batch: a pair line holds one float4 per column y'
+            float4 *o4 = reinterpret_cast<float4 *>(sG2 + (t * BX) * RS + (B == 0 ? G::PY2 : 0)) + yy;
+            if (B == 0) o2[0] = sum;
+            f2x Pp[H + 1], Pm[H + 1];   // P(+nu), P(-nu)
+#pragma unroll
+            for (int nu = NLO; nu <= NHI; ++nu) {
+                f2x A = mul2(U[1], tw.c2[nu % L]);
+                f2x Bs = mul2(D[1], tw.s2[nu % L]);
+#pragma unroll
+                for (int k = 2; k <= H; ++k) {
+                    A = fma2(U[k], tw.c2[(nu * k) % L], A);
+                    Bs = fma2(D[k], tw.s2[(nu * k) % L], Bs);
+                }
+                const float ax = lo(A), ay = hi(A), bx = lo(Bs), by = hi(Bs);
+                const f2x Fp = pk(ax + by, ay - bx);   // F_0(+nu) = A - iB
+                const f2x Fm = pk(ax - by, ay + bx);   // F_0(-nu) = A + iB
+                o4[(nu - NLO) * G::PY2] = make_float4(lo(Fp), lo(Fm), hi(Fp), hi(Fm));
+                Pp[nu] = Fp;
+                Pm[nu] = Fm;
+            }
+#pragma unroll
+            for (int r = 1; r < BX; ++r) {
+                const f2x d = sub2(z[r + 2 * H], z[r - 1]);
+                const f2x dsw = swapneg(d);
+                if (B == 0) {
+                    sum = add2(sum, d);
+                    o2[r * RS] = sum;
+                }
+#pragma unroll
+                for (int nu = NLO; nu <= NHI; ++nu) {
+                    const int k = tw_index<L>(nu, r - 1 - H);
+                    Pp[nu] = rot_acc<L>(Pp[nu], d, dsw, tw, k);
+                    Pm[nu] = rot_acc<L>(Pm[nu], d, dsw, tw, (L - k) % L);
+                    o4[r * (RS / 2) + (nu - NLO) * G::PY2] = make_float4(lo(Pp[nu]), lo(Pm[nu]), hi(Pp[nu]), hi(Pm[nu]));
+                }
+            }
+        }
+    }
+}
+
+// Stage y of batch B of one mu (the lines x_stage_q<G, B> left in sG2), in mode 0's order.
+template <class G, int B>
+__device__ __forceinline__ void y_stage_q(const float2 *sG2, int row, int j, int mu, const float *sW,
+                                          const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
+{
+    constexpr int H = G::H;
+    const float2 *l0 = sG2 + row * G::RSB;
+    if (mu == 0) {
+        y_real<G>(l0, j, sW, tw, et, ex, ey);
+#pragma unroll 1
+        for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
+    } else if (B == 0) {
+        y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
+        y_pair4<G>(reinterpret_cast<const float4 *>(l0 + G::PY2), j, mu, 1, sW, tw, et, ex, ey);
+    } else {
+        const float4 *l4 = reinterpret_cast<const float4 *>(l0);
+#pragma unroll 1
+        for (int nu = 2; nu <= H; ++nu) y_pair4<G>(l4 + (nu - 2) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void energy_tile_q(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
+                                              int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
+                                              const SpecTables &tb, float *smem)
+{
+    constexpr int L = G::L, H = G::H;
+    float *sG1 = smem;
+    float2 *sG2 = reinterpret_cast<float2 *>(smem + G::NG1);
+    float *sV = smem + G::NG1;   // aliases sG2: dead once stage t is done
+    float *sW = smem + G::NG1 + G::NALIASQ;
+
+    fill_w<G>(sW, tb);
+    const int ty = (int)(tile % tiles_y);
+    const int tx = (int)((tile / tiles_y) % tiles_x);
+    const int64_t tt = tile / ((int64_t)tiles_y * tiles_x);
+    const int64_t t0 = tt * G::BT, x0 = (int64_t)tx * G::BX, y0 = (int64_t)ty * G::BY;
+
+    stage_v<G>(V, T, X, Y, bnd, t0, x0, y0, sV);
+    __syncthreads();
+    Tw<L> tw;
+    tw.load(tb);
+    t_stage<G>(sV, sG1, tw);
+    __syncthreads();
+
+    const int row = threadIdx.x % G::ROWS, j = threadIdx.x / G::ROWS;
+    const bool ylive = y0 + G::R * j < Y;   // strips wholly past the last column sit out stage y
+    float et[G::R], ex[G::R], ey[G::R];
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
+
+#pragma unroll 1
+    for (int mu = 0; mu <= H; ++mu) {
+        x_stage_q<G, 0>(sG1, sG2, mu, tw);
+        __syncthreads();
+        if (ylive) y_stage_q<G, 0>(sG2, row, j, mu, sW, tw, et, ex, ey);
+        __syncthreads();
+        if (mu > 0) {
+            x_stage_q<G, 1>(sG1, sG2, mu, tw);
+            __syncthreads();
+            if (ylive) y_stage_q<G, 1>(sG2, row, j, mu, sW, tw, et, ex, ey);
+            __syncthreads();
+        }
+    }
+
+    store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
+}
+
 template <class G>
 __device__ __forceinline__ void energy_tile_any(const float *__restrict__ V, int64_t T, int64_t X, int64_t Y, int bnd,
                                                 int64_t tile, int tiles_x, int tiles_y, float *__restrict__ E,
@@ -1344,6 +1534,8 @@ __device__ __forceinline__ void energy_tile_any(const float *__restrict__ V, int
 {
     if constexpr (G::MODE == 0)
         energy_tile<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
+    else if constexpr (G::MODE == 4)
+        energy_tile_q<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
     else
         energy_tile_b<G>(V, T, X, Y, bnd, tile, tiles_x, tiles_y, E, tb, smem);
 }
