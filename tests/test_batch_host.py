@@ -56,17 +56,17 @@ def test_autotune_cache_roundtrip_and_corrupt_file(lib, tmp_path):
     assert lib.sal_autotune_clear() == 0
     c = N.SalTileChoice()
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0
-    assert (c.shape, c.ms) == (0, 0.0) and (c.bt, c.bx, c.by, c.mode) == (2, 8, 32, 0)
+    assert (c.shape, c.ms) == (0, 0.0) and (c.bt, c.bx, c.by, c.mode) == (2, 8, 32, 4)
     good = tmp_path / "tune.txt"
-    good.write_text("# sal autotune cache v1: L precision size_class shape ms\n7 0 1 2 31.5\n5 0 0 1 0.25\n")
+    good.write_text("# sal autotune cache v1: L precision size_class shape ms\n7 0 1 3 31.5\n5 0 0 1 0.25\n")
     assert lib.sal_autotune_load(str(good).encode()) == 0
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0
-    assert (c.shape, c.bt, c.bx, c.by, c.mode, c.size_class) == (2, 2, 8, 32, 3, 1) and abs(c.ms - 31.5) < 1e-5
+    assert (c.shape, c.bt, c.bx, c.by, c.mode, c.size_class) == (3, 2, 8, 32, 3, 1) and abs(c.ms - 31.5) < 1e-5
     assert lib.sal_autotune_query(7, 0, 1000, ctypes.byref(c)) == 0 and c.shape == 0   # other size class
     saved = tmp_path / "saved.txt"
     assert lib.sal_autotune_save(str(saved).encode()) == 0
     lines = [ln for ln in saved.read_text().splitlines() if not ln.startswith("#")]
-    assert sorted(ln.split()[:4] for ln in lines) == [["5", "0", "0", "1"], ["7", "0", "1", "2"]]
+    assert sorted(ln.split()[:4] for ln in lines) == [["5", "0", "0", "1"], ["7", "0", "1", "3"]]
     for bad in ("# sal autotune cache v1\n7 0 1 9 1.0\n",            # shape index out of range
                 "# sal autotune cache v1\n8 0 1 0 1.0\n",            # even L
                 "# sal autotune cache v1\n7 0 1 0\n",                # short line
@@ -75,7 +75,7 @@ def test_autotune_cache_roundtrip_and_corrupt_file(lib, tmp_path):
         corrupt = tmp_path / "bad.txt"
         corrupt.write_text(bad)
         assert lib.sal_autotune_load(str(corrupt).encode()) == N.SAL_ERR_INVALID_ARG
-        assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0 and c.shape == 2   # unchanged
+        assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0 and c.shape == 3   # unchanged
     assert lib.sal_autotune_load(str(tmp_path / "missing.txt").encode()) == N.SAL_ERR_INVALID_ARG
     assert lib.sal_autotune_clear() == 0
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0 and c.shape == 0
