@@ -1459,25 +1459,29 @@ __device__ __forceinline__ void x_stage_q(const float *sG1, float2 *sG2, int mu,
     }
 }
 
-// Stage y of batch B of one mu (the lines x_stage_q<G, B> left in sG2), in mode 0's order.
-template <class G, int B>
-__device__ __forceinline__ void y_stage_q(const float2 *sG2, int row, int j, int mu, const float *sW,
+// Stage y of batch b of one mu (the lines x_stage_q<G, b> left in sG2), in mode 0's order;
+// rolled loops over the step's single lines and pairs, so each walker is inlined once.
+template <class G>
+__device__ __forceinline__ void y_stage_q(const float2 *sG2, int row, int j, int mu, int b, const float *sW,
                                           const Tw<G::L> &tw, float (&et)[G::R], float (&ex)[G::R], float (&ey)[G::R])
 {
     constexpr int H = G::H;
     const float2 *l0 = sG2 + row * G::RSB;
+    // single lines: mu = 0, nu = 1..H (after the real line nu = 0); mu > 0, batch 0: nu = 0
+    int s0 = 0, s1 = b == 0 ? 0 : -1;
     if (mu == 0) {
         y_real<G>(l0, j, sW, tw, et, ex, ey);
-#pragma unroll 1
-        for (int nu = 1; nu <= H; ++nu) y_single<G>(l0 + nu * G::PY2, j, 0, nu, sW, tw, et, ex, ey);
-    } else if (B == 0) {
-        y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
-        y_pair4<G>(reinterpret_cast<const float4 *>(l0 + G::PY2), j, mu, 1, sW, tw, et, ex, ey);
-    } else {
-        const float4 *l4 = reinterpret_cast<const float4 *>(l0);
-#pragma unroll 1
-        for (int nu = 2; nu <= H; ++nu) y_pair4<G>(l4 + (nu - 2) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
+        s0 = 1;
+        s1 = H;
     }
+#pragma unroll 1
+    for (int nu = s0; nu <= s1; ++nu) y_single<G>(l0 + nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
+    if (mu == 0) return;
+    // pairs: batch 0 the pair |nu| = 1 after the single line, batch 1 the pairs 2..H
+    const int p0 = b == 0 ? 1 : 2, p1 = b == 0 ? 1 : H;
+    const float4 *l4 = reinterpret_cast<const float4 *>(l0 + (b == 0 ? G::PY2 : 0));
+#pragma unroll 1
+    for (int nu = p0; nu <= p1; ++nu) y_pair4<G>(l4 + (nu - p0) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
 }
 
 template <class G>
@@ -1510,18 +1514,17 @@ __device__ __forceinline__ void energy_tile_q(const float *__restrict__ V, int64
 #pragma unroll
     for (int r = 0; r < G::R; ++r) et[r] = ex[r] = ey[r] = 0.f;
 
+    // (mu, batch) steps in order, one call site each so that stage y is inlined once
 #pragma unroll 1
-    for (int mu = 0; mu <= H; ++mu) {
-        x_stage_q<G, 0>(sG1, sG2, mu, tw);
-        __syncthreads();
-        if (ylive) y_stage_q<G, 0>(sG2, row, j, mu, sW, tw, et, ex, ey);
-        __syncthreads();
-        if (mu > 0) {
+    for (int step = 0; step < 2 * H + 1; ++step) {
+        const int mu = (step + 1) >> 1, b = step > 0 && !(step & 1);
+        if (b == 0)
+            x_stage_q<G, 0>(sG1, sG2, mu, tw);
+        else
             x_stage_q<G, 1>(sG1, sG2, mu, tw);
-            __syncthreads();
-            if (ylive) y_stage_q<G, 1>(sG2, row, j, mu, sW, tw, et, ex, ey);
-            __syncthreads();
-        }
+        __syncthreads();
+        if (ylive) y_stage_q<G>(sG2, row, j, mu, b, sW, tw, et, ex, ey);
+        __syncthreads();
     }
 
     store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
