@@ -47,8 +47,8 @@ MUFU_PER_SM_CLK = 16             # square roots per SM and clock on the XU (MUFU
 # scaled to the full volume by the voxel count), keyed by (workload, L, precision).  Only
 # the default tile shape; any other configuration reports null.
 ENERGY_TRAFFIC = {
-    ("f3", 7, "fp32"): (4.360e9, "profiles/traffic_slab_462x951x160_L7.md: "
-                                 "(281.4 MB + 790.3 MB) on the slab x 4.0687"),
+    ("f3", 7, "fp32"): (4.371e9, "profiles/traffic_slab_462x951x160_L7.md: "
+                                 "(282.6 MB + 791.8 MB) on the slab x 4.0687"),
 }
 
 
