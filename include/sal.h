@@ -153,7 +153,9 @@ SAL_API sal_status sal_interpolate_lattice(const float *Ec, sal_dims dims, const
 /*
  * Directional centre-surround comparison, Eq. 5, of each E_m: Sm [3][T*X*Y], plus the
  * global (min, max, sum) of each S_m in `stats` (device, SAL_STATS_LEN doubles; the
- * reductions are FP64).  `ws` must hold sal_dcs_workspace_size bytes.
+ * reductions are FP64).  `ws` must hold sal_dcs_workspace_size bytes.  The line and
+ * offset-list stencils address a plane by 32-bit offsets: with them X * Y must stay below
+ * 2^31 (beyond, SAL_ERR_CUDA from the launch), in every call that runs the compare.
  */
 SAL_API sal_status sal_directional_compare(const float *E, sal_dims dims, const sal_params *p,
                                    float *Sm, double *stats, void *ws, size_t ws_bytes,
