@@ -1082,6 +1082,12 @@ __device__ __forceinline__ void y_stage_mu(const float2 *sG2, int row, int j, in
 #pragma unroll 1
         for (int q = 0; q < H / 2; ++q) y_single_pair4<G>(l4 + q * G::PY2, j, 0, 2 * q + 1, 2 * q + 2, sW, tw, et, ex, ey);
         if (H & 1) y_single<G>(l0 + H * G::PY2, j, 0, H, sW, tw, et, ex, ey);
+    } else if constexpr (G::PAIR4 && G::PAIR0) {
+        const float2 *l0 = sG2 + row * L * G::PY2;         // line nu = 0, then the pairs |nu| = 1..H
+        y_single<G>(l0, j, mu, 0, sW, tw, et, ex, ey);
+        const float4 *l4 = reinterpret_cast<const float4 *>(l0 + G::PY2);
+#pragma unroll 1
+        for (int nu = 1; nu <= H; ++nu) y_pair4<G>(l4 + (nu - 1) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
     } else if constexpr (G::PAIR4) {
         // single lines from one call site (mu = 0: nu = 1..H after the real line; mu > 0: the
         // nu = 0 line before the pairs), so the walker is inlined once
