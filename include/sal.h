@@ -342,8 +342,8 @@ SAL_API sal_status sal_graph_destroy(sal_graph *g);
  * 1: larger), candidate index, its BT x BX x BY output tile and staging mode (0: all
  * intermediate spectra of a mu in shared memory; 1: the lines of one (mu, |nu|) at a time;
  * 2: as 1, with stage t rerun per mu; 3: as 0, the next tile's halo copied while the current
- * one is computed; 4: as 0, the spectra of a mu in batches of at most four lines, so that
- * four CTAs fit an SM (L = 7)), and its measured time. */
+ * one is computed; 4: as 0, the spectra of a mu in batches of a few lines, so that one more
+ * CTA fits an SM (L = 7, 9)), and its measured time. */
 typedef struct {
     int32_t L, precision, size_class, shape;
     int32_t bt, bx, by, mode;

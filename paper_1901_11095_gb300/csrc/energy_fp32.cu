@@ -24,7 +24,7 @@ const ShapeList kShapes[] = {
     {3, {{2, 8, 32, 0}, {4, 8, 32, 0}, {2, 16, 32, 0}}},
     {5, {{2, 8, 32, 0}, {1, 8, 32, 0}, {2, 16, 32, 0}}},
     {7, {{2, 8, 32, 4}, {2, 8, 32, 0}, {2, 16, 32, 0}, {2, 8, 32, 3}, {1, 16, 32, 0}, {2, 8, 32, 2}}},
-    {9, {{2, 8, 32, 0}, {2, 16, 32, 0}, {1, 16, 32, 0}}},
+    {9, {{2, 8, 32, 4}, {2, 8, 32, 0}, {2, 16, 32, 0}, {1, 16, 32, 0}}},
     {11, {{2, 16, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
     {13, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},
     {15, {{2, 8, 32, 0}, {1, 16, 32, 0}, {1, 8, 32, 0}}},

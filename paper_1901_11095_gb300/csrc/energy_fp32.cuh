@@ -68,9 +68,13 @@ struct EGeo {
     // mode 3: each region holds G1, a G2 slice or a V halo tile
     static constexpr int NREG_RAW = NG1 > 2 * NG2 ? (NG1 > NVR ? NG1 : NVR) : (2 * NG2 > NVR ? 2 * NG2 : NVR);
     static constexpr int NREG = (NREG_RAW + 3) / 4 * 4;
-    // mode 4: G2 slices in batches of at most four lines, RSB float2 per output row (an odd
-    // multiple of 16 bytes, as PY2 is an odd multiple of 16 bytes)
-    static constexpr int RSB = 4 * PY2 + 2;
+    // mode 4: G2 slices in batches of at most NSL line slots per output row (mu = 0 in one
+    // batch: its H + 1 lines, or with paired single lines its nu = 0 line and pairs; mu > 0: the
+    // nu = 0 line and the pairs 1..P0, then the pairs P0 + 1..H), RSB float2 per output row (an
+    // odd multiple of 16 bytes, as PY2 is an odd multiple of 16 bytes)
+    static constexpr int NSL = PAIR0 ? 1 + 2 * (H / 2) + (H & 1) : H + 1;
+    static constexpr int P0 = (NSL - 1) / 2;
+    static constexpr int RSB = NSL * PY2 + ((NSL & 1) ? 0 : 2);
     static constexpr int NG2Q = ROWS * RSB;             // float2
     static constexpr int NALIASQ = (NV * 4 > NG2Q * 8) ? NV : NG2Q * 2;
     static constexpr size_t SMEM =
@@ -80,7 +84,8 @@ struct EGeo {
                                  : MODE == 4 ? NG1 + NALIASQ + NW
                                              : 2 * NREG + NW);
     static_assert(MODE >= 0 && MODE <= 4, "tile mode");
-    static_assert(MODE != 4 || (L_ == 7 && PAIR4 && !PAIR0), "mode 4 is laid out for L = 7");
+    static_assert(MODE != 4 || (PAIR4 && (L_ == 7 || L_ == 9) && 2 * (H - P0) <= NSL && RSB % 2 == 0),
+                  "mode 4 is laid out for L = 7 and 9");
 };
 
 // ---- packed pairs of floats -------------------------------------------------------------
@@ -1362,25 +1367,73 @@ __device__ __forceinline__ void energy_tile_b(const float *__restrict__ V, int64
     store_outputs<G>(E, T, X, Y, t0, x0, y0, row, j, tb.escale, et, ex, ey);
 }
 
-// ---- mode 4: the G2 slice of a mu in batches of at most four lines ----------------------
-// Rows of RSB float2 (an odd multiple of 16 bytes apart).  mu = 0: lines nu = 0..H at slots
-// 0..H (batch 0 only).  mu > 0, batch 0: the nu = 0 line at slot 0 and the pair |nu| = 1 at
-// slots 1-2; batch 1: the pairs |nu| = 2, 3 at slots 0-1 and 2-3 (pairs interleaved per column
-// as in mode 0).  Stage x walks a column once per batch (its loads and differences twice per
-// mu > 0, the per-frequency work once), so a CTA needs 50 KB instead of 65 KB and four fit an
-// SM instead of three; the arithmetic and its order are mode 0's.
+// ---- mode 4: the G2 slice of a mu in batches of at most NSL line slots --------------------
+// Rows of RSB float2 (an odd multiple of 16 bytes apart).  mu = 0 (batch 0 only): lines
+// nu = 0..H at slots 0..H, or, with paired single lines (L = 9), the nu = 0 line at slot 0 and
+// the pairs (1, 2), (3, 4) at slots 1-2, 3-4.  mu > 0, batch 0: the nu = 0 line at slot 0 and the
+// pairs |nu| = 1..P0 from slot 1; batch 1: the pairs P0 + 1..H from slot 0 (pairs interleaved
+// per column as in mode 0).  Stage x walks a column once per batch (its loads and differences
+// twice per mu > 0, the per-frequency work once), so a CTA needs less shared memory (L = 7:
+// 50 KB instead of 65 KB, four CTAs per SM instead of three; L = 9: 74 KB instead of 94 KB,
+// three instead of two); the arithmetic and its order are mode 0's.
 template <class G, int B>
 __device__ __forceinline__ void x_stage_q(const float *sG1, float2 *sG2, int mu, const Tw<G::L> &tw)
 {
     constexpr int L = G::L, H = G::H, PY = G::PY, BX = G::BX, NZX = BX + 2 * H;
     constexpr int XS = L * PY;           // G1 stride between x'
     constexpr int RS = G::RSB;           // G2 stride between output rows x (float2)
-    constexpr int NLO = B == 0 ? 1 : 2, NHI = B == 0 ? 1 : H;   // pairs of this batch (mu > 0)
+    constexpr int NLO = B == 0 ? 1 : G::P0 + 1, NHI = B == 0 ? G::P0 : H;   // pairs of this batch (mu > 0)
     for (int i = threadIdx.x; i < G::BT * PY; i += G::NT) {
         const int t = i / PY, yy = i - t * PY;
         const float *g = sG1 + (t * G::HX * L) * PY + yy;
         float2 *o = sG2 + (t * BX) * RS + yy;   // slot 0 of output row (t, x = 0)
-        if (mu == 0) {
+        if (mu == 0 && G::PAIR0) {
+            // real input: the nu = 0 line at slot 0, the pairs (1, 2), (3, 4), ... from slot 1
+            // (Re a, Re b, Im a, Im b per column), nu = H alone after them when H is odd
+            float z[NZX];
+#pragma unroll
+            for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
+            const float z0 = z[H];
+            float sum = z0, U[H + 1], D[H + 1];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const float p = z[H + k] + z[H - k];
+                sum += p;
+                U[k] = fmaf(-2.f, z0, p);
+                D[k] = z[H + k] - z[H - k];
+            }
+            float4 *q0 = reinterpret_cast<float4 *>(sG2 + (t * BX) * RS + G::PY2) + yy;
+            float pr[H + 1], pi[H + 1];
+#pragma unroll
+            for (int nu = 1; nu <= H; ++nu) {
+                float A = 0.f, Bs = 0.f;
+#pragma unroll
+                for (int k = 1; k <= H; ++k) {
+                    A = fmaf(U[k], lo(tw.c2[(nu * k) % L]), A);
+                    Bs = fmaf(D[k], lo(tw.s2[(nu * k) % L]), Bs);
+                }
+                pr[nu] = A;   // F_0(nu) = A - iB = Q_0(nu)
+                pi[nu] = -Bs;
+            }
+#pragma unroll
+            for (int r = 0; r < BX; ++r) {
+                if (r > 0) {
+                    const float d = z[r + 2 * H] - z[r - 1];
+                    sum += d;
+#pragma unroll
+                    for (int nu = 1; nu <= H; ++nu) {
+                        const int k = tw_index<L>(nu, r - 1 - H);
+                        pr[nu] = fmaf(d, lo(tw.c2[k]), pr[nu]);    // + d e^{-i th k}
+                        pi[nu] = fmaf(-d, lo(tw.s2[k]), pi[nu]);
+                    }
+                }
+                o[r * RS] = make_float2(sum, 0.f);
+#pragma unroll
+                for (int q = 0; q < H / 2; ++q)
+                    q0[r * (RS / 2) + q * G::PY2] = make_float4(pr[2 * q + 1], pr[2 * q + 2], pi[2 * q + 1], pi[2 * q + 2]);
+                if (H & 1) o[r * RS + H * G::PY2] = make_float2(pr[H], pi[H]);
+            }
+        } else if (mu == 0) {
             float z[NZX];
 #pragma unroll
             for (int n = 0; n < NZX; ++n) z[n] = g[n * XS];
@@ -1485,9 +1538,20 @@ __device__ __forceinline__ void y_stage_q(const float2 *sG2, int row, int j, int
 {
     constexpr int H = G::H;
     const float2 *l0 = sG2 + row * G::RSB;
+    if constexpr (G::PAIR0) {
+        if (mu == 0) {   // the real line, then the paired single lines (and nu = H alone if odd)
+            y_real<G>(l0, j, sW, tw, et, ex, ey);
+            const float4 *q4 = reinterpret_cast<const float4 *>(l0 + G::PY2);
+#pragma unroll 1
+            for (int q = 0; q < H / 2; ++q)
+                y_single_pair4<G>(q4 + q * G::PY2, j, 0, 2 * q + 1, 2 * q + 2, sW, tw, et, ex, ey);
+            if (H & 1) y_single<G>(l0 + H * G::PY2, j, 0, H, sW, tw, et, ex, ey);
+            return;
+        }
+    }
     // single lines: mu = 0, nu = 1..H (after the real line nu = 0); mu > 0, batch 0: nu = 0
     int s0 = 0, s1 = b == 0 ? 0 : -1;
-    if (mu == 0) {
+    if (!G::PAIR0 && mu == 0) {
         y_real<G>(l0, j, sW, tw, et, ex, ey);
         s0 = 1;
         s1 = H;
@@ -1495,8 +1559,8 @@ __device__ __forceinline__ void y_stage_q(const float2 *sG2, int row, int j, int
 #pragma unroll 1
     for (int nu = s0; nu <= s1; ++nu) y_single<G>(l0 + nu * G::PY2, j, mu, nu, sW, tw, et, ex, ey);
     if (mu == 0) return;
-    // pairs: batch 0 the pair |nu| = 1 after the single line, batch 1 the pairs 2..H
-    const int p0 = b == 0 ? 1 : 2, p1 = b == 0 ? 1 : H;
+    // pairs: batch 0 the pairs 1..P0 after the single line, batch 1 the pairs P0 + 1..H
+    const int p0 = b == 0 ? 1 : G::P0 + 1, p1 = b == 0 ? G::P0 : H;
     const float4 *l4 = reinterpret_cast<const float4 *>(l0 + (b == 0 ? G::PY2 : 0));
 #pragma unroll 1
     for (int nu = p0; nu <= p1; ++nu) y_pair4<G>(l4 + (nu - p0) * G::PY2, j, mu, nu, sW, tw, et, ex, ey);

@@ -81,7 +81,7 @@ def test_autotune_single_volume_and_identical_results():
     api.sal_autotune_clear()
 
 
-@pytest.mark.parametrize("L", [3, 7])
+@pytest.mark.parametrize("L", [3, 5, 7, 9])
 def test_every_tile_shape_and_mode_agrees(L, tmp_path):
     """Each candidate (tile shape, staging mode) is forced through a cache file.  The kernels
     differ in how work is split and staged and in where the sliding recurrence along x
