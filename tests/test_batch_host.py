@@ -57,6 +57,10 @@ def test_autotune_cache_roundtrip_and_corrupt_file(lib, tmp_path):
     c = N.SalTileChoice()
     assert lib.sal_autotune_query(7, 0, 286_000_000, ctypes.byref(c)) == 0
     assert (c.shape, c.ms) == (0, 0.0) and (c.bt, c.bx, c.by, c.mode) == (2, 8, 32, 4)
+    # the defaults: batched spectra (mode 4) for L = 7 and 9, mode 0 elsewhere
+    for L, want in ((3, (2, 8, 32, 0)), (5, (2, 8, 32, 0)), (9, (2, 8, 32, 4)), (11, (2, 16, 32, 0))):
+        assert lib.sal_autotune_query(L, 0, 1000, ctypes.byref(c)) == 0
+        assert (c.shape, c.bt, c.bx, c.by, c.mode) == (0,) + want, L
     good = tmp_path / "tune.txt"
     good.write_text("# sal autotune cache v1: L precision size_class shape ms\n7 0 1 3 31.5\n5 0 0 1 0.25\n")
     assert lib.sal_autotune_load(str(good).encode()) == 0
